@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the dust equilibrium-temperature + emission hot path on GB300.
+
+One step = one dust_solve over the 2^18-cell, 200-wavelength, 96-grain
+workload (absorbed powers -> temperatures -> SED -> energy-balance residual)
+with inputs resident in device memory (J is 210 MB, larger than L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is whole-job grain-temperature solves per
+second of the full path in the mixed-precision (BF16x3) form; the FP32 path,
+the temperature-only rates, the SED cells/s and the errors against the FP64
+oracle are reported beside it.  Under torchrun every rank solves its own
+batch (weak scaling, no data-path collective).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grain-T solves/s & SED cells/s, mixed vs FP32 at stated err, 1 GB300; p99 ms"
+UNIT = "grain-T solves/s"
+CONFIG_ID = 1
+WORKLOAD = "2^18 cells x 200 wavelengths (0.09-1000 um) x 96 grains (3 species x 32 sizes), P_g(T) table 4096 pts"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="bf16x3")
+    ap.add_argument("--paths", default="fp32,bf16x3,fp16x3", help="precisions to measure")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.lines = []
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, line in self.lines:
+            if not (t0 - 0.06 <= ts <= t1 + 0.06):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    import synth
+    from paper_0907_3768_gb300 import Context, _lib
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world > 1:
+        __graft_entry__.build() if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+        __graft_entry__.build()
+
+    seed = synth.CONFIGS[CONFIG_ID]["seed"] + 7919 * rank
+    wl = synth.make_workload(CONFIG_ID, seed=seed)
+    C, K, G = wl.n_cells_total, wl.K, wl.G
+    ld = (K + 3) // 4 * 4
+    Jbuf = torch.zeros((C, ld), dtype=torch.float32, device=dev)
+    Jbuf[:, :K] = torch.from_numpy(wl.J).to(dev)
+    J = Jbuf[:, :K]
+    n = torch.from_numpy(wl.n).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ctxs = {}
+    for p in args.paths.split(","):
+        c = Context.from_workload(wl, precision=p, device=local)
+        try:
+            c.solve(J[:256], n[:256], precision=p)
+            torch.cuda.synchronize()
+            ctxs[p] = c
+        except _lib.DustError as e:
+            print(f"# precision {p} unavailable: {e}", file=sys.stderr)
+            c.close()
+    main = args.precision if args.precision in ctxs else "fp32"
+
+    def timed(ctx, steps, warmup, prec, want_L=True, want_resid=True, profile=False, clocks=False):
+        out = ctx.alloc_outputs(C, ld, want_L, want_resid, True)
+        for _ in range(warmup):
+            ctx.solve(J, n, precision=prec, out=out, stream=stream)
+        torch.cuda.synchronize()
+        _lib.dust_ctx_profile_read(ctx.handle)
+        if profile:
+            _lib.dust_ctx_profile(ctx.handle, True)
+        sampler = ClockSampler(_uuid(dev)) if clocks else None
+        if clocks:
+            time.sleep(0.3)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.solve(J, n, precision=prec, out=out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if world > 1:
+            dist.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = tt.item()
+        prof = None
+        if profile:
+            a, b, cnt = _lib.dust_ctx_profile_read(ctx.handle)
+            _lib.dust_ctx_profile(ctx.handle, False)
+            prof = (a / max(cnt, 1), b / max(cnt, 1), cnt)
+        clk = sampler.stop(t0, t1) if sampler else None
+        return ms, out, prof, clk
+
+    res = {}
+    ms_main, out_main, prof_main, clk = timed(ctxs[main], args.steps, args.warmup, main, profile=True, clocks=True)
+    res[main] = dict(ms_step=ms_main, out=out_main, prof=prof_main)
+    others = [p for p in ctxs if p != main]
+    k2 = max(3, min(args.steps, 60))
+    for p in others:
+        ms, out, prof, _ = timed(ctxs[p], k2, 3, p, profile=True)
+        res[p] = dict(ms_step=ms, out=out, prof=prof)
+    for p in ctxs:
+        ms_t, _, prof_t, _ = timed(ctxs[p], k2, 3, p, want_L=False, want_resid=False, profile=True)
+        res[p]["ms_T_only"] = ms_t
+        res[p]["prof_T_only"] = prof_t
+    for p in res:
+        ok = ctxs[p].check()
+        if ok != 0:
+            raise RuntimeError(f"device status {ok} after {p} runs")
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    Jh = torch.zeros((C, ld), dtype=torch.float32).pin_memory()
+    Jh[:, :K] = torch.from_numpy(wl.J)
+    nh = torch.from_numpy(wl.n).pin_memory()
+    Th = torch.empty((C, G), dtype=torch.float32).pin_memory()
+    Lh = torch.empty((C, ld), dtype=torch.float32).pin_memory()
+    rh = torch.empty((C,), dtype=torch.float64).pin_memory()
+    fh = torch.empty((C, G), dtype=torch.uint8).pin_memory()
+    cm = ctxs[main]
+    cm.set_precision(main)
+    args_h = (cm.handle, C, Jh.data_ptr(), ld, nh.data_ptr(), Th.data_ptr(), Lh.data_ptr(), rh.data_ptr(),
+              fh.data_ptr())
+    for _ in range(2):
+        _lib.dust_solve_host(*args_h)
+    ke = max(3, min(args.steps, 30))
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        _lib.dust_solve_host(*args_h)
+    te = (time.perf_counter() - t0) / ke
+    if world > 1:
+        tt = torch.tensor([te], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = tt.item()
+    h2d = C * ld * 4 + C * G * 4
+    d2h = C * G * 4 + C * ld * 4 + C * 8 + C * G
+
+    # roofline of the dominant kernel (the fused solve + emission kernel)
+    ex2_rate, fma_rate = _lib.dust_diag_throughput(local)
+    ms_emit = res[main]["prof"][1]
+    terms = C * G * K
+    achieved = terms / (ms_emit * 1e-3) / 1e9
+    peak = ex2_rate / 1e9
+    roofline = {"bound": "alu", "kernel": "k_solve_emit (temperature solve + emission, MUFU ex2)",
+                "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "G Planck terms/s",
+                "frac": round(achieved / peak, 4),
+                "peak_source": "measured MUFU ex2.approx issue rate (dust_diag_throughput), 1 ex2 per term",
+                "traffic": None, "ms_per_launch": round(ms_emit, 4),
+                "fma_pipe_peak_Gflop_lanes": round(fma_rate / 1e9, 1)}
+
+    line = {
+        "metric": METRIC, "value": C * G * world / (ms_main * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_main, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded generators: 2-temperature stellar field x U, toy grain model, MRN sizes)",
+        "config": {"workload": WORKLOAD, "precision": main, "cells_per_gpu": C, "K": K, "G": G,
+                   "l2": "inputs larger than L2 (J 210 MB, L 210 MB per step)",
+                   "parallelism": f"dp{world} (independent cell batches)"},
+        "sed_cells_per_s": C * world / (ms_main * 1e-3),
+        "gpu_launches": 2 * args.steps,
+        "roofline": roofline,
+        "clocks": clk,
+        "e2e": {"value": C * G * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": round(te * 1e3, 4), "api": "dust_solve_host (pinned host buffers)"},
+    }
+    paths = {}
+    for p in ctxs:
+        r = res[p]
+        paths[p] = {"ms_step": round(r["ms_step"], 5),
+                    "solves_per_s": C * G * world / (r["ms_step"] * 1e-3),
+                    "sed_cells_per_s": C * world / (r["ms_step"] * 1e-3),
+                    "ms_absorb": round(r["prof"][0], 5), "ms_solve_emit": round(r["prof"][1], 5),
+                    "T_only_ms": round(r["ms_T_only"], 5),
+                    "T_only_solves_per_s": C * G * world / (r["ms_T_only"] * 1e-3)}
+    line["paths"] = paths
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"], line["err_vs_oracle"] = cpu_baseline(args, wl, res)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for c in ctxs.values():
+        c.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _uuid(dev):
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def _oracle_sample(seconds, cfg_id=CONFIG_ID, seed=None):
+    """Oracle on the first cells of the workload, sized to ~`seconds` of work."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    probe = synth.make_workload(cfg_id, cells=np.arange(64), seed=seed)
+    t = time.perf_counter()
+    oracle.run_workload(probe)
+    per_cell = (time.perf_counter() - t) / 64
+    ncell = int(max(64, min(synth.CONFIGS[cfg_id]["n_cells"], seconds / max(per_cell, 1e-9))))
+    wl = synth.make_workload(cfg_id, cells=np.arange(ncell), seed=seed)
+    t = time.perf_counter()
+    ref = oracle.run_workload(wl)
+    dt = time.perf_counter() - t
+    return wl, ref, dt, oracle.max_threads()
+
+
+def cpu_baseline(args, wl_full, res):
+    import numpy as np
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from metrics import l_err, t_err
+
+    wl, ref, dt, cores = _oracle_sample(args.cpu_seconds, seed=wl_full.seed)
+    nc = len(wl.cells)
+    base = {"value": nc * wl.G / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {nc} of {wl_full.n_cells_total} cells, full path (A, Brent T, L, resid), "
+                      f"FP64 C + OpenMP, {dt:.1f} s"}
+    errs = {}
+    for p, r in res.items():
+        out = r["out"]
+        T = out["T"][:nc].cpu().numpy()
+        L = out["L"][:nc].cpu().numpy()
+        fl = out["flags"][:nc].cpu().numpy()
+        rs = out["resid"][:nc].cpu().numpy()
+        eT = t_err(T, ref["T"], ref["flags"])
+        eL = l_err(L, ref["L"])
+        errs[p] = {"T_max": float(eT.max()), "T_p99": float(np.percentile(eT, 99)),
+                   "L_max": float(eL.max()), "L_p99": float(np.percentile(eL, 99)),
+                   "resid_max": float(np.abs(rs).max()), "flags_equal": bool((fl == ref["flags"]).all()),
+                   "cells": nc}
+    return base, errs
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores (a deliberately slow baseline)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import synth
+
+    oracle.lib()
+    budget = 100.0
+    per_step = max(0.2, budget / max(1, args.steps + args.warmup))
+    wl = synth.make_workload(CONFIG_ID, cells=np.arange(64))
+    t = time.perf_counter()
+    oracle.run_workload(wl)
+    per_cell = (time.perf_counter() - t) / 64
+    ncell = int(max(8, min(4096, per_step / max(per_cell, 1e-9))))
+    wl = synth.make_workload(CONFIG_ID, cells=np.arange(ncell))
+    for _ in range(args.warmup):
+        oracle.run_workload(wl)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run_workload(wl)
+    dt = (time.perf_counter() - t) / args.steps
+    v = ncell * wl.G / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_cells_per_step": ncell},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"first {ncell} cells per step, full path"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * dust.h -- C ABI of libdust, a GB300 (sm_103a) engine for dust-grain
+ * equilibrium temperatures and the resulting infrared emission SED.
+ *
+ * Method: Jonsson & Primack, "Accelerating Dust Temperature Calculations with
+ * Graphics Processing Units".  For every cell c of a radiation-transfer grid
+ * and every grain g (species x size), with wavelengths lambda_k and quadrature
+ * weights w_k:
+ *
+ *   A[c,g] = sum_k w_k C_abs[g,k] J[c,k]                   absorbed power (Eq. 6)
+ *   P_g(T) = sum_k w_k C_abs[g,k] B_k(T)                   emitted power  (Eq. 7)
+ *   T[c,g] : P_g(T[c,g]) = A[c,g], T in [T_min, T_max]     equilibrium    (Eqs. 1, 7)
+ *   L[c,k] = 4 pi sum_g n[c,g] C_abs[g,k] B_k(T[c,g])      emission SED   (Eqs. 8-10)
+ *
+ * with B_k(T) = 2 h c^2 lambda_k^-5 / (exp(h c / (lambda_k k_B T)) - 1)
+ * (Eq. 1) and n[c,g] the number of grains g in cell c (the paper's
+ * n_s m_d;c of Eqs. 9-10, generalised to any per-cell, per-grain value).
+ *
+ * Conventions shared by every entry point:
+ *  - Status: every function returning int returns a dust_status code; a
+ *    non-zero code leaves a thread-local message for dust_last_error().
+ *    Nothing throws or aborts across this boundary.
+ *  - Argument checks happen on the host before anything is enqueued; a call
+ *    that fails them has no effect.
+ *  - Units are the caller's, but must be consistent: with lambda and w in m,
+ *    C_abs in m^2 and J in W m^-2 m^-1 sr^-1, A and P are in W sr^-1 and L
+ *    in W m^-1 (per unit n).
+ *  - Device pointers are plain CUDA device addresses on the context's device
+ *    (e.g. torch tensor data pointers); "stream" is a cudaStream_t passed as
+ *    void* (NULL = the legacy default stream).
+ */
+#ifndef DUST_H
+#define DUST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dust_ctx dust_ctx;
+typedef struct dust_server dust_server;
+
+enum dust_status {
+    DUST_OK = 0,
+    DUST_EINVAL = 1,     /* invalid argument                                   */
+    DUST_ENOMEM = 2,     /* device or host allocation failed                   */
+    DUST_ECUDA = 3,      /* a CUDA runtime / driver call failed                */
+    DUST_EBUSY = 4,      /* request can never be admitted (over the budget)    */
+    DUST_ETIMEOUT = 5,   /* a bounded device-side wait gave up                 */
+    DUST_ENOTFOUND = 6   /* unknown ticket                                     */
+};
+
+/* Arithmetic of the absorption contraction A = J W^T (Eq. 6).  The
+ * temperature solve and the emission always run in FP32; FP64 is used only
+ * to build the context tables and for the energy-balance residual. */
+enum dust_precision {
+    DUST_PREC_FP32 = 0,   /* FP32 FMA on the CUDA cores                          */
+    DUST_PREC_BF16X3 = 1, /* tensor cores: BF16 hi+lo split, 3 products, FP32 acc */
+    DUST_PREC_FP16X3 = 2  /* tensor cores: FP16 hi+lo split, 3 products, FP32 acc */
+};
+
+/* Per-grain solve flags written to the optional flags output. */
+enum dust_flag {
+    DUST_FLAG_OK = 0,      /* T solved inside the bracket                          */
+    DUST_FLAG_LOW = 1,     /* A < P_g(T_min) (includes A = 0): T = T_min           */
+    DUST_FLAG_HIGH = 2,    /* A > P_g(T_max): T = T_max                            */
+    DUST_FLAG_INVALID = 4  /* A negative or not finite (bad J): T = NaN            */
+};
+
+/* Create a context for one wavelength grid and one set of grains on `device`.
+ *
+ *  K, lambda[K], w[K]  host FP64, 2 <= K <= 8192: wavelengths (strictly increasing, > 0) and
+ *                      quadrature weights (>= 0) such that sum_k w_k f(lambda_k)
+ *                      approximates the integral over wavelength (the paper's
+ *                      Delta lambda_l, Eqs. 6-8).
+ *  G, c_abs[G*K]       host FP64, row-major [g][k]: absorption cross sections
+ *                      (the paper's sigma_a;s,l), >= 0, every row with some
+ *                      w_k C_abs[g,k] > 0.  1 <= G <= 512.
+ *  T_min, T_max        temperature bracket, 0 < T_min < T_max.
+ *  n_table             points of the P_g(T) table (uniform in log T), 64..65536;
+ *                      0 selects 4096.
+ *  precision           default dust_precision of dust_solve (changeable later).
+ *
+ * The context copies every input (the caller may free them on return), keeps
+ * all tables resident in device memory, and owns a scratch buffer for the
+ * absorbed powers that dust_solve grows on demand.  The P_g(T) table, its
+ * slope and an inverse table are built on the device in FP64 (replacing the
+ * per-iteration quadrature of the paper's Newton kernel, Section 4.3, by the
+ * table lookup its production code uses, Section 6).
+ * Also fails with DUST_EINVAL when h c / (lambda_max k_B T_max) < 1e-3 (the
+ * emission kernel's rational accumulation needs 1 - exp(-x) >= 1e-3).
+ * Synchronous; returns DUST_OK and *out, or an error and *out = NULL. */
+int dust_ctx_create(dust_ctx **out, int K, const double *lambda, const double *w, int G,
+                    const double *c_abs, double T_min, double T_max, int n_table,
+                    int precision, int device);
+
+/* Free a context and all its device memory (synchronises the device first).
+ * NULL is a no-op. */
+void dust_ctx_destroy(dust_ctx *ctx);
+
+/* Change the default precision of later dust_solve calls. */
+int dust_ctx_set_precision(dust_ctx *ctx, int precision);
+
+/* Shape and capability query: any output pointer may be NULL. */
+int dust_ctx_info(const dust_ctx *ctx, int *K, int *G, int *n_table, int *precision,
+                  int *device, size_t *device_bytes);
+
+/* Solve one batch of cells: the whole hot path of Eqs. 6-10, enqueued on
+ * `stream`; returns after enqueueing (the results are ready when the stream
+ * reaches that point).
+ *
+ *  n_cells   number of cells C >= 0 (0 is a no-op).
+ *  J         device FP32 [C x ld], row-major: mean intensity J[c,k] at
+ *            lambda_k (the paper's I_c,l), >= 0.  Columns K..ld-1 are ignored.
+ *  ld        row stride of J and L in elements, ld >= K.  The tensor-core
+ *            precisions also need ld % 4 == 0 and J 16-byte aligned (rows
+ *            read with the Tensor Memory Accelerator).
+ *  n         device FP32 [C x G] row-major: number of grains g in cell c, >= 0.
+ *  T         device FP32 [C x G] out: equilibrium temperatures.
+ *  L         device FP32 [C x ld] out, or NULL: emission SED L[c,k] (columns
+ *            K..ld-1 are not written).  With L = NULL and resid = NULL the
+ *            call stops after the temperatures.
+ *  resid     device FP64 [C] out, or NULL: per-cell energy-balance residual
+ *            r_c = sum_k w_k L[c,k] / (4 pi sum_g n[c,g] Pe[c,g]) - 1, where
+ *            Pe = A for solved grains and P_g(T_clamp) for clamped ones; it
+ *            vanishes for the exact solution (Eqs. 6, 7 and 10 together).
+ *  flags     device uint8 [C x G] out, or NULL: dust_flag per grain.
+ *  stream    cudaStream_t as void*.
+ *
+ * Ownership: all buffers belong to the caller and must stay valid until the
+ * stream passes this call.  Outputs must not overlap inputs.  One context may
+ * be used by one stream at a time (its scratch buffer is shared).  If the
+ * scratch buffer must grow, the call first synchronises `stream`.
+ * Errors: DUST_EINVAL (bad pointer / size / alignment), DUST_ENOMEM,
+ * DUST_ECUDA (launch failure; asynchronous faults surface at the next
+ * synchronisation). */
+int dust_solve(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n,
+               float *T, float *L, double *resid, uint8_t *flags, void *stream);
+
+/* Same as dust_solve, with an explicit precision for this call only. */
+int dust_solve_prec(dust_ctx *ctx, int precision, int64_t n_cells, const float *J, int64_t ld,
+                    const float *n, float *T, float *L, double *resid, uint8_t *flags,
+                    void *stream);
+
+/* dust_solve on HOST buffers (same shapes; ld applies to J and L): the cells
+ * are processed in chunks whose host->device copies, kernels and
+ * device->host copies overlap on two internal streams.  Host buffers should
+ * be page-locked for the copies to overlap.  Blocks until every output is
+ * in host memory.  Device staging buffers are owned by the context. */
+int dust_solve_host(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n,
+                    float *T, float *L, double *resid, uint8_t *flags);
+
+/* Read and clear the context's device status word (a dust_status: DUST_OK,
+ * or DUST_ETIMEOUT if a bounded wait inside a kernel gave up since the last
+ * call).  Synchronises the device. */
+int dust_ctx_check(dust_ctx *ctx, int *device_status);
+
+/* Per-kernel device timing.  While enabled, every solve on this context
+ * records CUDA events on its stream before the absorption kernel, between
+ * the two kernels and after the solve/emission kernel.
+ * dust_ctx_profile_read synchronises on the recorded events and returns the
+ * summed milliseconds of each kernel and the number of solves since the last
+ * read (any output may be NULL), then forgets them. */
+int dust_ctx_profile(dust_ctx *ctx, int enable);
+int dust_ctx_profile_read(dust_ctx *ctx, double *ms_absorb, double *ms_solve_emit,
+                          int64_t *n_solves);
+
+/* Diagnostics (no counterpart in the paper): measured issue rates on `device`
+ * of the two pipes the emission kernel uses, MUFU ex2.approx and FP32 FMA, in
+ * operations per second (lane operations), from compute-only kernels with 8
+ * independent chains per thread.  Used as roofline denominators. */
+int dust_diag_throughput(int device, double *ex2_per_s, double *ffma_per_s);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *dust_last_error(void);
+
+/* Library version string. */
+const char *dust_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DUST_H */

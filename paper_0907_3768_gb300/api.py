@@ -1,0 +1,143 @@
+"""Python front end of libdust: a context object over the C ABI.
+
+PyTorch supplies device memory and streams; every number is computed by the
+library's kernels.  There is no CPU fallback: without the built library or a
+CUDA device the calls raise.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PRECISIONS
+
+
+def _prec(p):
+    if isinstance(p, str):
+        return PRECISIONS[p.lower()]
+    return int(p)
+
+
+def _ptr(t):
+    return 0 if t is None else t.data_ptr()
+
+
+def padded_rows(J, multiple=4):
+    """A [C, K] view of J whose row stride is a multiple of `multiple` elements
+    (the tensor-core precisions read rows with 16-byte aligned TMA boxes)."""
+    C, K = J.shape
+    if J.stride(1) == 1 and J.stride(0) % multiple == 0 and J.data_ptr() % 16 == 0:
+        return J
+    ld = (K + multiple - 1) // multiple * multiple
+    buf = torch.zeros((C, ld), dtype=torch.float32, device=J.device)
+    buf[:, :K] = J
+    return buf[:, :K]
+
+
+class Context:
+    """One wavelength grid + grain set, with its tables resident on `device`."""
+
+    def __init__(self, lam, w, C_abs, T_min=2.0, T_max=3000.0, n_table=4096, precision="fp32", device=0):
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        C_abs = np.ascontiguousarray(C_abs, dtype=np.float64)
+        G, K = C_abs.shape
+        if lam.shape != (K,) or w.shape != (K,):
+            raise ValueError("lambda / w must have C_abs.shape[1] entries")
+        self.handle = None
+        self.handle = _lib.dust_ctx_create(K, lam.ctypes.data, w.ctypes.data, G, C_abs.ctypes.data,
+                                           float(T_min), float(T_max), int(n_table), _prec(precision),
+                                           int(device))
+        self.K, self.G, self.device = K, G, int(device)
+        self.T_min, self.T_max = float(T_min), float(T_max)
+
+    @classmethod
+    def from_workload(cls, wl, precision="fp32", device=0):
+        return cls(wl.lam, wl.w, wl.C_abs, wl.T_min, wl.T_max, wl.n_table, precision, device)
+
+    def close(self):
+        if self.handle:
+            _lib.dust_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def info(self):
+        return _lib.dust_ctx_info(self.handle)
+
+    def set_precision(self, precision):
+        _lib.dust_ctx_set_precision(self.handle, _prec(precision))
+
+    def check(self):
+        """Device status word since the last check (0 = DUST_OK)."""
+        return _lib.dust_ctx_check(self.handle)
+
+    def _check_inputs(self, J, n):
+        if not (J.is_cuda and n.is_cuda):
+            raise ValueError("J and n must be CUDA tensors")
+        if J.dtype != torch.float32 or n.dtype != torch.float32:
+            raise ValueError("J and n must be float32")
+        C = J.shape[0]
+        if J.dim() != 2 or J.shape[1] != self.K or J.stride(1) != 1 or J.stride(0) < self.K:
+            raise ValueError(f"J must be [C, {self.K}] with unit column stride")
+        if n.shape != (C, self.G) or not n.is_contiguous():
+            raise ValueError(f"n must be a contiguous [C, {self.G}] tensor")
+        return C, J.stride(0)
+
+    def alloc_outputs(self, C, ld, want_L=True, want_resid=True, want_flags=True):
+        dev = torch.device("cuda", self.device)
+        out = dict(T=torch.empty((C, self.G), dtype=torch.float32, device=dev))
+        out["L_buf"] = torch.empty((C, ld), dtype=torch.float32, device=dev) if want_L else None
+        out["L"] = out["L_buf"][:, :self.K] if want_L else None
+        out["resid"] = torch.empty((C,), dtype=torch.float64, device=dev) if want_resid else None
+        out["flags"] = torch.empty((C, self.G), dtype=torch.uint8, device=dev) if want_flags else None
+        return out
+
+    def solve(self, J, n, precision=None, want_L=True, want_resid=True, want_flags=True, out=None,
+              stream=None):
+        """Run the hot path on device tensors; returns a dict of output tensors
+        (T [C,G], L [C,K] view, resid [C] float64, flags [C,G] uint8)."""
+        C, ld = self._check_inputs(J, n)
+        if out is None:
+            out = self.alloc_outputs(C, ld, want_L, want_resid, want_flags)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        prec = _prec(precision) if precision is not None else self.info()["precision"]
+        _lib.dust_solve_prec(self.handle, prec, C, J.data_ptr(), ld, n.data_ptr(), out["T"].data_ptr(),
+                             _ptr(out["L_buf"]), _ptr(out["resid"]), _ptr(out["flags"]), sptr)
+        return out
+
+    def solve_host(self, J, n, T=None, L=None, resid=None, flags=None):
+        """The hot path on host arrays (numpy or CPU tensors, ideally pinned);
+        outputs are written into / returned as host arrays."""
+        Jn = J.numpy() if isinstance(J, torch.Tensor) else J
+        nn = n.numpy() if isinstance(n, torch.Tensor) else n
+        C, K = Jn.shape
+        if K != self.K or Jn.dtype != np.float32 or nn.dtype != np.float32 or nn.shape != (C, self.G):
+            raise ValueError("J [C,K] and n [C,G] must be float32 host arrays")
+        if Jn.strides[1] != 4 or not nn.flags.c_contiguous:
+            raise ValueError("J rows must be unit stride and n contiguous")
+        ld = Jn.strides[0] // 4
+        T = np.empty((C, self.G), np.float32) if T is None else T
+        if L is None:
+            Lb = np.empty((C, ld), np.float32)
+            L = Lb[:, :K]
+        else:
+            Lb = L
+        resid = np.empty(C, np.float64) if resid is None else resid
+        flags = np.empty((C, self.G), np.uint8) if flags is None else flags
+        _lib.dust_solve_host(self.handle, C, Jn.ctypes.data, ld, nn.ctypes.data, T.ctypes.data,
+                             Lb.ctypes.data, resid.ctypes.data, flags.ctypes.data)
+        return dict(T=T, L=L, resid=resid, flags=flags)

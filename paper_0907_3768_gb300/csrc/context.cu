@@ -1,0 +1,479 @@
+// Context creation: validation, the FP64 device build of the P_g(T) tables
+// and of every constant the solve kernels read.
+//
+// Per grain g (Eq. 7 with the quadrature of Eqs. 6-8):
+//   P_g(T)  = sum_k W[g,k] B_k(T),   W[g,k] = w_k C_abs[g,k]      (FP64)
+//   t_g(u)  = log2(P_g(2^u) / P_g(T_min)),  u = log2 T  on NT uniform nodes
+//   s_g(u)  = d log P / d log T = sum W B x / (1 - e^-x) / P
+// stored as FP32 Hermite intervals; the inverse u(t) on NI uniform nodes of t
+// seeds the device Newton iteration.  The paper solved Eq. 7 by Newton with a
+// quadrature per iteration (Section 4.3) and notes that production runs
+// interpolate a temperature table instead (Section 6); here the table is
+// built once per context in FP64 and every solve is a table lookup plus a
+// Newton step on its Hermite interpolant.
+//
+// Scaled operands:
+//   W32[g,k]  = W[g,k] / P_g(T_min) * 2^-f_g  (max_k W32 in (1/2, 1]), so that
+//   S[c,g]    = sum_k J[c,k] W32[g,k]  gives  A / P_g(T_min) = S 2^f_g.
+//   Chat[g,k] = 4 pi 2 h c^2 lambda_k^-5 C_abs[g,k] 2^-q_k  (max_g in (1/2, 1])
+// so that L[c,k] = 2^(m_c + q_k) sum_g n[c,g] 2^-m_c Chat[g,k] t/(1-t),
+// t = 2^(nax_k / T), nax_k = -log2(e) h c / (lambda_k k_B)  (Eqs. 8-10).
+#include "dust_internal.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace dust {
+
+namespace {
+
+constexpr double H_PL = 6.62607015e-34;
+constexpr double C_LI = 299792458.0;
+constexpr double K_BO = 1.380649e-23;
+constexpr double PI_D = 3.14159265358979323846;
+constexpr double LOG2E_D = 1.4426950408889634074;
+
+thread_local std::string g_err;
+
+// Per-wavelength FP64 constants: W = w C, Planck prefactor and x coefficient.
+__global__ void k_fold(int K, int G, const double *lam, const double *w, const double *C,
+                       double *W, double *pref, double *xc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < G * K) W[i] = w[i % K] * C[i];
+    if (i < K) {
+        double l = lam[i];
+        pref[i] = 2.0 * H_PL * C_LI * C_LI / (l * l * l * l * l);
+        xc[i] = H_PL * C_LI / (K_BO * l);
+    }
+}
+
+// log2 P_g(T_j) and d ln P / d ln T at T_j = 2^(log2Tmin + j h2), in FP64.
+__global__ void k_forward(int K, int G, int NT, double log2Tmin, double h2, const double *W,
+                          const double *pref, const double *xc, double *lp, double *sl) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= G * NT) return;
+    int g = i / NT, j = i % NT;
+    double T = exp2(log2Tmin + j * h2);
+    double P = 0.0, dP = 0.0;
+    const double *Wg = W + (size_t)g * K;
+    for (int k = 0; k < K; ++k) {
+        double x = xc[k] / T;
+        double e, den;
+        if (x > 0.5) { e = exp(-x); den = 1.0 - e; }
+        else { double em = expm1(-x); e = 1.0 + em; den = -em; }
+        double b = Wg[k] * pref[k] * e / den;
+        P += b;
+        dP += b * x / den;
+    }
+    lp[i] = log2(P);
+    sl[i] = dP / P;
+}
+
+// Per-grain scalars: P0, Pmax, the exponent f_g of W / P0 and the t range.
+__global__ void k_grain(int K, int G, int NT, int NI, const double *W, const double *lp,
+                        GrainParam *gp, double *gscale, double *P0, double *Pmax, int *bad) {
+    int g = blockIdx.x;
+    if (g >= G) return;
+    double l0 = lp[(size_t)g * NT], l1 = lp[(size_t)g * NT + NT - 1];
+    double p0 = exp2(l0);
+    double mx = 0.0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, W[(size_t)g * K + k] / p0);
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) {
+        if (!(p0 > 0.0) || !isfinite(l0) || !isfinite(l1) || !(mx > 0.0) || !isfinite(mx)) {
+            atomicExch(bad, g + 1);
+            return;
+        }
+        int f = (int)ceil(log2(mx));
+        GrainParam q;
+        q.f = (float)f;
+        q.tmax = (float)(l1 - l0);
+        q.invdy = (float)((NI - 1) / (l1 - l0));
+        q.pad = 0.f;
+        gp[g] = q;
+        gscale[g] = p0 * exp2((double)f);
+        P0[g] = p0;
+        Pmax[g] = exp2(l1);
+    }
+}
+
+// FP32 Hermite intervals of t_g(u) in units of the interval parameter.
+__global__ void k_fw32(int G, int NT, double h2, const double *lp, const double *sl, float4 *fw) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= G * (NT - 1)) return;
+    int g = i / (NT - 1), j = i % (NT - 1);
+    const double *l = lp + (size_t)g * NT;
+    const double *s = sl + (size_t)g * NT;
+    fw[i] = make_float4((float)(l[j] - l[0]), (float)(s[j] * h2), (float)(l[j + 1] - l[0]),
+                        (float)(s[j + 1] * h2));
+}
+
+// Hermite cubic on one interval: value and derivative in the interval parameter.
+__device__ void herm(double t0, double m0, double t1, double m1, double tau, double *p, double *dp) {
+    double d = t1 - t0;
+    double c2 = 3.0 * d - 2.0 * m0 - m1;
+    double c3 = m0 + m1 - 2.0 * d;
+    *p = t0 + tau * (m0 + tau * (c2 + tau * c3));
+    *dp = m0 + tau * (2.0 * c2 + 3.0 * tau * c3);
+}
+
+// Inverse table nodes: u(t_m) and du/dt at t_m = m dy, by bisection-guarded
+// Newton on the FP64 Hermite interpolant of t(u).
+__global__ void k_inverse(int G, int NT, int NI, double log2Tmin, double h2, const double *lp,
+                          const double *sl, double *iu, double *idu) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= G * NI) return;
+    int g = i / NI, m = i % NI;
+    const double *l = lp + (size_t)g * NT;
+    const double *s = sl + (size_t)g * NT;
+    double tmax = l[NT - 1] - l[0];
+    double y = (m == NI - 1) ? tmax : m * (tmax / (NI - 1));
+    int lo = 0, hi = NT - 1;  // find j with t_j <= y <= t_j+1
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (l[mid] - l[0] <= y) lo = mid; else hi = mid;
+    }
+    int j = lo;
+    double t0 = l[j] - l[0], t1 = l[j + 1] - l[0], m0 = s[j] * h2, m1 = s[j + 1] * h2;
+    double a = 0.0, b = 1.0;
+    double tau = (t1 > t0) ? (y - t0) / (t1 - t0) : 0.0;
+    double p, dp;
+    for (int it = 0; it < 60; ++it) {
+        herm(t0, m0, t1, m1, tau, &p, &dp);
+        if (p < y) a = tau; else b = tau;
+        double nt = tau - (p - y) / dp;
+        if (!(nt > a && nt < b)) nt = 0.5 * (a + b);
+        if (fabs(nt - tau) < 1e-15) { tau = nt; break; }
+        tau = nt;
+    }
+    herm(t0, m0, t1, m1, tau, &p, &dp);
+    iu[i] = log2Tmin + (j + tau) * h2;
+    idu[i] = h2 / dp;
+}
+
+__global__ void k_inv32(int G, int NI, double dy_unused, const double *iu, const double *idu,
+                        const GrainParam *gp, float4 *inv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= G * (NI - 1)) return;
+    int g = i / (NI - 1), m = i % (NI - 1);
+    size_t b = (size_t)g * NI + m;
+    double dy = (double)gp[g].tmax / (NI - 1);
+    inv[i] = make_float4((float)iu[b], (float)(idu[b] * dy), (float)iu[b + 1], (float)(idu[b + 1] * dy));
+}
+
+__global__ void k_tnode(int NT, double log2Tmin, double h2, float *Tnode) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < NT) Tnode[j] = (float)exp2(log2Tmin + j * h2);
+}
+
+// W32 [Gs][Kw] (zero padded) and the 16-bit hi/lo operand images of the
+// tensor-core kernel: per K chunk of KC columns, a hi block then a lo block
+// of Gs rows, each in the no-swizzle K-major core-matrix layout
+// (8 rows x 16 bytes per core matrix, LBO = 128 B along K, SBO = 512 B along rows).
+__global__ void k_w32(int K, int G, int Gs, int Kw, const double *W, const double *P0,
+                      const GrainParam *gp, float *W32, uint16_t *img_bf, uint16_t *img_h) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Gs * Kw) return;
+    int g = i / Kw, k = i % Kw;
+    float v = 0.f;
+    if (g < G && k < K) v = (float)(W[(size_t)g * K + k] / P0[g] * exp2(-(double)gp[g].f));
+    W32[i] = v;
+    __nv_bfloat16 bh = __float2bfloat16_rn(v);
+    __nv_bfloat16 bl = __float2bfloat16_rn(v - __bfloat162float(bh));
+    // FP16 image carries a 2^14 factor (max_k in (2^13, 2^14]) to keep small
+    // weights out of the FP16 subnormal range; the kernel divides it back out.
+    const float vh = v * 16384.0f;
+    __half hh = __float2half_rn(vh);
+    __half hl = __float2half_rn(vh - __half2float(hh));
+    int kc = k / KC, kk = k % KC;
+    size_t chunk = (size_t)kc * 2 * Gs * KC;  // elements
+    size_t off = (size_t)(g / 8) * (KC * 8) + (kk / 8) * 64 + (g % 8) * 8 + (kk % 8);
+    img_bf[chunk + off] = __bfloat16_as_ushort(bh);
+    img_bf[chunk + (size_t)Gs * KC + off] = __bfloat16_as_ushort(bl);
+    img_h[chunk + off] = __half_as_ushort(hh);
+    img_h[chunk + (size_t)Gs * KC + off] = __half_as_ushort(hl);
+}
+
+// Emission constants: q_k, Chat (split into two float4 halves per group of 8
+// wavelengths) and nax_k; padding wavelengths get Chat = 0 and nax = -1.
+__global__ void k_emis(int K, int G, int Kp, int NKG, const double *lam, const double *C,
+                       float *Chat, int *qexp, float *nax) {
+    int k = blockIdx.x;
+    if (k >= Kp) return;
+    double fac = 0.0;
+    double mx = 0.0;
+    if (k < K) {
+        double l = lam[k];
+        fac = 4.0 * PI_D * 2.0 * H_PL * C_LI * C_LI / (l * l * l * l * l);
+        for (int g = threadIdx.x; g < G; g += blockDim.x) mx = fmax(mx, fac * C[(size_t)g * K + k]);
+    }
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int q = (mx > 0.0) ? (int)ceil(log2(mx)) : 0;
+    int kg = k / 8, h = (k % 8) / 4, e = k % 4;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        float v = (k < K) ? (float)(fac * C[(size_t)g * K + k] * exp2(-(double)q)) : 0.f;
+        Chat[(((size_t)g * 2 + h) * NKG + kg) * 4 + e] = v;
+    }
+    if (threadIdx.x == 0) {
+        qexp[k] = q;
+        nax[k] = (k < K) ? (float)(-LOG2E_D * H_PL * C_LI / (lam[k] * K_BO)) : -1.0f;
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+int set_error(int code, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+const char *last_error_str() { return g_err.c_str(); }
+
+}  // namespace dust
+
+using namespace dust;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+int build_context(dust_ctx *ctx, const double *lambda, const double *w, const double *c_abs) {
+    const int K = ctx->K, G = ctx->G, NT = ctx->NT, NI = ctx->NI;
+    const int Gs = (G + GPAD - 1) / GPAD * GPAD;
+    const int NKG = (K + KQ - 1) / KQ;
+    const int Kp = NKG * KQ;
+    const int Kw = (K + KC - 1) / KC * KC;
+    ctx->Kw = Kw;
+    const double log2Tmin = std::log2(ctx->Tmin);
+    const double h2 = (std::log2(ctx->Tmax) - log2Tmin) / (NT - 1);
+
+    // temporaries (FP64)
+    DevBuf t_lam, t_w, t_C, t_W, t_pref, t_xc, t_lp, t_sl, t_iu, t_idu, t_bad;
+    DUST_CUDA_TRY(cudaMalloc(&t_lam.p, sizeof(double) * K));
+    DUST_CUDA_TRY(cudaMalloc(&t_w.p, sizeof(double) * K));
+    DUST_CUDA_TRY(cudaMalloc(&t_C.p, sizeof(double) * G * K));
+    DUST_CUDA_TRY(cudaMalloc(&t_W.p, sizeof(double) * G * K));
+    DUST_CUDA_TRY(cudaMalloc(&t_pref.p, sizeof(double) * K));
+    DUST_CUDA_TRY(cudaMalloc(&t_xc.p, sizeof(double) * K));
+    DUST_CUDA_TRY(cudaMalloc(&t_lp.p, sizeof(double) * G * NT));
+    DUST_CUDA_TRY(cudaMalloc(&t_sl.p, sizeof(double) * G * NT));
+    DUST_CUDA_TRY(cudaMalloc(&t_iu.p, sizeof(double) * G * NI));
+    DUST_CUDA_TRY(cudaMalloc(&t_idu.p, sizeof(double) * G * NI));
+    DUST_CUDA_TRY(cudaMalloc(&t_bad.p, sizeof(int)));
+    DUST_CUDA_TRY(cudaMemcpy(t_lam.p, lambda, sizeof(double) * K, cudaMemcpyHostToDevice));
+    DUST_CUDA_TRY(cudaMemcpy(t_w.p, w, sizeof(double) * K, cudaMemcpyHostToDevice));
+    DUST_CUDA_TRY(cudaMemcpy(t_C.p, c_abs, sizeof(double) * G * K, cudaMemcpyHostToDevice));
+    DUST_CUDA_TRY(cudaMemset(t_bad.p, 0, sizeof(int)));
+
+    // resident tables: one allocation, carved in 256-byte aligned pieces
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    size_t o_fw = take(sizeof(float4) * (size_t)G * (NT - 1));
+    size_t o_inv = take(sizeof(float4) * (size_t)G * (NI - 1));
+    size_t o_Tn = take(sizeof(float) * NT);
+    size_t o_gp = take(sizeof(GrainParam) * G);
+    size_t o_gs = take(sizeof(double) * G);
+    size_t o_P0 = take(sizeof(double) * G);
+    size_t o_Pm = take(sizeof(double) * G);
+    size_t o_nax = take(sizeof(float) * Kp);
+    size_t o_Ch = take(sizeof(float) * (size_t)G * Kp);
+    size_t o_q = take(sizeof(int) * Kp);
+    size_t o_w = take(sizeof(double) * K);
+    size_t o_st = take(sizeof(int));
+    DUST_CUDA_TRY(cudaMalloc(&ctx->tables_mem, off));
+    ctx->tables_bytes = off;
+    char *base = (char *)ctx->tables_mem;
+    DUST_CUDA_TRY(cudaMemset(base, 0, off));
+    DevTables &tb = ctx->tb;
+    tb.K = K; tb.G = G; tb.Kp = Kp; tb.NKG = NKG; tb.Gs = Gs; tb.NT = NT; tb.NI = NI;
+    tb.log2Tmin = (float)log2Tmin; tb.h2 = (float)h2;
+    tb.Tmin = (float)ctx->Tmin; tb.Tmax = (float)ctx->Tmax;
+    tb.fw = (const float4 *)(base + o_fw);
+    tb.inv = (const float4 *)(base + o_inv);
+    tb.Tnode = (const float *)(base + o_Tn);
+    tb.gp = (const GrainParam *)(base + o_gp);
+    tb.gscale = (const double *)(base + o_gs);
+    tb.P0 = (const double *)(base + o_P0);
+    tb.Pmax = (const double *)(base + o_Pm);
+    tb.nax = (const float *)(base + o_nax);
+    tb.Chat = (const float *)(base + o_Ch);
+    tb.qexp = (const int *)(base + o_q);
+    tb.w = (const double *)(base + o_w);
+    tb.status = (int *)(base + o_st);
+    DUST_CUDA_TRY(cudaMemcpy(base + o_w, w, sizeof(double) * K, cudaMemcpyHostToDevice));
+
+    DUST_CUDA_TRY(cudaMalloc(&ctx->W32, sizeof(float) * (size_t)Gs * Kw));
+    ctx->Wimg_bytes = sizeof(uint16_t) * 2 * (size_t)Gs * Kw;
+    DUST_CUDA_TRY(cudaMalloc(&ctx->Wimg[0], ctx->Wimg_bytes));
+    DUST_CUDA_TRY(cudaMalloc(&ctx->Wimg[1], ctx->Wimg_bytes));
+
+    const int B = 256;
+    auto blocks = [](size_t n) { return (unsigned)((n + 255) / 256); };
+    double *lam_d = (double *)t_lam.p, *W_d = (double *)t_W.p;
+    k_fold<<<blocks((size_t)G * K), B>>>(K, G, lam_d, (double *)t_w.p, (double *)t_C.p, W_d,
+                                         (double *)t_pref.p, (double *)t_xc.p);
+    k_forward<<<blocks((size_t)G * NT), B>>>(K, G, NT, log2Tmin, h2, W_d, (double *)t_pref.p,
+                                             (double *)t_xc.p, (double *)t_lp.p, (double *)t_sl.p);
+    k_grain<<<G, 32>>>(K, G, NT, NI, W_d, (double *)t_lp.p, (GrainParam *)(base + o_gp),
+                       (double *)(base + o_gs), (double *)(base + o_P0), (double *)(base + o_Pm),
+                       (int *)t_bad.p);
+    DUST_CUDA_TRY(cudaGetLastError());
+    int bad = 0;
+    DUST_CUDA_TRY(cudaMemcpy(&bad, t_bad.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad)
+        return set_error(DUST_EINVAL,
+                         "grain %d: P_g(T) is zero or not finite in FP64 over [T_min, T_max] "
+                         "(no absorption, or T_min too low for this wavelength grid)", bad - 1);
+    k_fw32<<<blocks((size_t)G * (NT - 1)), B>>>(G, NT, h2, (double *)t_lp.p, (double *)t_sl.p,
+                                                (float4 *)(base + o_fw));
+    k_inverse<<<blocks((size_t)G * NI), B>>>(G, NT, NI, log2Tmin, h2, (double *)t_lp.p,
+                                             (double *)t_sl.p, (double *)t_iu.p, (double *)t_idu.p);
+    k_inv32<<<blocks((size_t)G * (NI - 1)), B>>>(G, NI, 0.0, (double *)t_iu.p, (double *)t_idu.p,
+                                                 (const GrainParam *)(base + o_gp),
+                                                 (float4 *)(base + o_inv));
+    k_tnode<<<blocks(NT), B>>>(NT, log2Tmin, h2, (float *)(base + o_Tn));
+    k_w32<<<blocks((size_t)Gs * Kw), B>>>(K, G, Gs, Kw, W_d, (double *)(base + o_P0),
+                                          (const GrainParam *)(base + o_gp), ctx->W32,
+                                          ctx->Wimg[0], ctx->Wimg[1]);
+    k_emis<<<Kp, 32>>>(K, G, Kp, NKG, lam_d, (double *)t_C.p, (float *)(base + o_Ch),
+                       (int *)(base + o_q), (float *)(base + o_nax));
+    DUST_CUDA_TRY(cudaGetLastError());
+    DUST_CUDA_TRY(cudaDeviceSynchronize());
+    return DUST_OK;
+}
+
+void free_context(dust_ctx *ctx) {
+    if (!ctx) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(ctx->tables_mem);
+    cudaFree(ctx->W32);
+    cudaFree(ctx->Wimg[0]);
+    cudaFree(ctx->Wimg[1]);
+    cudaFree(ctx->S);
+    auto &hs = ctx->hs;
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(hs.J[i]); cudaFree(hs.n[i]); cudaFree(hs.T[i]); cudaFree(hs.L[i]);
+        cudaFree(hs.r[i]); cudaFree(hs.f[i]); cudaFree(hs.S[i]);
+        if (hs.st[i]) cudaStreamDestroy(hs.st[i]);
+        if (hs.ev[i]) cudaEventDestroy(hs.ev[i]);
+    }
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->prof_marks) cudaEventDestroy(e);
+    cudaSetDevice(prev);
+    delete ctx;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dust_last_error(void) { return dust::last_error_str(); }
+
+const char *dust_version(void) { return "libdust 0.1 (sm_103a)"; }
+
+int dust_ctx_create(dust_ctx **out, int K, const double *lambda, const double *w, int G,
+                    const double *c_abs, double T_min, double T_max, int n_table, int precision,
+                    int device) {
+    if (!out) return set_error(DUST_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!lambda || !w || !c_abs) return set_error(DUST_EINVAL, "lambda, w and c_abs must be non-NULL");
+    if (K < 2 || K > 8192) return set_error(DUST_EINVAL, "K=%d outside [2, 8192]", K);
+    if (G < 1 || G > 512) return set_error(DUST_EINVAL, "G=%d outside [1, 512]", G);
+    if (!(T_min > 0.0) || !(T_max > T_min) || !std::isfinite(T_max))
+        return set_error(DUST_EINVAL, "need 0 < T_min < T_max < inf");
+    if (n_table == 0) n_table = 4096;
+    if (n_table < 64 || n_table > 65536)
+        return set_error(DUST_EINVAL, "n_table=%d outside [64, 65536]", n_table);
+    if (precision < DUST_PREC_FP32 || precision > DUST_PREC_FP16X3)
+        return set_error(DUST_EINVAL, "unknown precision %d", precision);
+    for (int k = 0; k < K; ++k) {
+        if (!(lambda[k] > 0.0) || !std::isfinite(lambda[k]) || (k && !(lambda[k] > lambda[k - 1])))
+            return set_error(DUST_EINVAL, "lambda must be finite, positive and strictly increasing (k=%d)", k);
+        if (!(w[k] >= 0.0) || !std::isfinite(w[k]))
+            return set_error(DUST_EINVAL, "w[%d] must be finite and >= 0", k);
+    }
+    for (int g = 0; g < G; ++g) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) {
+            double c = c_abs[(size_t)g * K + k];
+            if (!(c >= 0.0) || !std::isfinite(c))
+                return set_error(DUST_EINVAL, "c_abs[%d,%d] must be finite and >= 0", g, k);
+            s += c * w[k];
+        }
+        if (!(s > 0.0)) return set_error(DUST_EINVAL, "grain %d absorbs nothing (sum_k w C = 0)", g);
+    }
+    double xmin = H_PL * C_LI / (K_BO * lambda[K - 1] * T_max);
+    if (xmin < 1e-3)
+        return set_error(DUST_EINVAL,
+                         "h c / (lambda_max k T_max) = %g < 1e-3: outside the emission kernel's range", xmin);
+    int ndev = 0;
+    DUST_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return set_error(DUST_EINVAL, "device %d of %d", device, ndev);
+    int prev = 0;
+    DUST_CUDA_TRY(cudaGetDevice(&prev));
+    DUST_CUDA_TRY(cudaSetDevice(device));
+    dust_ctx *ctx = new dust_ctx();
+    ctx->device = device;
+    ctx->precision = precision;
+    ctx->K = K; ctx->G = G; ctx->NT = n_table; ctx->NI = n_table;
+    ctx->Tmin = T_min; ctx->Tmax = T_max;
+    cudaDeviceProp prop;
+    int rc = DUST_OK;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        rc = set_error(DUST_ECUDA, "cudaGetDeviceProperties failed");
+    } else {
+        ctx->num_sms = prop.multiProcessorCount;
+        ctx->smem_optin = prop.sharedMemPerBlockOptin;
+        if (prop.major < 10)
+            rc = set_error(DUST_EINVAL, "device %d is sm_%d%d; libdust is built for sm_103a", device,
+                           prop.major, prop.minor);
+    }
+    if (rc == DUST_OK) rc = build_context(ctx, lambda, w, c_abs);
+    cudaSetDevice(prev);
+    if (rc != DUST_OK) { free_context(ctx); return rc; }
+    *out = ctx;
+    return DUST_OK;
+}
+
+void dust_ctx_destroy(dust_ctx *ctx) { free_context(ctx); }
+
+int dust_ctx_set_precision(dust_ctx *ctx, int precision) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    if (precision < DUST_PREC_FP32 || precision > DUST_PREC_FP16X3)
+        return set_error(DUST_EINVAL, "unknown precision %d", precision);
+    ctx->precision = precision;
+    return DUST_OK;
+}
+
+int dust_ctx_info(const dust_ctx *ctx, int *K, int *G, int *n_table, int *precision, int *device,
+                  size_t *device_bytes) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    if (K) *K = ctx->K;
+    if (G) *G = ctx->G;
+    if (n_table) *n_table = ctx->NT;
+    if (precision) *precision = ctx->precision;
+    if (device) *device = ctx->device;
+    if (device_bytes)
+        *device_bytes = ctx->tables_bytes + sizeof(float) * (size_t)ctx->tb.Gs * ctx->Kw +
+                        2 * ctx->Wimg_bytes + sizeof(float) * ctx->S_cap * ctx->tb.Gs;
+    return DUST_OK;
+}
+
+}  // extern "C"

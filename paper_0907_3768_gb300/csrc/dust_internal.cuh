@@ -1,0 +1,148 @@
+// Internal declarations shared by libdust's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <cstdio>
+#include <cstdarg>
+#include <string>
+#include <mutex>
+#include <vector>
+
+#include "../../include/dust.h"
+
+namespace dust {
+
+// Wavelengths handled by one thread in the emission phase (Eq. 10's sum over
+// grains is accumulated for KQ consecutive wavelengths per thread).
+constexpr int KQ = 8;
+// Grains folded into one rational accumulator N/D before its single division.
+constexpr int RG = 8;
+// Column padding of the scratch matrix of scaled absorbed powers.
+constexpr int GPAD = 16;
+// K-chunk (FP32 columns) of the tensor-core absorption kernel.
+constexpr int KC = 32;
+
+// Per-grain constants of the temperature solve (float4-packed for one load).
+struct GrainParam {
+    float f;      // exponent f_g: A / P_g(T_min) = S * 2^f_g
+    float tmax;   // t_max = log2(P_g(T_max) / P_g(T_min))
+    float invdy;  // (NI - 1) / tmax: inverse-table bins per unit of log2 P
+    float pad;
+};
+
+// Everything the device kernels read from a context, passed by value.
+struct DevTables {
+    int K, G, Kp, NKG;        // Kp = NKG * KQ >= K (emission padding)
+    int Gs;                   // row stride of the absorbed-power scratch (G rounded to GPAD)
+    int NT, NI;               // forward / inverse table sizes
+    float log2Tmin, h2;       // u_j = log2Tmin + j h2 (u = log2 T)
+    float Tmin, Tmax;
+    const float4 *fw;         // [G][NT-1] (t_j, s_j h2, t_j+1, s_j+1 h2), t = log2(P/P0)
+    const float4 *inv;        // [G][NI-1] (u_m, u'_m dy, u_m+1, u'_m+1 dy)
+    const float *Tnode;       // [NT] 2^u_j
+    const GrainParam *gp;     // [G]
+    const double *gscale;     // [G] A = S * gscale (= P0 2^f)
+    const double *P0;         // [G] P_g(T_min)
+    const double *Pmax;       // [G] P_g(T_max)
+    const float *nax;         // [Kp] -log2(e) h c / (lambda_k k_B), 0 in the padding
+    const float *Chat;        // [G][2][NKG][4] scaled emission weights (see context.cu)
+    const int *qexp;          // [Kp] per-wavelength exponent of Chat
+    const double *w;          // [K] quadrature weights (residual)
+    int *status;              // device status word (dust_status)
+};
+
+}  // namespace dust
+
+// The opaque context of the C ABI.
+struct dust_ctx {
+    int device = 0;
+    int precision = DUST_PREC_FP32;
+    int K = 0, G = 0, NT = 0, NI = 0;
+    int Kw = 0;               // row length of the FP32 / 16-bit W copies (K rounded to KC)
+    double Tmin = 0, Tmax = 0;
+    dust::DevTables tb{};
+    // device allocations owned by the context
+    float *W32 = nullptr;     // [Gs][Kw] FP32 scaled W (SIMT path)
+    uint16_t *Wimg[2] = {nullptr, nullptr};  // BF16 / FP16 hi+lo images (tensor-core path)
+    size_t Wimg_bytes = 0;
+    void *tables_mem = nullptr;  // one block holding every table
+    size_t tables_bytes = 0;
+    // scratch of scaled absorbed powers S[C][Gs]
+    float *S = nullptr;
+    size_t S_cap = 0;         // in cells
+    // host-staging for dust_solve_host
+    struct HostStage {
+        cudaStream_t st[2] = {nullptr, nullptr};
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        float *J[2] = {nullptr, nullptr}, *n[2] = {nullptr, nullptr};
+        float *T[2] = {nullptr, nullptr}, *L[2] = {nullptr, nullptr};
+        double *r[2] = {nullptr, nullptr};
+        uint8_t *f[2] = {nullptr, nullptr};
+        float *S[2] = {nullptr, nullptr};
+        int64_t cap = 0, ld = 0;
+    } hs;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    std::mutex mu;
+    // per-kernel event timing (dust_ctx_profile): three events per solve
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_pool;   // reusable events
+    std::vector<cudaEvent_t> prof_marks;  // recorded, not yet read (triples)
+};
+
+namespace dust {
+
+// Thread-local error reporting.
+int set_error(int code, const char *fmt, ...);
+const char *cuda_err_name(cudaError_t e);
+
+#define DUST_CUDA_TRY(expr)                                                          \
+    do {                                                                             \
+        cudaError_t _e = (expr);                                                     \
+        if (_e != cudaSuccess)                                                       \
+            return ::dust::set_error(_e == cudaErrorMemoryAllocation ? DUST_ENOMEM     \
+                                                                    : DUST_ECUDA,    \
+                                     "%s failed: %s (%s:%d)", #expr,                 \
+                                     cudaGetErrorString(_e), __FILE__, __LINE__);    \
+    } while (0)
+
+// Kernels' entry points (host launchers), each returning a dust_status.
+int launch_gemm_simt(const dust_ctx *ctx, int64_t C, const float *J, int64_t ld, float *S,
+                     cudaStream_t st);
+int launch_gemm_tc(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld,
+                   float *S, cudaStream_t st);
+int launch_solve_emit(const dust_ctx *ctx, int64_t C, const float *S, const float *n, float *T,
+                      float *L, int64_t ld, double *resid, uint8_t *flags, cudaStream_t st);
+
+// Grow the context's scratch to hold `cells` rows (synchronises `st` first).
+int ensure_scratch(dust_ctx *ctx, int64_t cells, cudaStream_t st);
+
+// The whole path on device buffers with scratch S of at least C x Gs floats.
+int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld,
+                 const float *n, float *T, float *L, double *resid, uint8_t *flags, float *S,
+                 cudaStream_t st);
+
+// Bounded spin budget for device-side waits: a wait that exceeds it records
+// DUST_ETIMEOUT in the status word and gives up.
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void record_status(int *status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+// x * 2^e for |e| <= 252 without leaving the exact power-of-two scaling
+// (two steps so that each factor is a normal float).
+__device__ __forceinline__ float scale2(float x, int e) {
+    int e1 = e / 2, e2 = e - e1;
+    return x * __int_as_float((e1 + 127) << 23) * __int_as_float((e2 + 127) << 23);
+}
+
+}  // namespace dust

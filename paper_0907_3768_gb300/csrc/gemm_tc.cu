@@ -1,0 +1,459 @@
+// Kernel (a): the absorption contraction of Eq. 6 on the 5th-generation
+// tensor cores, S[c,g] = sum_k J[c,k] W32[g,k], with 16-bit operands split
+// into hi + lo parts (three products hi.hi + lo.hi + hi.lo, FP32 accumulation
+// in tensor memory).  The paper's kernel 2 (Section 4.2) is the same matrix
+// product on CUDA cores in FP32.
+//
+// One persistent CTA per SM walks 128-cell tiles.  Warp roles:
+//   warp 0      TMA producer: FP32 tiles of J (128 cells x 32 wavelengths,
+//               128-byte swizzle) into a ring of staging buffers, and the
+//               pre-split 16-bit W chunk images (bulk copies) next to the
+//               converted A operand.
+//   warp 1      owns the TMEM accumulator (128 lanes x Gs columns FP32) and
+//               issues tcgen05.mma from one thread.
+//   warps 2-5   one thread per cell row: per-cell power-of-two exponent of
+//               max_k J[c,k] (first pass over the tile, FP16 only: J spans
+//               ~8 decades), conversion of J 2^-e into hi/lo 16-bit values
+//               in the K-major core-matrix layout (second pass), then the
+//               epilogue: TMEM -> registers -> S = acc 2^(e - offsets).
+// Every mbarrier wait is bounded; on expiry the kernel records
+// DUST_ETIMEOUT in the context's status word and winds down.
+#include "dust_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+namespace dust {
+namespace {
+
+constexpr int BM = 128;               // cells per tile (UMMA M)
+constexpr int NTHREADS = 192;
+constexpr int STAGE1_BYTES = BM * KC * 4;  // FP32 staging tile: 16 KB
+constexpr int A_BYTES = BM * KC * 2;       // one 16-bit A part: 8 KB
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          int *status) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer_ns() - t0 > WAIT_NS) {
+                *abort_flag = 1;
+                record_status(status, DUST_ETIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+// Bounded wait that ignores the abort flag (used to drain asynchronous work
+// before shared memory or tensor memory is released).
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity, int *status) {
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try(bar, parity)) {
+        if (globaltimer_ns() - t0 > WAIT_NS) { record_status(status, DUST_ETIMEOUT); return; }
+    }
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16, FP32 accumulation.
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// 32 lanes x 32 bits, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of
+// 8 rows x 16 bytes; LBO = byte step between core matrices along K,
+// SBO = byte step between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor cores
+    return d;                // base offset 0, absolute LBO mode, no swizzle
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, K-major A and B.
+__host__ __device__ constexpr uint32_t instr_desc(bool bf16, int M, int N) {
+    return (1u << 4)                       // D format: F32
+           | ((bf16 ? 1u : 0u) << 7)       // A format: BF16 = 1, F16 = 0
+           | ((bf16 ? 1u : 0u) << 10)      // B format
+           | ((uint32_t)(N >> 3) << 17)    // N / 8
+           | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+__device__ __forceinline__ uint32_t pack_split(float x0, float x1, bool bf16, uint32_t &lo) {
+    uint32_t hi;
+    if (bf16) {
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
+        float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(x1 - h1), "f"(x0 - h0));
+    } else {
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
+        __half2 h2 = *reinterpret_cast<__half2 *>(&hi);
+        float2 hf = __half22float2(h2);
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(x1 - hf.y), "f"(x0 - hf.x));
+    }
+    return hi;
+}
+
+struct TcParams {
+    int64_t C;
+    int K, Gs, nkc;         // nkc = K chunks of KC wavelengths
+    int ns1, ns2;           // ring depths
+    int tmem_cols;
+    int off_exp;            // J and W scale offsets folded into the epilogue exponent
+    int j_off;              // J is scaled to [2^(j_off-1), 2^j_off) per cell
+    const uint16_t *Wimg;   // [nkc][2][Gs x KC] 16-bit images
+    float *S;
+    int *status;
+};
+
+template <bool BF16, bool TWO_PASS>
+__global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__ CUtensorMap tmJ, TcParams p) {
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+    const int B_BYTES = p.Gs * KC * 2 * 2;  // hi + lo W chunk
+    unsigned char *st1 = smem;
+    unsigned char *stA = st1 + (size_t)p.ns1 * STAGE1_BYTES;
+    unsigned char *stB = stA + (size_t)p.ns2 * 2 * A_BYTES;
+    uint64_t *bars = (uint64_t *)(stB + (size_t)p.ns2 * B_BYTES);
+    uint64_t *full1 = bars, *empty1 = full1 + p.ns1;
+    uint64_t *a_full = empty1 + p.ns1, *a_empty = a_full + p.ns2, *b_full = a_empty + p.ns2;
+    uint64_t *acc_full = b_full + p.ns2, *acc_empty = acc_full + 1, *drain = acc_empty + 1;
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = (p.C + BM - 1) / BM;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < p.ns1; ++s) { mbar_init(&full1[s], 1); mbar_init(&empty1[s], 4); }
+        for (int s = 0; s < p.ns2; ++s) { mbar_init(&a_full[s], 4); mbar_init(&a_empty[s], 1); mbar_init(&b_full[s], 1); }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 4);
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(p.tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int s1 = 0, sa = 0;
+            uint32_t ph1 = 0, pha = 0;
+            int64_t n1 = 0, n2 = 0;  // copies issued into each ring
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int row0 = (int)(tile * BM);
+                for (int pass = TWO_PASS ? 0 : 1; pass < 2 && ok; ++pass) {
+                    for (int kc = 0; kc < p.nkc && ok; ++kc) {
+                        if (!(ok = mbar_wait(&empty1[s1], ph1 ^ 1, abort_flag, p.status))) break;
+                        mbar_expect_tx(&full1[s1], STAGE1_BYTES);
+                        tma_load_2d(st1 + (size_t)s1 * STAGE1_BYTES, &tmJ, kc * KC, row0, &full1[s1]);
+                        ++n1;
+                        if (++s1 == p.ns1) { s1 = 0; ph1 ^= 1; }
+                        if (pass == 1) {
+                            if (!(ok = mbar_wait(&a_empty[sa], pha ^ 1, abort_flag, p.status))) break;
+                            mbar_expect_tx(&b_full[sa], B_BYTES);
+                            bulk_load(stB + (size_t)sa * B_BYTES, p.Wimg + (size_t)kc * (B_BYTES / 2), B_BYTES,
+                                      &b_full[sa]);
+                            ++n2;
+                            if (++sa == p.ns2) { sa = 0; pha ^= 1; }
+                        }
+                    }
+                }
+            }
+            if (!ok) {
+                // after an abort, let the copies already issued land before the CTA exits
+                for (int s = 0; s < p.ns1; ++s) {
+                    int64_t last = n1 - 1 - ((n1 - 1 - s) % p.ns1 + p.ns1) % p.ns1;
+                    if (last >= 0 && last % p.ns1 == s) mbar_drain(&full1[s], (uint32_t)((last / p.ns1) & 1), p.status);
+                }
+                for (int s = 0; s < p.ns2; ++s) {
+                    int64_t last = n2 - 1 - ((n2 - 1 - s) % p.ns2 + p.ns2) % p.ns2;
+                    if (last >= 0 && last % p.ns2 == s) mbar_drain(&b_full[s], (uint32_t)((last / p.ns2) & 1), p.status);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc_full = instr_desc(BF16, BM, p.Gs <= 256 ? p.Gs : 256);
+            const uint32_t idesc_tail = instr_desc(BF16, BM, p.Gs > 256 ? p.Gs - 256 : 16);
+            int sa = 0;
+            uint32_t pha = 0, phacc = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                if (!(ok = mbar_wait(acc_empty, phacc ^ 1, abort_flag, p.status))) break;
+                tc_fence_after();
+                for (int kc = 0; kc < p.nkc && ok; ++kc) {
+                    if (!(ok = mbar_wait(&a_full[sa], pha, abort_flag, p.status))) break;
+                    if (!(ok = mbar_wait(&b_full[sa], pha, abort_flag, p.status))) break;
+                    tc_fence_after();
+                    const uint32_t a_base = smem_u32(stA + (size_t)sa * 2 * A_BYTES);
+                    const uint32_t b_base = smem_u32(stB + (size_t)sa * B_BYTES);
+#pragma unroll
+                    for (int ks = 0; ks < KC / 16; ++ks) {
+#pragma unroll
+                        for (int part = 0; part < 3; ++part) {
+                            // hi.hi, lo.hi, hi.lo
+                            const uint32_t aoff = (part == 1 ? A_BYTES : 0) + ks * 256;
+                            const uint32_t boff = (part == 2 ? p.Gs * KC * 2 : 0) + ks * 256;
+                            const uint32_t acc = (kc | ks | part) ? 1u : 0u;
+                            tc_mma(tmem, smem_desc(a_base + aoff, 128, 512), smem_desc(b_base + boff, 128, 512),
+                                   idesc_full, acc);
+                            if (p.Gs > 256)
+                                tc_mma(tmem + 256, smem_desc(a_base + aoff, 128, 512),
+                                       smem_desc(b_base + boff + 32 * 512, 128, 512), idesc_tail, acc);
+                        }
+                    }
+                    tc_commit(&a_empty[sa]);
+                    if (++sa == p.ns2) { sa = 0; pha ^= 1; }
+                }
+                if (ok) tc_commit(acc_full);
+                phacc ^= 1;
+            }
+            // drain every MMA still in flight before the accumulator is freed
+            tc_commit(drain);
+            mbar_drain(drain, 0, p.status);
+        }
+    } else {
+        // ------------------------------------------------------------ converters + epilogue
+        const int quad = warp & 3;           // TMEM lane quarter this warp may access
+        const int r = quad * 32 + lane;      // tile row owned by this thread
+        int s1 = 0, sa = 0;
+        uint32_t ph1 = 0, pha = 0, phacc = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            int e = 0;
+            if (TWO_PASS) {
+                float mx = 0.f;
+                for (int kc = 0; kc < p.nkc; ++kc) {
+                    if (!(ok = mbar_wait(&full1[s1], ph1, abort_flag, p.status))) break;
+                    const unsigned char *src = st1 + (size_t)s1 * STAGE1_BYTES + r * 128;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float4 v = *reinterpret_cast<const float4 *>(src + ((j ^ (r & 7)) << 4));
+                        mx = fmaxf(mx, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty1[s1]);
+                    if (++s1 == p.ns1) { s1 = 0; ph1 ^= 1; }
+                }
+                if (!ok) break;
+                if (mx > 0.f && mx < INFINITY) frexpf(mx, &e);
+                e = min(max(e, p.j_off - 126), p.j_off + 126);  // keep 2^(j_off - e) a normal float
+            }
+            const float scale = __int_as_float((127 - e + p.j_off) << 23);  // 2^(j_off - e)
+            for (int kc = 0; kc < p.nkc; ++kc) {
+                if (!(ok = mbar_wait(&full1[s1], ph1, abort_flag, p.status))) break;
+                if (!(ok = mbar_wait(&a_empty[sa], pha ^ 1, abort_flag, p.status))) break;
+                const unsigned char *src = st1 + (size_t)s1 * STAGE1_BYTES + r * 128;
+                unsigned char *dhi = stA + (size_t)sa * 2 * A_BYTES + (r >> 3) * 512 + (r & 7) * 16;
+                unsigned char *dlo = dhi + A_BYTES;
+#pragma unroll
+                for (int cm = 0; cm < 4; ++cm) {  // 8 wavelengths = one core-matrix row
+                    float4 v0 = *reinterpret_cast<const float4 *>(src + (((2 * cm) ^ (r & 7)) << 4));
+                    float4 v1 = *reinterpret_cast<const float4 *>(src + (((2 * cm + 1) ^ (r & 7)) << 4));
+                    uint4 h, l;
+                    h.x = pack_split(v0.x * scale, v0.y * scale, BF16, l.x);
+                    h.y = pack_split(v0.z * scale, v0.w * scale, BF16, l.y);
+                    h.z = pack_split(v1.x * scale, v1.y * scale, BF16, l.z);
+                    h.w = pack_split(v1.z * scale, v1.w * scale, BF16, l.w);
+                    *reinterpret_cast<uint4 *>(dhi + cm * 128) = h;
+                    *reinterpret_cast<uint4 *>(dlo + cm * 128) = l;
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) { mbar_arrive(&a_full[sa]); mbar_arrive(&empty1[s1]); }
+                if (++s1 == p.ns1) { s1 = 0; ph1 ^= 1; }
+                if (++sa == p.ns2) { sa = 0; pha ^= 1; }
+            }
+            if (!ok) break;
+            // epilogue
+            if (!(ok = mbar_wait(acc_full, phacc, abort_flag, p.status))) break;
+            phacc ^= 1;
+            tc_fence_after();
+            const int64_t row = tile * BM + r;
+            const int ex = e - p.j_off - p.off_exp;
+            float *dst = p.S + row * p.Gs;
+            for (int c0 = 0; c0 < p.Gs; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + c0, v);
+                if (row < p.C) {
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4)
+                        *reinterpret_cast<float4 *>(dst + c0 + i) =
+                            make_float4(scale2(v[i], ex), scale2(v[i + 1], ex), scale2(v[i + 2], ex),
+                                        scale2(v[i + 3], ex));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+    }
+    return fn;
+}
+
+template <bool BF16, bool TWO_PASS>
+int launch_t(const dust_ctx *ctx, const CUtensorMap &tm, const TcParams &p, size_t smem, int grid,
+             cudaStream_t st) {
+    auto kern = k_gemm_tc<BF16, TWO_PASS>;
+    DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, NTHREADS, smem, st>>>(tm, p);
+    DUST_CUDA_TRY(cudaGetLastError());
+    return DUST_OK;
+}
+
+}  // namespace
+
+int launch_gemm_tc(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, float *S,
+                   cudaStream_t st) {
+    if (C <= 0) return DUST_OK;
+    const bool bf16 = precision == DUST_PREC_BF16X3;
+    const int Gs = ctx->tb.Gs, K = ctx->K;
+    if (C > 0x7fffffffLL - BM) return set_error(DUST_EINVAL, "too many cells for one tensor-core launch");
+    auto encode = get_encode();
+    if (!encode) return set_error(DUST_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    CUtensorMap tm;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)C};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult cr = encode(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)J, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return set_error(DUST_EINVAL, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+
+    TcParams p{};
+    p.C = C;
+    p.K = K;
+    p.Gs = Gs;
+    p.nkc = (K + KC - 1) / KC;
+    int cols = 32;
+    while (cols < Gs) cols <<= 1;
+    p.tmem_cols = cols;
+    // FP16 keeps J in [2^14, 2^15) and W in (2^13, 2^14] (the W image is
+    // built with 2^14 folded in); BF16 has FP32's exponent range and needs none.
+    p.j_off = bf16 ? 0 : 15;
+    p.off_exp = bf16 ? 0 : 14;
+    p.Wimg = ctx->Wimg[bf16 ? 0 : 1];
+    p.S = S;
+    p.status = ctx->tb.status;
+    const size_t b_bytes = (size_t)Gs * KC * 4;
+    const size_t budget = (ctx->smem_optin ? ctx->smem_optin : 232448) - 1024 - 256;
+    int ns2 = 4, ns1 = 6;
+    auto need = [&](int a, int b) { return (size_t)a * STAGE1_BYTES + (size_t)b * (2 * A_BYTES + b_bytes) + 256; };
+    while (need(ns1, ns2) > budget && ns1 > 3) --ns1;
+    while (need(ns1, ns2) > budget && ns2 > 2) --ns2;
+    while (need(ns1, ns2) > budget && ns1 > 2) --ns1;
+    if (need(ns1, ns2) > budget) return set_error(DUST_EINVAL, "G too large for the tensor-core kernel");
+    p.ns1 = ns1;
+    p.ns2 = ns2;
+    const size_t smem = need(ns1, ns2) + 1024;
+    const int64_t ntiles = (C + BM - 1) / BM;
+    const int grid = (int)std::min<int64_t>(ntiles, ctx->num_sms);
+    // BF16: the per-cell power-of-two scale is exact and leaves every product
+    // unchanged, so the exponent pass runs only for FP16.
+    if (bf16) return launch_t<true, false>(ctx, tm, p, smem, grid, st);
+    return launch_t<false, true>(ctx, tm, p, smem, grid, st);
+}
+
+}  // namespace dust

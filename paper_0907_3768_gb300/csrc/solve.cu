@@ -1,0 +1,246 @@
+// dust_solve and friends: argument checks, scratch management and the launch
+// sequence of the hot path (absorption contraction -> fused solve/emission).
+#include "dust_internal.cuh"
+
+#include <algorithm>
+
+namespace dust {
+namespace {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    int rc = DUST_OK;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { rc = set_error(DUST_ECUDA, "cudaGetDevice failed"); return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess)
+            rc = set_error(DUST_ECUDA, "cudaSetDevice(%d) failed", dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int check_device_ptr(const void *p, int device, const char *name) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(DUST_EINVAL, "%s: not a CUDA pointer", name);
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return set_error(DUST_EINVAL, "%s must be device memory", name);
+    if (a.type == cudaMemoryTypeDevice && a.device != device)
+        return set_error(DUST_EINVAL, "%s lives on device %d, the context on device %d", name, a.device,
+                         device);
+    return DUST_OK;
+}
+
+int validate(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, const float *n,
+             float *T, float *L, double *resid, uint8_t *flags, bool device_ptrs) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    if (C < 0) return set_error(DUST_EINVAL, "n_cells < 0");
+    if (precision < DUST_PREC_FP32 || precision > DUST_PREC_FP16X3)
+        return set_error(DUST_EINVAL, "unknown precision %d", precision);
+    if (ld < ctx->K) return set_error(DUST_EINVAL, "ld=%lld < K=%d", (long long)ld, ctx->K);
+    if (C == 0) return DUST_OK;
+    if (!J || !n || !T) return set_error(DUST_EINVAL, "J, n and T must be non-NULL");
+    if (precision != DUST_PREC_FP32) {
+        if (ld % 4 != 0 || ((uintptr_t)J & 15) != 0)
+            return set_error(DUST_EINVAL,
+                             "tensor-core precisions need ld %% 4 == 0 and a 16-byte aligned J "
+                             "(ld=%lld)", (long long)ld);
+    }
+    if (device_ptrs) {
+        int rc;
+        if ((rc = check_device_ptr(J, ctx->device, "J")) != DUST_OK) return rc;
+        if ((rc = check_device_ptr(n, ctx->device, "n")) != DUST_OK) return rc;
+        if ((rc = check_device_ptr(T, ctx->device, "T")) != DUST_OK) return rc;
+        if (L && (rc = check_device_ptr(L, ctx->device, "L")) != DUST_OK) return rc;
+        if (resid && (rc = check_device_ptr(resid, ctx->device, "resid")) != DUST_OK) return rc;
+        if (flags && (rc = check_device_ptr(flags, ctx->device, "flags")) != DUST_OK) return rc;
+    }
+    return DUST_OK;
+}
+
+}  // namespace
+
+int ensure_scratch(dust_ctx *ctx, int64_t cells, cudaStream_t st) {
+    if ((size_t)cells <= ctx->S_cap) return DUST_OK;
+    DUST_CUDA_TRY(cudaStreamSynchronize(st));
+    if (ctx->S) { cudaFree(ctx->S); ctx->S = nullptr; ctx->S_cap = 0; }
+    DUST_CUDA_TRY(cudaMalloc(&ctx->S, sizeof(float) * (size_t)cells * ctx->tb.Gs));
+    ctx->S_cap = (size_t)cells;
+    return DUST_OK;
+}
+
+namespace {
+cudaEvent_t prof_event(dust_ctx *ctx) {
+    cudaEvent_t e = nullptr;
+    if (!ctx->prof_pool.empty()) {
+        e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return nullptr;
+    }
+    return e;
+}
+}  // namespace
+
+int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, const float *n,
+                 float *T, float *L, double *resid, uint8_t *flags, float *S, cudaStream_t st) {
+    if (C == 0) return DUST_OK;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    if (ctx->prof_on)
+        for (int i = 0; i < 3; ++i) ev[i] = prof_event(ctx);
+    const bool prof = ev[0] && ev[1] && ev[2];
+    if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[0], st));
+    int rc = precision == DUST_PREC_FP32 ? launch_gemm_simt(ctx, C, J, ld, S, st)
+                                         : launch_gemm_tc(ctx, precision, C, J, ld, S, st);
+    if (rc == DUST_OK) {
+        if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[1], st));
+        rc = launch_solve_emit(ctx, C, S, n, T, L, ld, resid, flags, st);
+        if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[2], st));
+    }
+    for (int i = 0; i < 3; ++i) {
+        if (!ev[i]) continue;
+        if (prof && rc == DUST_OK) ctx->prof_marks.push_back(ev[i]);
+        else ctx->prof_pool.push_back(ev[i]);
+    }
+    return rc;
+}
+
+}  // namespace dust
+
+using namespace dust;
+
+extern "C" {
+
+int dust_solve_prec(dust_ctx *ctx, int precision, int64_t n_cells, const float *J, int64_t ld,
+                    const float *n, float *T, float *L, double *resid, uint8_t *flags, void *stream) {
+    int rc = validate(ctx, precision, n_cells, J, ld, n, T, L, resid, flags, true);
+    if (rc != DUST_OK || n_cells == 0) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    if (dg.rc != DUST_OK) return dg.rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ensure_scratch(ctx, n_cells, st)) != DUST_OK) return rc;
+    return solve_device(ctx, precision, n_cells, J, ld, n, T, L, resid, flags, ctx->S, st);
+}
+
+int dust_solve(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n, float *T,
+               float *L, double *resid, uint8_t *flags, void *stream) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    return dust_solve_prec(ctx, ctx->precision, n_cells, J, ld, n, T, L, resid, flags, stream);
+}
+
+int dust_solve_host(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n, float *T,
+                    float *L, double *resid, uint8_t *flags) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    const int precision = ctx->precision;
+    int rc = validate(ctx, DUST_PREC_FP32, n_cells, J, ld, n, T, L, resid, flags, false);
+    if (rc != DUST_OK || n_cells == 0) return rc;
+    if (precision != DUST_PREC_FP32 && ld % 4 != 0)
+        return set_error(DUST_EINVAL, "tensor-core precisions need ld %% 4 == 0");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    if (dg.rc != DUST_OK) return dg.rc;
+    const int G = ctx->G, Gs = ctx->tb.Gs;
+    // chunks of at least 8192 cells, about 8 of them for large batches
+    int64_t chunk = std::max<int64_t>(8192, (n_cells + 7) / 8);
+    chunk = (chunk + 127) / 128 * 128;
+    chunk = std::min<int64_t>(chunk, n_cells);
+    auto &hs = ctx->hs;
+    if (hs.cap < chunk || hs.ld != ld) {
+        for (int i = 0; i < 2; ++i) {
+            cudaFree(hs.J[i]); cudaFree(hs.n[i]); cudaFree(hs.T[i]); cudaFree(hs.L[i]);
+            cudaFree(hs.r[i]); cudaFree(hs.f[i]); cudaFree(hs.S[i]);
+            hs.J[i] = hs.n[i] = hs.T[i] = hs.L[i] = hs.S[i] = nullptr;
+            hs.r[i] = nullptr; hs.f[i] = nullptr;
+        }
+        hs.cap = 0;
+        for (int i = 0; i < 2; ++i) {
+            if (!hs.st[i]) DUST_CUDA_TRY(cudaStreamCreateWithFlags(&hs.st[i], cudaStreamNonBlocking));
+            DUST_CUDA_TRY(cudaMalloc(&hs.J[i], sizeof(float) * chunk * ld));
+            DUST_CUDA_TRY(cudaMalloc(&hs.n[i], sizeof(float) * chunk * G));
+            DUST_CUDA_TRY(cudaMalloc(&hs.T[i], sizeof(float) * chunk * G));
+            DUST_CUDA_TRY(cudaMalloc(&hs.L[i], sizeof(float) * chunk * ld));
+            DUST_CUDA_TRY(cudaMalloc(&hs.r[i], sizeof(double) * chunk));
+            DUST_CUDA_TRY(cudaMalloc(&hs.f[i], sizeof(uint8_t) * chunk * G));
+            DUST_CUDA_TRY(cudaMalloc(&hs.S[i], sizeof(float) * chunk * Gs));
+        }
+        hs.cap = chunk;
+        hs.ld = ld;
+    }
+    int64_t i = 0;
+    for (int64_t c0 = 0; c0 < n_cells; c0 += chunk, ++i) {
+        const int s = (int)(i & 1);
+        const int64_t cn = std::min<int64_t>(chunk, n_cells - c0);
+        cudaStream_t st = hs.st[s];
+        DUST_CUDA_TRY(cudaMemcpyAsync(hs.J[s], J + c0 * ld, sizeof(float) * cn * ld, cudaMemcpyHostToDevice, st));
+        DUST_CUDA_TRY(cudaMemcpyAsync(hs.n[s], n + c0 * G, sizeof(float) * cn * G, cudaMemcpyHostToDevice, st));
+        rc = solve_device(ctx, precision, cn, hs.J[s], ld, hs.n[s], hs.T[s], L ? hs.L[s] : nullptr,
+                          resid ? hs.r[s] : nullptr, flags ? hs.f[s] : nullptr, hs.S[s], st);
+        if (rc != DUST_OK) { cudaStreamSynchronize(hs.st[0]); cudaStreamSynchronize(hs.st[1]); return rc; }
+        DUST_CUDA_TRY(cudaMemcpyAsync(T + c0 * G, hs.T[s], sizeof(float) * cn * G, cudaMemcpyDeviceToHost, st));
+        if (L)
+            DUST_CUDA_TRY(cudaMemcpyAsync(L + c0 * ld, hs.L[s], sizeof(float) * cn * ld, cudaMemcpyDeviceToHost, st));
+        if (resid)
+            DUST_CUDA_TRY(cudaMemcpyAsync(resid + c0, hs.r[s], sizeof(double) * cn, cudaMemcpyDeviceToHost, st));
+        if (flags)
+            DUST_CUDA_TRY(cudaMemcpyAsync(flags + c0 * G, hs.f[s], cn * G, cudaMemcpyDeviceToHost, st));
+    }
+    DUST_CUDA_TRY(cudaStreamSynchronize(hs.st[0]));
+    DUST_CUDA_TRY(cudaStreamSynchronize(hs.st[1]));
+    return DUST_OK;
+}
+
+int dust_ctx_profile(dust_ctx *ctx, int enable) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->prof_on = enable != 0;
+    return DUST_OK;
+}
+
+int dust_ctx_profile_read(dust_ctx *ctx, double *ms_absorb, double *ms_solve_emit, int64_t *n_solves) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    if (dg.rc != DUST_OK) return dg.rc;
+    double a = 0.0, b = 0.0;
+    int64_t cnt = 0;
+    int rc = DUST_OK;
+    for (size_t i = 0; i + 2 < ctx->prof_marks.size(); i += 3) {
+        cudaEvent_t *e = &ctx->prof_marks[i];
+        float t01 = 0.f, t12 = 0.f;
+        if (cudaEventSynchronize(e[2]) != cudaSuccess || cudaEventElapsedTime(&t01, e[0], e[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t12, e[1], e[2]) != cudaSuccess) {
+            rc = set_error(DUST_ECUDA, "profiling events could not be read");
+            break;
+        }
+        a += t01;
+        b += t12;
+        ++cnt;
+    }
+    for (cudaEvent_t e : ctx->prof_marks) ctx->prof_pool.push_back(e);
+    ctx->prof_marks.clear();
+    if (ms_absorb) *ms_absorb = a;
+    if (ms_solve_emit) *ms_solve_emit = b;
+    if (n_solves) *n_solves = cnt;
+    return rc;
+}
+
+int dust_ctx_check(dust_ctx *ctx, int *device_status) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    DeviceGuard dg(ctx->device);
+    if (dg.rc != DUST_OK) return dg.rc;
+    DUST_CUDA_TRY(cudaDeviceSynchronize());
+    int v = 0;
+    DUST_CUDA_TRY(cudaMemcpy(&v, ctx->tb.status, sizeof(int), cudaMemcpyDeviceToHost));
+    DUST_CUDA_TRY(cudaMemset(ctx->tb.status, 0, sizeof(int)));
+    if (device_status) *device_status = v;
+    return DUST_OK;
+}
+
+}  // extern "C"
