@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--paths", default="fp32,bf16x3,fp16x3", help="precisions to measure")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-stream measurement")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-load", type=float, default=0.7, help="arrival rate / saturated throughput")
     return ap.parse_args()
 
 
@@ -205,33 +209,38 @@ def run_ours(args):
         if ok != 0:
             raise RuntimeError(f"device status {ok} after {p} runs")
 
-    # end to end through the host-buffer entry point (pinned host memory)
-    Jh = torch.zeros((C, ld), dtype=torch.float32).pin_memory()
-    Jh[:, :K] = torch.from_numpy(wl.J)
-    nh = torch.from_numpy(wl.n).pin_memory()
-    Th = torch.empty((C, G), dtype=torch.float32).pin_memory()
-    Lh = torch.empty((C, ld), dtype=torch.float32).pin_memory()
-    rh = torch.empty((C,), dtype=torch.float64).pin_memory()
-    fh = torch.empty((C, G), dtype=torch.uint8).pin_memory()
-    cm = ctxs[main]
-    cm.set_precision(main)
-    args_h = (cm.handle, C, Jh.data_ptr(), ld, nh.data_ptr(), Th.data_ptr(), Lh.data_ptr(), rh.data_ptr(),
-              fh.data_ptr())
-    for _ in range(2):
-        _lib.dust_solve_host(*args_h)
-    ke = max(3, min(args.steps, 30))
-    if world > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(ke):
-        _lib.dust_solve_host(*args_h)
-    te = (time.perf_counter() - t0) / ke
-    if world > 1:
-        tt = torch.tensor([te], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = tt.item()
-    h2d = C * ld * 4 + C * G * 4
-    d2h = C * G * 4 + C * ld * 4 + C * 8 + C * G
+    # end to end through the host-buffer entry point (pinned host memory):
+    # every step copies J and n in and T, L, resid, flags out
+    e2e = None
+    if not args.no_e2e:
+        Jh = torch.zeros((C, ld), dtype=torch.float32).pin_memory()
+        Jh[:, :K] = torch.from_numpy(wl.J)
+        nh = torch.from_numpy(wl.n).pin_memory()
+        Th = torch.empty((C, G), dtype=torch.float32).pin_memory()
+        Lh = torch.empty((C, ld), dtype=torch.float32).pin_memory()
+        rh = torch.empty((C,), dtype=torch.float64).pin_memory()
+        fh = torch.empty((C, G), dtype=torch.uint8).pin_memory()
+        cm = ctxs[main]
+        cm.set_precision(main)
+        args_h = (cm.handle, C, Jh.data_ptr(), ld, nh.data_ptr(), Th.data_ptr(), Lh.data_ptr(), rh.data_ptr(),
+                  fh.data_ptr())
+        for _ in range(2):
+            _lib.dust_solve_host(*args_h)
+        ke = max(3, min(args.steps, 30))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            _lib.dust_solve_host(*args_h)
+        te = (time.perf_counter() - t0) / ke
+        if world > 1:
+            tt = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = tt.item()
+        h2d = C * ld * 4 + C * G * 4
+        d2h = C * G * 4 + C * ld * 4 + C * 8 + C * G
+        e2e = {"value": C * G * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": round(te * 1e3, 4), "api": "dust_solve_host (pinned host buffers)"}
 
     # roofline of the dominant kernel (the fused solve + emission kernel)
     ex2_rate, fma_rate = _lib.dust_diag_throughput(local)
@@ -258,8 +267,7 @@ def run_ours(args):
         "gpu_launches": 2 * args.steps,
         "roofline": roofline,
         "clocks": clk,
-        "e2e": {"value": C * G * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": round(te * 1e3, 4), "api": "dust_solve_host (pinned host buffers)"},
+        "e2e": e2e,
     }
     paths = {}
     for p in ctxs:
@@ -274,6 +282,10 @@ def run_ours(args):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], line["err_vs_oracle"] = cpu_baseline(args, wl, res)
+    if not args.no_serving:
+        del out_main, res, Jbuf, J, n
+        torch.cuda.empty_cache()
+        line["serving"] = run_serving(args, dev, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     for c in ctxs.values():
@@ -336,6 +348,133 @@ def cpu_baseline(args, wl_full, res):
                    "resid_max": float(np.abs(rs).max()), "flags_equal": bool((fl == ref["flags"]).all()),
                    "cells": nc}
     return base, errs
+
+
+# ------------------------------------------------------------------ serving
+def run_serving(args, dev, local):
+    """Request stream shaped like the serving workload: Poisson arrivals of
+    solves from 64 snapshots, cells log-uniform 1e3-1e6, K in {100, 200, 350,
+    500}, G in {48, 96, 240}.  Request inputs are generated on the device just
+    before submission (same recipe as synth, seeded per request).  Measures the
+    saturated throughput with a closed loop, then a Poisson stream at
+    `serve_load` x that rate through the continuous-batching server (BF16x3),
+    and the same stream through a one-request-at-a-time FP32 loop."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_0907_3768_gb300 import Context, Server
+    from synth import workloads as W
+
+    reqs = W.serve_requests(n_requests=args.serve_requests, rate_hz=1.0)
+    grids = {}
+    for K in W.SERVE_K:
+        for G in W.SERVE_G:
+            cfg = W.serve_snapshot_config(0, K, G, 8)
+            wl = synth.make_workload(cfg, cells=np.arange(1))
+            grids[(K, G)] = dict(
+                cfg=cfg, ld=(K + 3) // 4 * 4,
+                shape=torch.tensor(W.J_ISRF * W.stellar_shape(wl.lam), device=dev, dtype=torch.float64),
+                ext=torch.tensor((wl.lam / (0.55 * W.UM)) ** -1.3, device=dev, dtype=torch.float64),
+                n0=torch.tensor(W.size_weights(wl.sp_of_g, wl.a_of_g), device=dev, dtype=torch.float64),
+                mixed=Context.from_workload(wl, precision="bf16x3", device=local),
+                fp32=Context.from_workload(wl, precision="fp32", device=local))
+
+    def inputs(i):
+        r = reqs[i]
+        g = grids[(r["K"], r["G"])]
+        cfg, C, K = g["cfg"], r["n_cells"], r["K"]
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(cfg["seed"] * 1000003 + i)
+        lo, hi = cfg["log10U"]
+        U = 10.0 ** (torch.rand(C, generator=gen, device=dev, dtype=torch.float64) * (hi - lo) + lo)
+        rho = torch.exp(torch.randn(C, generator=gen, device=dev, dtype=torch.float64))
+        op = torch.rand(C, generator=gen, device=dev, dtype=torch.float64) < cfg["opaque_frac"]
+        tau = torch.rand(C, generator=gen, device=dev, dtype=torch.float64) * (cfg["tau_V"][1] - cfg["tau_V"][0]) \
+            + cfg["tau_V"][0]
+        Jb = torch.zeros((C, g["ld"]), dtype=torch.float32, device=dev)
+        Jb[:, :K] = U.float()[:, None] * g["shape"].float()[None, :]
+        idx = op.nonzero().squeeze(1)
+        if idx.numel():
+            Jb[idx, :K] *= torch.exp(-(tau[idx].float()[:, None] * g["ext"].float()[None, :]))
+        n = (rho[:, None] * g["n0"][None, :]).float()
+        return g, Jb[:, :K], n
+
+    total_cells = sum(r["n_cells"] for r in reqs)
+    total_solves = sum(r["n_cells"] * r["G"] for r in reqs)
+    budget = 48 << 30
+    res = {"requests": len(reqs), "cells": total_cells, "hbm_budget_bytes": budget,
+           "workload": "Poisson stream, 64 snapshots, cells log-uniform 1e3-1e6, K in {100,200,350,500}, "
+                       "G in {48,96,240}"}
+    # closed loop: saturated throughput of the server
+    with Server(budget, max_inflight=24, device=local) as srv:
+        pend = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(len(reqs)):
+            g, J, n = inputs(i)
+            pend.append((g["mixed"].submit(srv, J, n), J, n))
+            while len(pend) > 32:
+                (t, _), _, _ = pend.pop(0)
+                srv.wait(t, 600000.0)
+        for (t, _), _, _ in pend:
+            srv.wait(t, 600000.0)
+        sat = time.perf_counter() - t0
+        st = srv.stats()
+    res["saturated"] = {"s": sat, "requests_per_s": len(reqs) / sat, "cells_per_s": total_cells / sat,
+                        "solves_per_s": total_solves / sat, "rounds": st["rounds"], "launches": st["launches"]}
+    rate = args.serve_load * len(reqs) / sat
+    arrivals = np.array([r["t"] for r in reqs]) / rate
+    res["rate_hz"] = rate
+    res["load"] = args.serve_load
+
+    # Poisson stream through the server
+    with Server(budget, max_inflight=24, device=local) as srv:
+        pend, lag = {}, []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(len(reqs)):
+            while time.perf_counter() - t0 < arrivals[i]:
+                for t in [t for t in pend if srv.poll(t)[0] in ("done", "cancelled")]:
+                    del pend[t]
+                time.sleep(0.0002)
+            lag.append(time.perf_counter() - t0 - arrivals[i])
+            g, J, n = inputs(i)
+            t, out = g["mixed"].submit(srv, J, n)
+            pend[t] = (J, n, out)
+        for t in list(pend):
+            if srv.poll(t)[0] not in ("done", "cancelled"):
+                srv.wait(t, 600000.0)
+        span = time.perf_counter() - t0
+        st = srv.stats()
+    res["mixed_server"] = {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                           "mean_ms": st["mean_ms"], "span_s": span, "requests_per_s": len(reqs) / span,
+                           "cells_per_s": total_cells / span, "solves_per_s": total_solves / span,
+                           "rounds": st["rounds"], "completed": st["completed"],
+                           "client_lag_p99_ms": float(np.percentile(lag, 99) * 1e3),
+                           "latency": "submit to completion, server clock"}
+
+    # the same stream, one request at a time, FP32
+    lat = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(len(reqs)):
+        while time.perf_counter() - t0 < arrivals[i]:
+            time.sleep(0.0002)
+        g, J, n = inputs(i)
+        out = g["fp32"].solve(J, n)
+        torch.cuda.synchronize()
+        lat.append((time.perf_counter() - t0 - arrivals[i]) * 1e3)
+        del out
+    span = time.perf_counter() - t0
+    res["fp32_one_at_a_time"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                 "max_ms": float(max(lat)), "span_s": span, "requests_per_s": len(reqs) / span,
+                                 "solves_per_s": total_solves / span,
+                                 "latency": "arrival to completion (includes queueing behind earlier requests)"}
+    for g in grids.values():
+        g["mixed"].close()
+        g["fp32"].close()
+    return res
 
 
 # ------------------------------------------------------------------ reference arm

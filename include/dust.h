@@ -71,7 +71,7 @@ enum dust_flag {
 
 /* Create a context for one wavelength grid and one set of grains on `device`.
  *
- *  K, lambda[K], w[K]  host FP64, 2 <= K <= 8192: wavelengths (strictly increasing, > 0) and
+ *  K, lambda[K], w[K]  host FP64, 2 <= K <= 4096: wavelengths (strictly increasing, > 0) and
  *                      quadrature weights (>= 0) such that sum_k w_k f(lambda_k)
  *                      approximates the integral over wavelength (the paper's
  *                      Delta lambda_l, Eqs. 6-8).
@@ -166,6 +166,53 @@ int dust_ctx_check(dust_ctx *ctx, int *device_status);
 int dust_ctx_profile(dust_ctx *ctx, int enable);
 int dust_ctx_profile_read(dust_ctx *ctx, double *ms_absorb, double *ms_solve_emit,
                           int64_t *n_solves);
+
+/* ------------------------------------------------------------------ serving
+ * Continuous batching of solve requests (many snapshots / sub-grids, uneven
+ * cell counts, different contexts) on one GPU.  A scheduler thread admits
+ * requests in FIFO order (later ones may pass one that does not fit yet)
+ * while the summed device footprint of admitted requests (J, n, T, L, resid,
+ * flags and the scratch the solve needs) stays within `hbm_budget_bytes` and
+ * at most `max_inflight` are active; it then runs them in rounds, each round
+ * a fair-share chunk of every active request through one launch per kernel,
+ * with two rounds in flight.  Requests arriving while the GPU is busy join
+ * the next round.  A request's results are bitwise those of dust_solve on
+ * the same context with the context's precision at submit time.  The paper
+ * processes one grid per call (Section 5); serving has no counterpart there.
+ *
+ * dust_server_create: the server allocates `hbm_budget_bytes` (>= 1 MiB) of
+ * device memory for scratch up front.  max_inflight in [1, 4096].
+ * dust_serve_submit: arguments as dust_solve (device buffers, caller-owned,
+ * valid until the request finishes).  Returns a ticket; DUST_EBUSY when the
+ * request's footprint exceeds the whole budget (it could never be admitted).
+ * dust_serve_poll: *state = 0 queued, 1 active, 2 done, 3 cancelled (and
+ * *latency_ms = submit-to-completion time, or the time so far).  A poll that
+ * reports 2 or 3 releases the ticket (a later call returns DUST_ENOTFOUND);
+ * a failed request returns its error code and is released.
+ * dust_serve_wait: blocks up to timeout_ms; DUST_ETIMEOUT if still running,
+ * DUST_OK when done (ticket released).
+ * dust_serve_cancel: a queued request is dropped; an active one gets no
+ * further chunks (chunks already launched finish; its outputs are partial).
+ * dust_server_destroy: cancels queued requests, finishes active ones, frees
+ * everything. */
+typedef struct {
+    int64_t submitted, completed, cancelled, failed, queued, active;
+    int64_t cells_completed, rounds, launches;
+    double p50_ms, p99_ms, max_ms, mean_ms;  /* submit-to-completion latency */
+    double span_ms;                          /* first submit to last completion */
+    size_t hbm_in_use;                       /* footprint of admitted requests */
+} dust_serve_stats;
+
+int dust_server_create(dust_server **out, size_t hbm_budget_bytes, int max_inflight, int device);
+int dust_serve_submit(dust_server *srv, dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld,
+                      const float *n, float *T, float *L, double *resid, uint8_t *flags,
+                      uint64_t *ticket);
+int dust_serve_poll(dust_server *srv, uint64_t ticket, int *state, double *latency_ms);
+int dust_serve_wait(dust_server *srv, uint64_t ticket, double timeout_ms, double *latency_ms);
+int dust_serve_cancel(dust_server *srv, uint64_t ticket);
+int dust_server_stats(dust_server *srv, dust_serve_stats *out);
+int dust_server_reset_stats(dust_server *srv);
+void dust_server_destroy(dust_server *srv);
 
 /* Diagnostics (no counterpart in the paper): measured issue rates on `device`
  * of the two pipes the emission kernel uses, MUFU ex2.approx and FP32 FMA, in

@@ -21,7 +21,7 @@ from ._lib import (  # noqa: F401
 def __getattr__(name):
     # the torch-facing front end is imported lazily so that the ctypes layer
     # stays usable without touching CUDA
-    if name in ("Context", "padded_rows"):
+    if name in ("Context", "Server", "padded_rows"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

@@ -40,6 +40,14 @@ _SIGS = {
     "dust_ctx_profile": (_i, [_p, _i]),
     "dust_ctx_profile_read": (_i, [_p, _p, _p, _p]),
     "dust_diag_throughput": (_i, [_i, _p, _p]),
+    "dust_server_create": (_i, [ctypes.POINTER(_p), _sz, _i, _i]),
+    "dust_serve_submit": (_i, [_p, _p, _i64, _p, _i64, _p, _p, _p, _p, _p, ctypes.POINTER(ctypes.c_uint64)]),
+    "dust_serve_poll": (_i, [_p, ctypes.c_uint64, _p, _p]),
+    "dust_serve_wait": (_i, [_p, ctypes.c_uint64, _d, _p]),
+    "dust_serve_cancel": (_i, [_p, ctypes.c_uint64]),
+    "dust_server_stats": (_i, [_p, _p]),
+    "dust_server_reset_stats": (_i, [_p]),
+    "dust_server_destroy": (None, [_p]),
     "dust_last_error": (ctypes.c_char_p, []),
     "dust_version": (ctypes.c_char_p, []),
 }
@@ -137,6 +145,62 @@ def dust_diag_throughput(device=0):
     a, b = ctypes.c_double(), ctypes.c_double()
     check(lib().dust_diag_throughput(device, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+class ServeStats(ctypes.Structure):
+    """Mirror of dust_serve_stats."""
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "cancelled", "failed", "queued", "active",
+                                              "cells_completed", "rounds", "launches")] + \
+               [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "max_ms", "mean_ms", "span_ms")] + \
+               [("hbm_in_use", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+SERVE_STATE = {0: "queued", 1: "active", 2: "done", 3: "cancelled"}
+
+
+def dust_server_create(hbm_budget_bytes, max_inflight, device):
+    out = _p()
+    check(lib().dust_server_create(ctypes.byref(out), int(hbm_budget_bytes), int(max_inflight), int(device)))
+    return out.value
+
+
+def dust_serve_submit(srv, ctx, n_cells, J, ld, n, T, L, resid, flags):
+    t = ctypes.c_uint64()
+    check(lib().dust_serve_submit(srv, ctx, n_cells, J, ld, n, T, L, resid, flags, ctypes.byref(t)))
+    return t.value
+
+
+def dust_serve_poll(srv, ticket):
+    st, lat = ctypes.c_int(), ctypes.c_double()
+    check(lib().dust_serve_poll(srv, ticket, ctypes.byref(st), ctypes.byref(lat)))
+    return st.value, lat.value
+
+
+def dust_serve_wait(srv, ticket, timeout_ms):
+    lat = ctypes.c_double()
+    check(lib().dust_serve_wait(srv, ticket, float(timeout_ms), ctypes.byref(lat)))
+    return lat.value
+
+
+def dust_serve_cancel(srv, ticket):
+    return check(lib().dust_serve_cancel(srv, ticket))
+
+
+def dust_server_stats(srv):
+    s = ServeStats()
+    check(lib().dust_server_stats(srv, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def dust_server_reset_stats(srv):
+    return check(lib().dust_server_reset_stats(srv))
+
+
+def dust_server_destroy(srv):
+    lib().dust_server_destroy(srv)
 
 
 def dust_last_error():

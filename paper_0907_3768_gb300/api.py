@@ -119,6 +119,17 @@ class Context:
                              _ptr(out["L_buf"]), _ptr(out["resid"]), _ptr(out["flags"]), sptr)
         return out
 
+    def submit(self, server, J, n, out=None, want_L=True, want_resid=True, want_flags=True):
+        """Queue a solve on `server` (continuous batching); returns (ticket, out).
+        J, n and out must stay alive until the request finishes."""
+        C, ld = self._check_inputs(J, n)
+        if out is None:
+            out = self.alloc_outputs(C, ld, want_L, want_resid, want_flags)
+        t = _lib.dust_serve_submit(server.handle, self.handle, C, J.data_ptr(), ld, n.data_ptr(),
+                                   out["T"].data_ptr(), _ptr(out["L_buf"]), _ptr(out["resid"]),
+                                   _ptr(out["flags"]))
+        return t, out
+
     def solve_host(self, J, n, T=None, L=None, resid=None, flags=None):
         """The hot path on host arrays (numpy or CPU tensors, ideally pinned);
         outputs are written into / returned as host arrays."""
@@ -141,3 +152,45 @@ class Context:
         _lib.dust_solve_host(self.handle, C, Jn.ctypes.data, ld, nn.ctypes.data, T.ctypes.data,
                              Lb.ctypes.data, resid.ctypes.data, flags.ctypes.data)
         return dict(T=T, L=L, resid=resid, flags=flags)
+
+
+class Server:
+    """Continuous-batching request server on one GPU (see include/dust.h)."""
+
+    def __init__(self, hbm_budget_bytes, max_inflight=32, device=0):
+        self.handle = None
+        self.handle = _lib.dust_server_create(int(hbm_budget_bytes), int(max_inflight), int(device))
+
+    def poll(self, ticket):
+        """(state name, latency ms); a finished ticket is released by the poll."""
+        st, lat = _lib.dust_serve_poll(self.handle, ticket)
+        return _lib.SERVE_STATE.get(st, st), lat
+
+    def wait(self, ticket, timeout_ms=60000.0):
+        return _lib.dust_serve_wait(self.handle, ticket, timeout_ms)
+
+    def cancel(self, ticket):
+        _lib.dust_serve_cancel(self.handle, ticket)
+
+    def stats(self):
+        return _lib.dust_server_stats(self.handle)
+
+    def reset_stats(self):
+        _lib.dust_server_reset_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            _lib.dust_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

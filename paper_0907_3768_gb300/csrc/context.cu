@@ -200,7 +200,7 @@ __global__ void k_w32(int K, int G, int Gs, int Kw, const double *W, const doubl
 
 // Emission constants: q_k, Chat (split into two float4 halves per group of 8
 // wavelengths) and nax_k; padding wavelengths get Chat = 0 and nax = -1.
-__global__ void k_emis(int K, int G, int Kp, int NKG, const double *lam, const double *C,
+__global__ void k_emis(int K, int G, int G8, int Kp, int NKG, const double *lam, const double *C,
                        float *Chat, int *qexp, float *nax) {
     int k = blockIdx.x;
     if (k >= Kp) return;
@@ -214,9 +214,9 @@ __global__ void k_emis(int K, int G, int Kp, int NKG, const double *lam, const d
     for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int q = (mx > 0.0) ? (int)ceil(log2(mx)) : 0;
     int kg = k / 8, h = (k % 8) / 4, e = k % 4;
-    for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        float v = (k < K) ? (float)(fac * C[(size_t)g * K + k] * exp2(-(double)q)) : 0.f;
-        Chat[(((size_t)g * 2 + h) * NKG + kg) * 4 + e] = v;
+    for (int g = threadIdx.x; g < G8; g += blockDim.x) {
+        float v = (k < K && g < G) ? (float)(fac * C[(size_t)g * K + k] * exp2(-(double)q)) : 0.f;
+        Chat[(((size_t)kg * G8 + g) * 2 + h) * 4 + e] = v;
     }
     if (threadIdx.x == 0) {
         qexp[k] = q;
@@ -255,6 +255,7 @@ int build_context(dust_ctx *ctx, const double *lambda, const double *w, const do
     const int K = ctx->K, G = ctx->G, NT = ctx->NT, NI = ctx->NI;
     const int Gs = (G + GPAD - 1) / GPAD * GPAD;
     const int NKG = (K + KQ - 1) / KQ;
+    const int G8 = (G + RG - 1) / RG * RG;
     const int Kp = NKG * KQ;
     const int Kw = (K + KC - 1) / KC * KC;
     ctx->Kw = Kw;
@@ -289,17 +290,19 @@ int build_context(dust_ctx *ctx, const double *lambda, const double *w, const do
     size_t o_gs = take(sizeof(double) * G);
     size_t o_P0 = take(sizeof(double) * G);
     size_t o_Pm = take(sizeof(double) * G);
+    size_t o_gr = take(sizeof(float4) * G);
     size_t o_nax = take(sizeof(float) * Kp);
-    size_t o_Ch = take(sizeof(float) * (size_t)G * Kp);
+    size_t o_Ch = take(sizeof(float) * (size_t)G8 * Kp);
     size_t o_q = take(sizeof(int) * Kp);
     size_t o_w = take(sizeof(double) * K);
+    size_t o_wq = take(sizeof(float) * K);
     size_t o_st = take(sizeof(int));
     DUST_CUDA_TRY(cudaMalloc(&ctx->tables_mem, off));
     ctx->tables_bytes = off;
     char *base = (char *)ctx->tables_mem;
     DUST_CUDA_TRY(cudaMemset(base, 0, off));
     DevTables &tb = ctx->tb;
-    tb.K = K; tb.G = G; tb.Kp = Kp; tb.NKG = NKG; tb.Gs = Gs; tb.NT = NT; tb.NI = NI;
+    tb.K = K; tb.G = G; tb.G8 = G8; tb.Kp = Kp; tb.NKG = NKG; tb.Gs = Gs; tb.NT = NT; tb.NI = NI;
     tb.log2Tmin = (float)log2Tmin; tb.h2 = (float)h2;
     tb.Tmin = (float)ctx->Tmin; tb.Tmax = (float)ctx->Tmax;
     tb.fw = (const float4 *)(base + o_fw);
@@ -309,10 +312,12 @@ int build_context(dust_ctx *ctx, const double *lambda, const double *w, const do
     tb.gscale = (const double *)(base + o_gs);
     tb.P0 = (const double *)(base + o_P0);
     tb.Pmax = (const double *)(base + o_Pm);
+    tb.gres = (const float4 *)(base + o_gr);
     tb.nax = (const float *)(base + o_nax);
     tb.Chat = (const float *)(base + o_Ch);
     tb.qexp = (const int *)(base + o_q);
     tb.w = (const double *)(base + o_w);
+    tb.wq = (const float *)(base + o_wq);
     tb.status = (int *)(base + o_st);
     DUST_CUDA_TRY(cudaMemcpy(base + o_w, w, sizeof(double) * K, cudaMemcpyHostToDevice));
 
@@ -338,6 +343,26 @@ int build_context(dust_ctx *ctx, const double *lambda, const double *w, const do
         return set_error(DUST_EINVAL,
                          "grain %d: P_g(T) is zero or not finite in FP64 over [T_min, T_max] "
                          "(no absorption, or T_min too low for this wavelength grid)", bad - 1);
+    // residual constants: grain scales as float-float under one power of two
+    {
+        std::vector<double> gs(G), pm(G);
+        std::vector<GrainParam> gpr(G);
+        DUST_CUDA_TRY(cudaMemcpy(gs.data(), base + o_gs, sizeof(double) * G, cudaMemcpyDeviceToHost));
+        DUST_CUDA_TRY(cudaMemcpy(pm.data(), base + o_Pm, sizeof(double) * G, cudaMemcpyDeviceToHost));
+        DUST_CUDA_TRY(cudaMemcpy(gpr.data(), base + o_gp, sizeof(GrainParam) * G, cudaMemcpyDeviceToHost));
+        double mx = 0.0;
+        for (int g = 0; g < G; ++g) mx = std::max(mx, gs[g]);
+        const int Eg = (int)std::ceil(std::log2(mx));
+        std::vector<float4> gr(G);
+        for (int g = 0; g < G; ++g) {
+            const double v = std::ldexp(gs[g], -Eg);
+            const float hi = (float)v;
+            gr[g] = make_float4(hi, (float)(v - (double)hi), (float)std::ldexp(1.0, -(int)gpr[g].f),
+                                (float)(pm[g] / gs[g]));
+        }
+        DUST_CUDA_TRY(cudaMemcpy(base + o_gr, gr.data(), sizeof(float4) * G, cudaMemcpyHostToDevice));
+        tb.Eg = Eg;
+    }
     k_fw32<<<blocks((size_t)G * (NT - 1)), B>>>(G, NT, h2, (double *)t_lp.p, (double *)t_sl.p,
                                                 (float4 *)(base + o_fw));
     k_inverse<<<blocks((size_t)G * NI), B>>>(G, NT, NI, log2Tmin, h2, (double *)t_lp.p,
@@ -349,9 +374,21 @@ int build_context(dust_ctx *ctx, const double *lambda, const double *w, const do
     k_w32<<<blocks((size_t)Gs * Kw), B>>>(K, G, Gs, Kw, W_d, (double *)(base + o_P0),
                                           (const GrainParam *)(base + o_gp), ctx->W32,
                                           ctx->Wimg[0], ctx->Wimg[1]);
-    k_emis<<<Kp, 32>>>(K, G, Kp, NKG, lam_d, (double *)t_C.p, (float *)(base + o_Ch),
+    k_emis<<<Kp, 32>>>(K, G, G8, Kp, NKG, lam_d, (double *)t_C.p, (float *)(base + o_Ch),
                        (int *)(base + o_q), (float *)(base + o_nax));
     DUST_CUDA_TRY(cudaGetLastError());
+    // residual weights w_k 2^(q_k - Ew), normalised by one power of two Ew
+    {
+        std::vector<int> q(Kp);
+        DUST_CUDA_TRY(cudaMemcpy(q.data(), base + o_q, sizeof(int) * Kp, cudaMemcpyDeviceToHost));
+        double mx = 0.0;
+        for (int k = 0; k < K; ++k) mx = std::max(mx, w[k] * std::ldexp(1.0, q[k]));
+        const int Ew = mx > 0.0 ? (int)std::ceil(std::log2(mx)) : 0;
+        std::vector<float> wq(K);
+        for (int k = 0; k < K; ++k) wq[k] = (float)std::ldexp(w[k], q[k] - Ew);
+        DUST_CUDA_TRY(cudaMemcpy(base + o_wq, wq.data(), sizeof(float) * K, cudaMemcpyHostToDevice));
+        tb.Ew = Ew;
+    }
     DUST_CUDA_TRY(cudaDeviceSynchronize());
     return DUST_OK;
 }
@@ -394,7 +431,7 @@ int dust_ctx_create(dust_ctx **out, int K, const double *lambda, const double *w
     if (!out) return set_error(DUST_EINVAL, "out is NULL");
     *out = nullptr;
     if (!lambda || !w || !c_abs) return set_error(DUST_EINVAL, "lambda, w and c_abs must be non-NULL");
-    if (K < 2 || K > 8192) return set_error(DUST_EINVAL, "K=%d outside [2, 8192]", K);
+    if (K < 2 || K > 4096) return set_error(DUST_EINVAL, "K=%d outside [2, 4096]", K);
     if (G < 1 || G > 512) return set_error(DUST_EINVAL, "G=%d outside [1, 512]", G);
     if (!(T_min > 0.0) || !(T_max > T_min) || !std::isfinite(T_max))
         return set_error(DUST_EINVAL, "need 0 < T_min < T_max < inf");

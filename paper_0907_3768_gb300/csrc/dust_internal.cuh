@@ -1,6 +1,7 @@
 // Internal declarations shared by libdust's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
@@ -35,6 +36,7 @@ struct GrainParam {
 // Everything the device kernels read from a context, passed by value.
 struct DevTables {
     int K, G, Kp, NKG;        // Kp = NKG * KQ >= K (emission padding)
+    int G8;                   // G rounded up to RG (emission padding, zero weights)
     int Gs;                   // row stride of the absorbed-power scratch (G rounded to GPAD)
     int NT, NI;               // forward / inverse table sizes
     float log2Tmin, h2;       // u_j = log2Tmin + j h2 (u = log2 T)
@@ -46,11 +48,75 @@ struct DevTables {
     const double *gscale;     // [G] A = S * gscale (= P0 2^f)
     const double *P0;         // [G] P_g(T_min)
     const double *Pmax;       // [G] P_g(T_max)
+    const float4 *gres;       // [G] residual constants: gscale 2^-Eg as float-float (x, y),
+                              //     S of a grain clamped low (z = 2^-f) and high (w = Pmax / gscale)
+    int Eg;
     const float *nax;         // [Kp] -log2(e) h c / (lambda_k k_B), 0 in the padding
-    const float *Chat;        // [G][2][NKG][4] scaled emission weights (see context.cu)
+    const float *Chat;        // [NKG][G8][2][4] scaled emission weights (see context.cu)
     const int *qexp;          // [Kp] per-wavelength exponent of Chat
-    const double *w;          // [K] quadrature weights (residual)
+    const double *w;          // [K] quadrature weights
+    const float *wq;          // [K] w_k 2^(q_k - Ew) (residual of the scaled emission sums)
+    int Ew;
     int *status;              // device status word (dust_status)
+};
+
+// ---- work lists of the batched kernels (passed by value as kernel parameters)
+constexpr int MAXREQ = 32;
+
+enum EmitMode { EMIT_ON = 1, EMIT_RESID = 2, EMIT_STORE_L = 4 };
+
+// One request of the solve/emission kernel.
+struct EmitReq {
+    DevTables tb;
+    int64_t C, ld, tile_begin;
+    const float *S, *n;
+    float *T, *L;
+    double *resid;
+    uint8_t *flags;
+    int TC, GC, resident, mode;
+};
+
+struct EmitBatch {
+    int nreq;
+    int64_t ntiles;
+    EmitReq req[MAXREQ];
+};
+
+struct EmitPlan {
+    int TC, GC, resident;
+    size_t smem;
+};
+
+// One request of the tensor-core absorption kernel (its TMA descriptor for J
+// sits in TcBatch::tm at the same index).
+struct TcReq {
+    int64_t C, tile_begin;
+    int Gs, nkc;
+    const uint16_t *Wimg;
+    float *S;
+};
+
+struct TcBatch {
+    CUtensorMap tm[MAXREQ];
+    TcReq req[MAXREQ];
+    int nreq;
+    int64_t ntiles;
+    int GsMax, ns1, ns2, tmem_cols, off_exp, j_off;
+    int *status;
+};
+
+// One request of the FP32 SIMT absorption kernel.
+struct SimtReq {
+    int64_t C, ld, tile_begin;
+    const float *J, *W;
+    float *S;
+    int K, Kw, Gs, ntn;  // ntn = grain tiles per cell tile
+};
+
+struct SimtBatch {
+    SimtReq req[MAXREQ];
+    int nreq;
+    int64_t ntiles;
 };
 
 }  // namespace dust
@@ -115,6 +181,20 @@ int launch_gemm_tc(const dust_ctx *ctx, int precision, int64_t C, const float *J
                    float *S, cudaStream_t st);
 int launch_solve_emit(const dust_ctx *ctx, int64_t C, const float *S, const float *n, float *T,
                       float *L, int64_t ld, double *resid, uint8_t *flags, cudaStream_t st);
+EmitPlan plan_emit(const dust_ctx *ctx, bool emit);
+// Tensor-core batches: one request entry (encodes its TMA descriptor), the
+// ring geometry of a batch, and the launch.  All requests of one launch share
+// the precision.
+int make_tc_req(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, float *S,
+                TcReq &r, CUtensorMap &tm);
+int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem);
+int launch_tc_batch(const TcBatch &B, int precision, size_t smem, int num_sms, cudaStream_t st);
+// FP32 SIMT batches.
+void make_simt_req(const dust_ctx *ctx, int64_t C, const float *J, int64_t ld, float *S, SimtReq &r);
+int launch_simt_batch(SimtBatch &B, cudaStream_t st);
+void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const float *S, const float *n,
+                   float *T, float *L, int64_t ld, double *resid, uint8_t *flags, EmitReq &r);
+int launch_emit_batch(const EmitBatch &B, size_t smem, int num_sms, cudaStream_t st);
 
 // Grow the context's scratch to hold `cells` rows (synchronises `st` first).
 int ensure_scratch(dust_ctx *ctx, int64_t cells, cudaStream_t st);

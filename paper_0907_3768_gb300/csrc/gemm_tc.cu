@@ -163,23 +163,21 @@ __device__ __forceinline__ uint32_t pack_split(float x0, float x1, bool bf16, ui
     return hi;
 }
 
-struct TcParams {
-    int64_t C;
-    int K, Gs, nkc;         // nkc = K chunks of KC wavelengths
-    int ns1, ns2;           // ring depths
-    int tmem_cols;
-    int off_exp;            // J and W scale offsets folded into the epilogue exponent
-    int j_off;              // J is scaled to [2^(j_off-1), 2^j_off) per cell
-    const uint16_t *Wimg;   // [nkc][2][Gs x KC] 16-bit images
-    float *S;
-    int *status;
-};
+// Request of global tile `tile` (tiles of a CTA increase, so the search
+// starts from the previous answer).
+__device__ __forceinline__ int tc_req_of(const TcBatch &p, int64_t tile, int ri) {
+    while (ri + 1 < p.nreq && tile >= p.req[ri + 1].tile_begin) ++ri;
+    return ri;
+}
 
+// TcBatch fields: GsMax sets the ring layout, ns1 / ns2 the ring depths,
+// j_off scales J to [2^(j_off-1), 2^j_off) per cell, off_exp is the W image
+// scale folded back in the epilogue.
 template <bool BF16, bool TWO_PASS>
-__global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__ CUtensorMap tmJ, TcParams p) {
+__global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__ TcBatch p) {
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
-    const int B_BYTES = p.Gs * KC * 2 * 2;  // hi + lo W chunk
+    const int B_BYTES = p.GsMax * KC * 2 * 2;  // ring slot of a hi + lo W chunk
     unsigned char *st1 = smem;
     unsigned char *stA = st1 + (size_t)p.ns1 * STAGE1_BYTES;
     unsigned char *stB = stA + (size_t)p.ns2 * 2 * A_BYTES;
@@ -191,7 +189,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ntiles = (p.C + BM - 1) / BM;
+    const int64_t ntiles = p.ntiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < p.ns1; ++s) { mbar_init(&full1[s], 1); mbar_init(&empty1[s], 4); }
@@ -220,19 +218,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
             uint32_t ph1 = 0, pha = 0;
             int64_t n1 = 0, n2 = 0;  // copies issued into each ring
             bool ok = true;
+            int ri = 0;
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                const int row0 = (int)(tile * BM);
+                ri = tc_req_of(p, tile, ri);
+                const TcReq &q = p.req[ri];
+                const CUtensorMap *tm = &p.tm[ri];
+                const int row0 = (int)((tile - q.tile_begin) * BM);
+                const uint32_t wbytes = (uint32_t)q.Gs * KC * 4;  // this request's hi + lo chunk
                 for (int pass = TWO_PASS ? 0 : 1; pass < 2 && ok; ++pass) {
-                    for (int kc = 0; kc < p.nkc && ok; ++kc) {
+                    for (int kc = 0; kc < q.nkc && ok; ++kc) {
                         if (!(ok = mbar_wait(&empty1[s1], ph1 ^ 1, abort_flag, p.status))) break;
                         mbar_expect_tx(&full1[s1], STAGE1_BYTES);
-                        tma_load_2d(st1 + (size_t)s1 * STAGE1_BYTES, &tmJ, kc * KC, row0, &full1[s1]);
+                        tma_load_2d(st1 + (size_t)s1 * STAGE1_BYTES, tm, kc * KC, row0, &full1[s1]);
                         ++n1;
                         if (++s1 == p.ns1) { s1 = 0; ph1 ^= 1; }
                         if (pass == 1) {
                             if (!(ok = mbar_wait(&a_empty[sa], pha ^ 1, abort_flag, p.status))) break;
-                            mbar_expect_tx(&b_full[sa], B_BYTES);
-                            bulk_load(stB + (size_t)sa * B_BYTES, p.Wimg + (size_t)kc * (B_BYTES / 2), B_BYTES,
+                            mbar_expect_tx(&b_full[sa], wbytes);
+                            bulk_load(stB + (size_t)sa * B_BYTES, q.Wimg + (size_t)kc * (wbytes / 2), wbytes,
                                       &b_full[sa]);
                             ++n2;
                             if (++sa == p.ns2) { sa = 0; pha ^= 1; }
@@ -255,15 +258,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc_full = instr_desc(BF16, BM, p.Gs <= 256 ? p.Gs : 256);
-            const uint32_t idesc_tail = instr_desc(BF16, BM, p.Gs > 256 ? p.Gs - 256 : 16);
-            int sa = 0;
+            int sa = 0, ri = 0;
             uint32_t pha = 0, phacc = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                ri = tc_req_of(p, tile, ri);
+                const int Gs = p.req[ri].Gs, nkc = p.req[ri].nkc;
+                const uint32_t idesc_full = instr_desc(BF16, BM, Gs <= 256 ? Gs : 256);
+                const uint32_t idesc_tail = instr_desc(BF16, BM, Gs > 256 ? Gs - 256 : 16);
                 if (!(ok = mbar_wait(acc_empty, phacc ^ 1, abort_flag, p.status))) break;
                 tc_fence_after();
-                for (int kc = 0; kc < p.nkc && ok; ++kc) {
+                for (int kc = 0; kc < nkc && ok; ++kc) {
                     if (!(ok = mbar_wait(&a_full[sa], pha, abort_flag, p.status))) break;
                     if (!(ok = mbar_wait(&b_full[sa], pha, abort_flag, p.status))) break;
                     tc_fence_after();
@@ -275,11 +280,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
                         for (int part = 0; part < 3; ++part) {
                             // hi.hi, lo.hi, hi.lo
                             const uint32_t aoff = (part == 1 ? A_BYTES : 0) + ks * 256;
-                            const uint32_t boff = (part == 2 ? p.Gs * KC * 2 : 0) + ks * 256;
+                            const uint32_t boff = (part == 2 ? Gs * KC * 2 : 0) + ks * 256;
                             const uint32_t acc = (kc | ks | part) ? 1u : 0u;
                             tc_mma(tmem, smem_desc(a_base + aoff, 128, 512), smem_desc(b_base + boff, 128, 512),
                                    idesc_full, acc);
-                            if (p.Gs > 256)
+                            if (Gs > 256)
                                 tc_mma(tmem + 256, smem_desc(a_base + aoff, 128, 512),
                                        smem_desc(b_base + boff + 32 * 512, 128, 512), idesc_tail, acc);
                         }
@@ -298,14 +303,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
         // ------------------------------------------------------------ converters + epilogue
         const int quad = warp & 3;           // TMEM lane quarter this warp may access
         const int r = quad * 32 + lane;      // tile row owned by this thread
-        int s1 = 0, sa = 0;
+        int s1 = 0, sa = 0, ri = 0;
         uint32_t ph1 = 0, pha = 0, phacc = 0;
         bool ok = true;
         for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            ri = tc_req_of(p, tile, ri);
+            const TcReq &q = p.req[ri];
             int e = 0;
             if (TWO_PASS) {
                 float mx = 0.f;
-                for (int kc = 0; kc < p.nkc; ++kc) {
+                for (int kc = 0; kc < q.nkc; ++kc) {
                     if (!(ok = mbar_wait(&full1[s1], ph1, abort_flag, p.status))) break;
                     const unsigned char *src = st1 + (size_t)s1 * STAGE1_BYTES + r * 128;
 #pragma unroll
@@ -322,7 +329,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
                 e = min(max(e, p.j_off - 126), p.j_off + 126);  // keep 2^(j_off - e) a normal float
             }
             const float scale = __int_as_float((127 - e + p.j_off) << 23);  // 2^(j_off - e)
-            for (int kc = 0; kc < p.nkc; ++kc) {
+            for (int kc = 0; kc < q.nkc; ++kc) {
                 if (!(ok = mbar_wait(&full1[s1], ph1, abort_flag, p.status))) break;
                 if (!(ok = mbar_wait(&a_empty[sa], pha ^ 1, abort_flag, p.status))) break;
                 const unsigned char *src = st1 + (size_t)s1 * STAGE1_BYTES + r * 128;
@@ -351,13 +358,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
             if (!(ok = mbar_wait(acc_full, phacc, abort_flag, p.status))) break;
             phacc ^= 1;
             tc_fence_after();
-            const int64_t row = tile * BM + r;
+            const int64_t row = (tile - q.tile_begin) * BM + r;
             const int ex = e - p.j_off - p.off_exp;
-            float *dst = p.S + row * p.Gs;
-            for (int c0 = 0; c0 < p.Gs; c0 += 16) {
+            float *dst = q.S + row * q.Gs;
+            for (int c0 = 0; c0 < q.Gs; c0 += 16) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + c0, v);
-                if (row < p.C) {
+                if (row < q.C) {
 #pragma unroll
                     for (int i = 0; i < 16; i += 4)
                         *reinterpret_cast<float4 *>(dst + c0 + i) =
@@ -393,26 +400,23 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 template <bool BF16, bool TWO_PASS>
-int launch_t(const dust_ctx *ctx, const CUtensorMap &tm, const TcParams &p, size_t smem, int grid,
-             cudaStream_t st) {
+int launch_t(const TcBatch &B, size_t smem, int grid, cudaStream_t st) {
     auto kern = k_gemm_tc<BF16, TWO_PASS>;
     DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, NTHREADS, smem, st>>>(tm, p);
+    kern<<<grid, NTHREADS, smem, st>>>(B);
     DUST_CUDA_TRY(cudaGetLastError());
     return DUST_OK;
 }
 
 }  // namespace
 
-int launch_gemm_tc(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, float *S,
-                   cudaStream_t st) {
-    if (C <= 0) return DUST_OK;
+int make_tc_req(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, float *S, TcReq &r,
+                CUtensorMap &tm) {
     const bool bf16 = precision == DUST_PREC_BF16X3;
-    const int Gs = ctx->tb.Gs, K = ctx->K;
+    const int K = ctx->K;
     if (C > 0x7fffffffLL - BM) return set_error(DUST_EINVAL, "too many cells for one tensor-core launch");
     auto encode = get_encode();
     if (!encode) return set_error(DUST_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    CUtensorMap tm;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)C};
     cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
     cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)BM};
@@ -421,39 +425,68 @@ int launch_gemm_tc(const dust_ctx *ctx, int precision, int64_t C, const float *J
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return set_error(DUST_EINVAL, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    r.C = C;
+    r.tile_begin = 0;
+    r.Gs = ctx->tb.Gs;
+    r.nkc = (K + KC - 1) / KC;
+    r.Wimg = ctx->Wimg[bf16 ? 0 : 1];
+    r.S = S;
+    return DUST_OK;
+}
 
-    TcParams p{};
-    p.C = C;
-    p.K = K;
-    p.Gs = Gs;
-    p.nkc = (K + KC - 1) / KC;
+// Tile offsets, ring depths and tensor-memory width of a filled batch.
+int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem) {
+    const bool bf16 = precision == DUST_PREC_BF16X3;
+    int64_t t = 0;
+    int gmax = 16;
+    for (int i = 0; i < B.nreq; ++i) {
+        B.req[i].tile_begin = t;
+        t += (B.req[i].C + BM - 1) / BM;
+        gmax = std::max(gmax, B.req[i].Gs);
+    }
+    B.ntiles = t;
+    B.GsMax = gmax;
     int cols = 32;
-    while (cols < Gs) cols <<= 1;
-    p.tmem_cols = cols;
+    while (cols < gmax) cols <<= 1;
+    B.tmem_cols = cols;
     // FP16 keeps J in [2^14, 2^15) and W in (2^13, 2^14] (the W image is
     // built with 2^14 folded in); BF16 has FP32's exponent range and needs none.
-    p.j_off = bf16 ? 0 : 15;
-    p.off_exp = bf16 ? 0 : 14;
-    p.Wimg = ctx->Wimg[bf16 ? 0 : 1];
-    p.S = S;
-    p.status = ctx->tb.status;
-    const size_t b_bytes = (size_t)Gs * KC * 4;
-    const size_t budget = (ctx->smem_optin ? ctx->smem_optin : 232448) - 1024 - 256;
+    B.j_off = bf16 ? 0 : 15;
+    B.off_exp = bf16 ? 0 : 14;
+    const size_t b_bytes = (size_t)gmax * KC * 4;
+    const size_t budget = (smem_optin ? smem_optin : 232448) - 1024 - 256;
     int ns2 = 4, ns1 = 6;
     auto need = [&](int a, int b) { return (size_t)a * STAGE1_BYTES + (size_t)b * (2 * A_BYTES + b_bytes) + 256; };
     while (need(ns1, ns2) > budget && ns1 > 3) --ns1;
     while (need(ns1, ns2) > budget && ns2 > 2) --ns2;
     while (need(ns1, ns2) > budget && ns1 > 2) --ns1;
     if (need(ns1, ns2) > budget) return set_error(DUST_EINVAL, "G too large for the tensor-core kernel");
-    p.ns1 = ns1;
-    p.ns2 = ns2;
-    const size_t smem = need(ns1, ns2) + 1024;
-    const int64_t ntiles = (C + BM - 1) / BM;
-    const int grid = (int)std::min<int64_t>(ntiles, ctx->num_sms);
+    B.ns1 = ns1;
+    B.ns2 = ns2;
+    *smem = need(ns1, ns2) + 1024;
+    return DUST_OK;
+}
+
+int launch_tc_batch(const TcBatch &B, int precision, size_t smem, int num_sms, cudaStream_t st) {
+    if (B.ntiles <= 0) return DUST_OK;
+    const int grid = (int)std::min<int64_t>(B.ntiles, num_sms);
     // BF16: the per-cell power-of-two scale is exact and leaves every product
     // unchanged, so the exponent pass runs only for FP16.
-    if (bf16) return launch_t<true, false>(ctx, tm, p, smem, grid, st);
-    return launch_t<false, true>(ctx, tm, p, smem, grid, st);
+    if (precision == DUST_PREC_BF16X3) return launch_t<true, false>(B, smem, grid, st);
+    return launch_t<false, true>(B, smem, grid, st);
+}
+
+int launch_gemm_tc(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, float *S,
+                   cudaStream_t st) {
+    if (C <= 0) return DUST_OK;
+    TcBatch B;
+    B.nreq = 1;
+    B.status = ctx->tb.status;
+    int rc = make_tc_req(ctx, precision, C, J, ld, S, B.req[0], B.tm[0]);
+    if (rc != DUST_OK) return rc;
+    size_t smem = 0;
+    if ((rc = finish_tc_batch(B, precision, ctx->smem_optin, &smem)) != DUST_OK) return rc;
+    return launch_tc_batch(B, precision, smem, ctx->num_sms, st);
 }
 
 }  // namespace dust

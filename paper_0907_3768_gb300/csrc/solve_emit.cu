@@ -1,29 +1,42 @@
-// Kernel (b): fused equilibrium-temperature solve and emission SED.
+// Kernel (b): fused equilibrium-temperature solve and emission SED over a
+// work list of requests (one request for dust_solve, many for the server).
 //
-// A persistent CTA walks tiles of TC cells.  For each tile:
-//  phase 0  per-cell exponent m_c of max_g n[c,g] (n is used as n 2^-m_c);
-//  phase 1  one thread per (cell, grain): the root of Eq. 7 from the scaled
-//           absorbed power S (A / P_g(T_min) = S 2^f_g): an initial guess from
-//           the inverse table u(t), then Newton on the FP32 Hermite
-//           interpolant of t_g(u) = log2(P_g(2^u) / P_g(T_min)) inside the
-//           bracketing table interval (bisection when a Newton step leaves
-//           it).  The paper's kernel 3 ran Newton with a fresh quadrature per
-//           iteration (Section 4.3); the table removes those exponentials.
-//  phase 2  one thread per (cell, 8 consecutive wavelengths): Eq. 10,
-//           L[c,k] = 2^(m_c+q_k) sum_g (n 2^-m_c) Chat[g,k] t/(1-t),
-//           t = 2^(nax_k / T[c,g]) (one MUFU ex2 per term), with the sum over
-//           grains accumulated as a fraction N/D over groups of 8 grains so
-//           that each group costs one reciprocal instead of eight:
+// A persistent CTA walks tiles of TC cells; a tile belongs to one request.
+// Per tile:
+//  load     S (scaled absorbed powers) and n of the tile into shared memory;
+//  phase 0  one warp per cell: exponent m_c of max_g n[c,g] (n enters the
+//           emission as n 2^-m_c);
+//  phase 1  (cell, grain) pairs spread over all threads, NB solves in flight
+//           per thread: the root of Eq. 7 from a guess out of the inverse
+//           table u(t), then Newton on the FP32 Hermite interpolant of
+//           t_g(u) = log2(P_g(2^u) / P_g(T_min)) inside the bracketing table
+//           interval, bisection when a step leaves it.  The paper's kernel 3
+//           iterated Newton with a fresh quadrature per step (Section 4.3);
+//           the device table removes those exponentials;
+//  phase 2  one thread per (cell, 8 consecutive wavelengths), Eq. 10:
+//             L[c,k] = 2^(m_c+q_k) sum_g (n 2^-m_c) Chat[g,k] t/(1-t),
+//             t = 2^(nax_k / T[c,g])  (one MUFU ex2 per term),
+//           the grain sum accumulated as a fraction N/D over groups of 8
+//           grains so that a group costs one reciprocal instead of eight:
 //             N <- N + t (w D - N),  D <- D - t D   (= sum of w t/(1-t)).
-//           Chat is staged in shared memory (in grain chunks when it does not
-//           fit), as the paper staged sigma per block (Section 4.4).
-//  resid    sum_k w_k L[c,k] / (4 pi sum_g n Pe) - 1 in FP64.
+//           Chat sits in shared memory ([k-group][grain][2] float4, odd row
+//           stride), in grain chunks when it does not fit, as the paper staged
+//           sigma per block (Section 4.4);
+//  resid    sum_k w_k L[c,k] / (4 pi sum_g n Pe) - 1.  Both sums are kept in
+//           float-float (error-free FP32 products and two-sums, ~48-bit) up to
+//           one FP64 combination per cell: this GPU's FP64 pipe is far too
+//           slow for per-term FP64.  Every reduction has a fixed order, so
+//           results depend neither on the batch nor on timing.
 #include "dust_internal.cuh"
+
+#include <algorithm>
 
 namespace dust {
 namespace {
 
 constexpr int NTH = 256;
+constexpr int R = 2;    // phase-2 work items per thread
+constexpr int NB = 4;   // solves in flight per thread in phase 1
 constexpr double FOUR_PI = 12.566370614359172954;
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -37,285 +50,409 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// (h, l) += (a, b) in float-float (two-sum of the high parts).
+__device__ __forceinline__ void ff_add(float &h, float &l, float a, float b) {
+    const float t = h + a, bp = t - h;
+    l += ((h - (t - bp)) + (a - bp)) + b;
+    h = t;
+}
+
 // Cubic Hermite on [0,1] with end values p0, p1 and end slopes d0, d1.
 __device__ __forceinline__ float hermite(float p0, float d0, float p1, float d1, float x) {
-    float d = p1 - p0;
-    float c2 = 3.f * d - 2.f * d0 - d1;
-    float c3 = d0 + d1 - 2.f * d;
+    const float d = p1 - p0;
+    const float c2 = 3.f * d - 2.f * d0 - d1;
+    const float c3 = d0 + d1 - 2.f * d;
     return p0 + x * (d0 + x * (c2 + x * c3));
 }
 
-// Equilibrium temperature of grain g for scaled absorbed power s (see above).
-__device__ __forceinline__ float solve_T(const DevTables &tb, int g, float s, int &flag) {
-    const float4 gq = __ldg(reinterpret_cast<const float4 *>(tb.gp) + g);  // f, tmax, invdy
-    if (!(s >= 0.f) || isinf(s)) { flag = DUST_FLAG_INVALID; return __int_as_float(0x7fc00000); }
-    if (s == 0.f) { flag = DUST_FLAG_LOW; return tb.Tmin; }
-    const float y = log2f(s) + gq.x;
-    if (y < 0.f) { flag = DUST_FLAG_LOW; return tb.Tmin; }
-    if (y > gq.y) { flag = DUST_FLAG_HIGH; return tb.Tmax; }
-    flag = DUST_FLAG_OK;
-    // initial guess u(y) from the inverse table
-    const float fy = y * gq.z;
-    const int m = min((int)fy, tb.NI - 2);
-    const float ty = fminf(fy - (float)m, 1.f);
-    const float4 iv = __ldg(tb.inv + (size_t)g * (tb.NI - 1) + m);
-    const float ug = hermite(iv.x, iv.y, iv.z, iv.w, ty);
-    const float fj = (ug - tb.log2Tmin) / tb.h2;
-    int j = min(max((int)floorf(fj), 0), tb.NT - 2);
-    float tau = fminf(fmaxf(fj - (float)j, 0.f), 1.f);
-    // bracketing interval t_j <= y <= t_j+1
-    const float4 *fwg = tb.fw + (size_t)g * (tb.NT - 1);
-    float4 f4 = __ldg(fwg + j);
-    for (int a = 0; a < 4; ++a) {
-        if (y < f4.x && j > 0) { --j; tau = 1.f; }
-        else if (y > f4.z && j < tb.NT - 2) { ++j; tau = 0.f; }
-        else break;
-        f4 = __ldg(fwg + j);
+// Equilibrium temperatures of NB grains at once (independent loads in
+// flight together).  s: scaled absorbed power (A / P_g(T_min) = s 2^f_g).
+__device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[NB], const bool (&ok)[NB],
+                                            const float (&s)[NB], const float4 (&gq)[NB], float (&T)[NB],
+                                            int (&fl)[NB]) {
+    float y[NB], ty[NB];
+    int m[NB];
+    bool act[NB];
+    float4 iv[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        act[i] = false;
+        fl[i] = DUST_FLAG_OK;
+        T[i] = tb.Tmin;
+        y[i] = 0.f;
+        m[i] = 0;
+        ty[i] = 0.f;
+        if (!ok[i]) continue;
+        if (!(s[i] >= 0.f) || isinf(s[i])) { fl[i] = DUST_FLAG_INVALID; T[i] = __int_as_float(0x7fc00000); continue; }
+        if (s[i] == 0.f) { fl[i] = DUST_FLAG_LOW; continue; }
+        y[i] = log2f(s[i]) + gq[i].x;
+        if (y[i] < 0.f) { fl[i] = DUST_FLAG_LOW; continue; }
+        if (y[i] > gq[i].y) { fl[i] = DUST_FLAG_HIGH; T[i] = tb.Tmax; continue; }
+        act[i] = true;
+        const float fy = y[i] * gq[i].z;
+        m[i] = min((int)fy, tb.NI - 2);
+        ty[i] = fminf(fy - (float)m[i], 1.f);
     }
-    // Newton on the Hermite cubic q(tau) = t(u_j + tau h2) - t_j = y - t_j
-    const float r = y - f4.x, d = f4.z - f4.x, m0 = f4.y, m1 = f4.w;
-    const float c2 = 3.f * d - 2.f * m0 - m1, c3 = m0 + m1 - 2.f * d;
-    float lo = 0.f, hi = 1.f;
-    for (int it = 0; it < 4; ++it) {
-        const float q = tau * (m0 + tau * (c2 + tau * c3)) - r;
-        const float dq = m0 + tau * (2.f * c2 + 3.f * tau * c3);
-        if (q < 0.f) lo = tau; else hi = tau;
-        float nt = tau - q / dq;
-        if (!(nt >= lo && nt <= hi)) nt = 0.5f * (lo + hi);  // bracketed fallback
-        const float step = fabsf(nt - tau);
-        tau = nt;
-        if (step * tb.h2 < 2e-7f) break;
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+        iv[i] = act[i] ? __ldg(tb.inv + (size_t)g[i] * (tb.NI - 1) + m[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    int j[NB];
+    float tau[NB], tn[NB];
+    float4 f4[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const float ug = hermite(iv[i].x, iv[i].y, iv[i].z, iv[i].w, ty[i]);
+        const float fj = (ug - tb.log2Tmin) / tb.h2;
+        j[i] = min(max((int)floorf(fj), 0), tb.NT - 2);
+        tau[i] = fminf(fmaxf(fj - (float)j[i], 0.f), 1.f);
     }
-    return __ldg(tb.Tnode + j) * exp2f(tau * tb.h2);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        f4[i] = act[i] ? __ldg(tb.fw + (size_t)g[i] * (tb.NT - 1) + j[i]) : make_float4(0.f, 1.f, 1.f, 1.f);
+        tn[i] = act[i] ? __ldg(tb.Tnode + j[i]) : 1.f;
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        if (!act[i]) continue;
+        // bracketing interval t_j <= y <= t_j+1 (the guess is almost always right)
+        for (int a = 0; a < 4; ++a) {
+            if (y[i] < f4[i].x && j[i] > 0) { --j[i]; tau[i] = 1.f; }
+            else if (y[i] > f4[i].z && j[i] < tb.NT - 2) { ++j[i]; tau[i] = 0.f; }
+            else break;
+            f4[i] = __ldg(tb.fw + (size_t)g[i] * (tb.NT - 1) + j[i]);
+            tn[i] = __ldg(tb.Tnode + j[i]);
+        }
+        // Newton on the Hermite cubic q(tau) = t(u_j + tau h2) - t_j = y - t_j
+        const float r = y[i] - f4[i].x, d = f4[i].z - f4[i].x, m0 = f4[i].y, m1 = f4[i].w;
+        const float c2 = 3.f * d - 2.f * m0 - m1, c3 = m0 + m1 - 2.f * d;
+        float lo = 0.f, hi = 1.f, t = tau[i];
+        for (int it = 0; it < 4; ++it) {
+            const float q = t * (m0 + t * (c2 + t * c3)) - r;
+            const float dq = m0 + t * (2.f * c2 + 3.f * t * c3);
+            if (q < 0.f) lo = t; else hi = t;
+            float nt = t - q / dq;
+            if (!(nt >= lo && nt <= hi)) nt = 0.5f * (lo + hi);  // bracketed fallback
+            const float step = fabsf(nt - t);
+            t = nt;
+            if (step * tb.h2 < 2e-7f) break;
+        }
+        T[i] = tn[i] * exp2f(t * tb.h2);
+    }
 }
 
-template <int R, bool EMIT, bool RESID, bool STORE_L>
-__global__ void __launch_bounds__(NTH, 2)
-k_solve_emit(DevTables tb, int64_t C, int TC, int GC, int chat_resident, const float *__restrict__ S,
-             const float *__restrict__ n, float *__restrict__ T, float *__restrict__ L, int64_t ld,
-             double *__restrict__ resid, uint8_t *__restrict__ flags) {
+__device__ __forceinline__ void emit_pair(float2 nax, float2 iT, float2 nn, float2 cw, float2 &N, float2 &D) {
+    const float2 a = __fmul2_rn(nax, iT);
+    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+    const float2 w = __fmul2_rn(nn, cw);
+    const float2 e = make_float2(fmaf(w.x, D.x, -N.x), fmaf(w.y, D.y, -N.y));
+    N = __ffma2_rn(t, e, N);
+    D = make_float2(fmaf(-t.x, D.x, D.x), fmaf(-t.y, D.y, D.y));
+}
+
+__global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ EmitBatch B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int G = tb.G, NKG = tb.NKG, K = tb.K, Gs = tb.Gs;
-    const int TNS = 2 * G + 2;  // floats per cell row of (1/T, n 2^-m) pairs
-    float4 *sC = reinterpret_cast<float4 *>(smem_raw);
-    float *sTN = reinterpret_cast<float *>(sC + (EMIT ? (size_t)GC * 2 * NKG : 0));
-    int *sM = reinterpret_cast<int *>(sTN + (size_t)TC * TNS);
-    double *sAbs = reinterpret_cast<double *>(sM + ((TC + 1) & ~1));
-    double *sEm = sAbs + TC;
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t ntiles = (C + TC - 1) / TC;
 
-    // phase-2 work items of this thread (fixed across tiles)
+    int cur = -1;
+    // per-request shared-memory layout (byte offsets) and thread state
+    int oTN = 0, oS = 0, oN = 0, oM = 0, oAbs = 0, oEm = 0;
+    int TNS = 0, CST = 0;
     int icell[R], ikg[R];
-    float nax[R][KQ];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        int it = r * NTH + tid;
-        bool ok = it < TC * NKG;
-        icell[r] = ok ? it / NKG : -1;
-        ikg[r] = ok ? it % NKG : 0;
-#pragma unroll
-        for (int q = 0; q < KQ; ++q) nax[r][q] = EMIT ? __ldg(tb.nax + ikg[r] * KQ + q) : 0.f;
-    }
 
-    if (EMIT && chat_resident) {
-        const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
-        for (int i = tid; i < G * 2 * NKG; i += NTH) sC[i] = __ldg(src + i);
-    }
-
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t c0 = tile * TC;
-        const int nc = (int)((C - c0) < (int64_t)TC ? (C - c0) : (int64_t)TC);
+    for (int64_t tile = blockIdx.x; tile < B.ntiles; tile += gridDim.x) {
+        int ri = cur < 0 ? 0 : cur;
+        while (ri + 1 < B.nreq && tile >= B.req[ri + 1].tile_begin) ++ri;
+        const EmitReq &q = B.req[ri];
+        const DevTables &tb = q.tb;
+        const int G = tb.G, G8 = tb.G8, NKG = tb.NKG, K = tb.K, Gs = tb.Gs, TC = q.TC;
+        const bool emit = (q.mode & EMIT_ON) != 0, rs = (q.mode & EMIT_RESID) != 0;
+        if (ri != cur) {
+            TNS = 2 * G8 + 2;
+            CST = 2 * (q.resident ? G8 : q.GC) + 1;
+            __syncthreads();  // the previous request is done with shared memory
+            cur = ri;
+            oTN = emit ? NKG * CST * 16 : 0;
+            oS = oTN + (TC + 1) * TNS * 4;
+            oN = oS + TC * G8 * 4;
+            oM = oN + TC * G8 * 4;
+            oAbs = oM + ((TC + 1) & ~1) * 4;
+            oEm = oAbs + TC * 8;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int it = r * NTH + tid;
+                const bool okit = it < TC * NKG;
+                icell[r] = okit ? it / NKG : TC;  // idle items read the dummy row TC
+                ikg[r] = okit ? it % NKG : 0;
+            }
+            float *dummy = reinterpret_cast<float *>(smem_raw + oTN) + (size_t)TC * TNS;
+            for (int g = tid; g < G8; g += NTH)
+                *reinterpret_cast<float2 *>(dummy + 2 * g) = make_float2(1.f / tb.Tmax, 0.f);
+            if (emit && q.resident) {
+                const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
+                float4 *dst = reinterpret_cast<float4 *>(smem_raw);
+                for (int i = tid; i < NKG * 2 * G8; i += NTH) {
+                    const int kg = i / (2 * G8), o = i - kg * 2 * G8;
+                    dst[(size_t)kg * CST + o] = __ldg(src + i);
+                }
+            }
+        }
+        float4 *sC = reinterpret_cast<float4 *>(smem_raw);
+        float *sTN = reinterpret_cast<float *>(smem_raw + oTN);
+        float *sS = reinterpret_cast<float *>(smem_raw + oS);
+        float *sN = reinterpret_cast<float *>(smem_raw + oN);
+        int *sM = reinterpret_cast<int *>(smem_raw + oM);
+        double *sAbs = reinterpret_cast<double *>(smem_raw + oAbs);
+        float2 *sEm = reinterpret_cast<float2 *>(smem_raw + oEm);
+        const int64_t c0 = (tile - q.tile_begin) * TC;
+        const int nc = (int)((q.C - c0) < (int64_t)TC ? (q.C - c0) : (int64_t)TC);
+        const int npair = TC * G8;
         __syncthreads();  // previous tile finished with shared memory
-        // phases 0 + 1, one warp per cell: exponent of max_g n, then the
-        // temperatures (lanes over grains); the absorbed power of the residual
-        // is reduced in a fixed order so that results do not depend on timing
+        // ---- load S and n of the tile (coalesced; padding grains read as 0)
+        for (int i = tid; i < npair; i += NTH) {
+            const int c = i / G8, g = i - c * G8;
+            const bool okv = c < nc && g < G;
+            sS[i] = okv ? __ldg(q.S + (c0 + c) * Gs + g) : 0.f;
+            sN[i] = okv ? __ldg(q.n + (c0 + c) * G + g) : 0.f;
+        }
+        __syncthreads();
+        // ---- phase 0: per-cell exponent of max_g n
         for (int c = warp; c < TC; c += NTH / 32) {
-            const int64_t cell = c0 + c;
             float mx = 0.f;
-            if (c < nc)
-                for (int g = lane; g < G; g += 32) mx = fmaxf(mx, __ldg(n + cell * G + g));
+            for (int g = lane; g < G8; g += 32) mx = fmaxf(mx, sN[c * G8 + g]);
             for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             int mc = 0;
             if (mx > 0.f && mx < INFINITY) frexpf(mx, &mc);
-            double ab = 0.0;
-            for (int g = lane; g < G; g += 32) {
-                float invT = 1.f / tb.Tmax, nn = 0.f;
-                if (c < nc) {
-                    const float s = __ldg(S + cell * Gs + g);
-                    const float nv = __ldg(n + cell * G + g);
-                    int flag;
-                    const float Tv = solve_T(tb, g, s, flag);
-                    T[cell * G + g] = Tv;
-                    if (flags) flags[cell * G + g] = (uint8_t)flag;
-                    invT = __frcp_rn(Tv);
-                    nn = scale2(nv, -mc);
-                    if (RESID) {
-                        double pe = flag == DUST_FLAG_OK ? (double)s * __ldg(tb.gscale + g)
-                                  : flag == DUST_FLAG_LOW ? __ldg(tb.P0 + g)
-                                  : flag == DUST_FLAG_HIGH ? __ldg(tb.Pmax + g)
-                                  : (double)__int_as_float(0x7fc00000);
-                        ab = fma((double)nv, pe, ab);
+            if (lane == 0) sM[c] = mc;
+        }
+        __syncthreads();
+        // ---- phase 1: temperatures, NB pairs per thread per round
+        for (int p0 = 0; p0 < npair; p0 += NTH * NB) {
+            int gi[NB], pi[NB], ci[NB];
+            bool ok[NB];
+            float s[NB], nv[NB], Tv[NB];
+            float4 gq[NB];
+            int fl[NB];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                pi[i] = p0 + tid + NTH * i;
+                const bool in = pi[i] < npair;
+                ci[i] = in ? pi[i] / G8 : 0;
+                gi[i] = in ? pi[i] - ci[i] * G8 : 0;
+                ok[i] = in && ci[i] < nc && gi[i] < G;
+                s[i] = in ? sS[pi[i]] : 0.f;
+                nv[i] = in ? sN[pi[i]] : 0.f;
+                gq[i] = ok[i] ? __ldg(reinterpret_cast<const float4 *>(tb.gp) + gi[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (!ok[i]) gi[i] = 0;
+            }
+            solve_batch(tb, gi, ok, s, gq, Tv, fl);
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                if (pi[i] >= npair) continue;
+                const int c = ci[i], g = pi[i] - c * G8;
+                float invT = 1.f / tb.Tmax, nn = 0.f, rh = 0.f, rl = 0.f;
+                if (ok[i]) {
+                    const int64_t cell = c0 + c;
+                    q.T[cell * G + g] = Tv[i];
+                    if (q.flags) q.flags[cell * G + g] = (uint8_t)fl[i];
+                    invT = __frcp_rn(Tv[i]);
+                    nn = scale2(nv[i], -sM[c]);
+                    if (rs) {
+                        // n 2^-m_c Pe 2^-Eg in float-float, Pe = s gscale (or the clamp powers)
+                        const float4 gr = __ldg(tb.gres + g);
+                        const float se = fl[i] == DUST_FLAG_OK ? s[i]
+                                       : fl[i] == DUST_FLAG_LOW ? gr.z
+                                       : fl[i] == DUST_FLAG_HIGH ? gr.w : __int_as_float(0x7fc00000);
+                        const float xh = nn * se, xl = fmaf(nn, se, -xh);
+                        rh = xh * gr.x;
+                        rl = fmaf(xh, gr.x, -rh) + fmaf(xh, gr.y, xl * gr.x);
                     }
                 }
-                if (EMIT) *reinterpret_cast<float2 *>(sTN + (size_t)c * TNS + 2 * g) = make_float2(invT, nn);
-            }
-            if (RESID)
-                for (int o = 16; o; o >>= 1) ab += __shfl_xor_sync(0xffffffffu, ab, o);
-            if (lane == 0) {
-                sM[c] = mc;
-                if (RESID) sAbs[c] = ab;
+                if (emit) *reinterpret_cast<float2 *>(sTN + (size_t)c * TNS + 2 * g) = make_float2(invT, nn);
+                if (rs) { sS[pi[i]] = rh; sN[pi[i]] = rl; }  // this thread's own slots
             }
         }
-        if (!EMIT) continue;
         __syncthreads();
-        // phase 2: emission
-        float acc[R][KQ], N[R][KQ], D[R][KQ];
+        // absorbed power per cell, reduced over grains in a fixed order
+        if (rs) {
+            for (int c = warp; c < TC; c += NTH / 32) {
+                float h = 0.f, l = 0.f;
+                for (int g = lane; g < G8; g += 32) ff_add(h, l, sS[c * G8 + g], sN[c * G8 + g]);
+                for (int o = 16; o; o >>= 1) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+                    ff_add(h, l, oh, ol);
+                }
+                if (lane == 0) sAbs[c] = ldexp((double)h + (double)l, sM[c] + tb.Eg);
+            }
+        }
+        if (!emit) continue;
+        // ---- phase 2: emission
+        float2 acc[R][4], nax2[R][4];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int q = 0; q < KQ; ++q) acc[r][q] = 0.f;
-        for (int g0 = 0; g0 < G; g0 += GC) {
-            const int gn = min(GC, G - g0);
-            if (!chat_resident) {
-                __syncthreads();
-                const float4 *src = reinterpret_cast<const float4 *>(tb.Chat) + (size_t)g0 * 2 * NKG;
-                for (int i = tid; i < gn * 2 * NKG; i += NTH) sC[i] = __ldg(src + i);
-                __syncthreads();
+            for (int p = 0; p < 4; ++p) {
+                acc[r][p] = make_float2(0.f, 0.f);
+                nax2[r][p] = __ldg(reinterpret_cast<const float2 *>(tb.nax + ikg[r] * KQ) + p);
             }
-            const float4 *cbase = chat_resident ? sC + (size_t)g0 * 2 * NKG : sC;
+        const int GC = q.resident ? G8 : q.GC;
+        for (int g0 = 0; g0 < G8; g0 += GC) {
+            const int gn = min(GC, G8 - g0);
+            if (!q.resident) {
+                __syncthreads();
+                const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
+                for (int i = tid; i < NKG * 2 * gn; i += NTH) {
+                    const int kg = i / (2 * gn), o = i - kg * 2 * gn;
+                    sC[(size_t)kg * CST + o] = __ldg(src + ((size_t)kg * G8 + g0) * 2 + o);
+                }
+            }
+            __syncthreads();
+            const int goff = q.resident ? g0 : 0;
             for (int gg0 = 0; gg0 < gn; gg0 += RG) {
+                const float2 *tnp[R];
+                const float4 *cp[R];
+                float2 N[R][4], D[R][4];
 #pragma unroll
-                for (int r = 0; r < R; ++r)
+                for (int r = 0; r < R; ++r) {
+                    tnp[r] = reinterpret_cast<const float2 *>(sTN + (size_t)icell[r] * TNS) + g0 + gg0;
+                    cp[r] = sC + (size_t)ikg[r] * CST + 2 * (goff + gg0);
 #pragma unroll
-                    for (int q = 0; q < KQ; ++q) { N[r][q] = 0.f; D[r][q] = 1.f; }
+                    for (int p = 0; p < 4; ++p) { N[r][p] = make_float2(0.f, 0.f); D[r][p] = make_float2(1.f, 1.f); }
+                }
 #pragma unroll
                 for (int u = 0; u < RG; ++u) {
-                    const int gg = gg0 + u;
-                    if (gg < gn) {
 #pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            if (icell[r] < 0) continue;
-                            const float2 tn = *reinterpret_cast<const float2 *>(
-                                sTN + (size_t)icell[r] * TNS + 2 * (g0 + gg));
-                            const float4 ca = cbase[(gg * 2 + 0) * NKG + ikg[r]];
-                            const float4 cb = cbase[(gg * 2 + 1) * NKG + ikg[r]];
-                            const float cw[KQ] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
-#pragma unroll
-                            for (int q = 0; q < KQ; ++q) {
-                                const float t = ex2_approx(nax[r][q] * tn.x);
-                                const float wq = tn.y * cw[q];
-                                const float e = fmaf(wq, D[r][q], -N[r][q]);
-                                N[r][q] = fmaf(t, e, N[r][q]);
-                                D[r][q] = fmaf(-t, D[r][q], D[r][q]);
-                            }
-                        }
+                    for (int r = 0; r < R; ++r) {
+                        const float2 tn = tnp[r][u];
+                        const float4 ca = cp[r][2 * u], cb = cp[r][2 * u + 1];
+                        const float2 iT = make_float2(tn.x, tn.x), nn = make_float2(tn.y, tn.y);
+                        emit_pair(nax2[r][0], iT, nn, make_float2(ca.x, ca.y), N[r][0], D[r][0]);
+                        emit_pair(nax2[r][1], iT, nn, make_float2(ca.z, ca.w), N[r][1], D[r][1]);
+                        emit_pair(nax2[r][2], iT, nn, make_float2(cb.x, cb.y), N[r][2], D[r][2]);
+                        emit_pair(nax2[r][3], iT, nn, make_float2(cb.z, cb.w), N[r][3], D[r][3]);
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < R; ++r)
 #pragma unroll
-                    for (int q = 0; q < KQ; ++q) acc[r][q] = fmaf(N[r][q], rcp_approx(D[r][q]), acc[r][q]);
+                    for (int p = 0; p < 4; ++p) {
+                        acc[r][p].x = fmaf(N[r][p].x, rcp_approx(D[r][p].x), acc[r][p].x);
+                        acc[r][p].y = fmaf(N[r][p].y, rcp_approx(D[r][p].y), acc[r][p].y);
+                    }
             }
         }
-        // epilogue: scale, store, residual partials
+        // ---- epilogue: scale, store, residual partials.  The 8-term partial
+        // sum_k w_k L_k of an item is accumulated error-free in float-float
+        // (products split by FMA, sums by two-sum).
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int c = icell[r];
-            if (c < 0 || c >= nc) continue;
+            if (c >= nc) continue;
             const int64_t cell = c0 + c;
             const int mc = sM[c];
-            double em = 0.0;
+            float sh = 0.f, sl = 0.f;
             const int kb = ikg[r] * KQ;
 #pragma unroll
-            for (int q = 0; q < KQ; ++q) {
-                const int k = kb + q;
-                if (k < K) {
-                    const float Lv = scale2(acc[r][q], mc + __ldg(tb.qexp + k));
-                    if (STORE_L) L[cell * ld + k] = Lv;
-                    if (RESID) em = fma(__ldg(tb.w + k), (double)Lv, em);
+            for (int p = 0; p < 4; ++p) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = kb + 2 * p + h;
+                    if (k < K) {
+                        const int qk = __ldg(tb.qexp + k);
+                        const float a = h ? acc[r][p].y : acc[r][p].x;
+                        const float Lv = scale2(a, mc + qk);
+                        if (q.mode & EMIT_STORE_L) q.L[cell * q.ld + k] = Lv;
+                        if (rs) {
+                            // w_k L_k 2^-(m_c + Ew) = wq_k a: the FP32 accumulator before
+                            // its power-of-two scaling (equal to the stored L unless L is subnormal)
+                            const float wk = __ldg(tb.wq + k);
+                            const float pr = wk * a;
+                            ff_add(sh, sl, pr, fmaf(wk, a, -pr));
+                        }
+                    }
                 }
             }
-            if (RESID) sEm[c * NKG + ikg[r]] = em;
+            if (rs) sEm[c * NKG + ikg[r]] = make_float2(sh, sl);
         }
-        if (RESID) {
+        if (rs) {
             __syncthreads();
             for (int c = tid; c < nc; c += NTH) {
-                double e = 0.0;
-                for (int kg = 0; kg < NKG; ++kg) e += sEm[c * NKG + kg];
-                resid[c0 + c] = e / (FOUR_PI * sAbs[c]) - 1.0;
+                float h = 0.f, l = 0.f;
+                for (int kg = 0; kg < NKG; ++kg) {
+                    const float2 v = sEm[c * NKG + kg];
+                    ff_add(h, l, v.x, v.y);
+                }
+                const double e = ldexp((double)h + (double)l, sM[c] + tb.Ew);
+                q.resid[c0 + c] = e / (FOUR_PI * sAbs[c]) - 1.0;
             }
         }
     }
-}
-
-struct Plan {
-    int R, TC, GC, resident;
-    size_t smem;
-};
-
-Plan make_plan(const dust_ctx *ctx, bool emit) {
-    const DevTables &tb = ctx->tb;
-    Plan p{};
-    p.R = 2;
-    if (tb.NKG > p.R * NTH) p.R = 4;
-    p.TC = emit ? (p.R * NTH) / tb.NKG : 64;
-    if (p.TC < 1) p.TC = 1;
-    if (p.TC > 64) p.TC = 64;
-    const size_t per_cta = (size_t)(ctx->smem_optin ? ctx->smem_optin : 101376);
-    const size_t budget = std::min<size_t>(per_cta, 110 * 1024);  // two CTAs per SM
-    auto fixed = [&](int TC) {  // sTN, sM, sAbs, sEm (per item)
-        return (size_t)TC * (2 * tb.G + 2) * 4 + (size_t)((TC + 1) & ~1) * 4 + (size_t)TC * 8 +
-               (size_t)TC * tb.NKG * 8 + 64;
-    };
-    const size_t per_grain = (size_t)2 * tb.NKG * 16;
-    if (!emit) { p.GC = 0; p.resident = 0; p.smem = fixed(p.TC); return p; }
-    size_t full = per_grain * tb.G + fixed(p.TC);
-    if (full <= budget) { p.GC = tb.G; p.resident = 1; p.smem = full; return p; }
-    size_t avail = budget > fixed(p.TC) ? budget - fixed(p.TC) : 0;
-    int gc = (int)(avail / per_grain) / RG * RG;
-    if (gc < RG) gc = RG;
-    p.GC = gc;
-    p.resident = 0;
-    p.smem = per_grain * gc + fixed(p.TC);
-    return p;
-}
-
-template <int R, bool EMIT, bool RESID, bool STORE_L>
-int launch_t(const dust_ctx *ctx, const Plan &p, int64_t C, const float *S, const float *n, float *T,
-             float *L, int64_t ld, double *resid, uint8_t *flags, cudaStream_t st) {
-    auto kern = k_solve_emit<R, EMIT, RESID, STORE_L>;
-    DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
-    int64_t ntiles = (C + p.TC - 1) / p.TC;
-    int blocks_per_sm = 0;
-    DUST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, NTH, p.smem));
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-    int64_t grid = std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * blocks_per_sm);
-    kern<<<(unsigned)grid, NTH, p.smem, st>>>(ctx->tb, C, p.TC, p.GC, p.resident, S, n, T, L, ld, resid,
-                                              flags);
-    DUST_CUDA_TRY(cudaGetLastError());
-    return DUST_OK;
-}
-
-template <int R>
-int launch_r(const dust_ctx *ctx, const Plan &p, int64_t C, const float *S, const float *n, float *T,
-             float *L, int64_t ld, double *resid, uint8_t *flags, cudaStream_t st) {
-    const bool emit = L || resid;
-    if (!emit) return launch_t<R, false, false, false>(ctx, p, C, S, n, T, L, ld, resid, flags, st);
-    if (L && resid) return launch_t<R, true, true, true>(ctx, p, C, S, n, T, L, ld, resid, flags, st);
-    if (L) return launch_t<R, true, false, true>(ctx, p, C, S, n, T, L, ld, resid, flags, st);
-    return launch_t<R, true, true, false>(ctx, p, C, S, n, T, L, ld, resid, flags, st);
 }
 
 }  // namespace
 
-int launch_solve_emit(const dust_ctx *ctx, int64_t C, const float *S, const float *n, float *T,
-                      float *L, int64_t ld, double *resid, uint8_t *flags, cudaStream_t st) {
+// Work-list geometry of one request: cells per tile, grain chunk, residency
+// of the emission weights and the shared memory they need.
+EmitPlan plan_emit(const dust_ctx *ctx, bool emit) {
+    const DevTables &tb = ctx->tb;
+    EmitPlan p{};
+    p.TC = emit ? (R * NTH) / tb.NKG : 64;
+    p.TC = std::max(1, std::min(p.TC, 64));
+    const size_t budget = 113 * 1024;  // two CTAs per SM
+    auto fixed = [&](int TC) {  // sTN (+ dummy row), sS, sN, sM, sAbs, sEm
+        return (size_t)(TC + 1) * (2 * tb.G8 + 2) * 4 + (size_t)2 * TC * tb.G8 * 4 + (size_t)((TC + 1) & ~1) * 4 +
+               (size_t)TC * 8 + (size_t)TC * tb.NKG * 8 + 64;
+    };
+    if (!emit) { p.GC = tb.G8; p.resident = 0; p.smem = fixed(p.TC); return p; }
+    const size_t full = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + fixed(p.TC);
+    if (full <= budget) { p.GC = tb.G8; p.resident = 1; p.smem = full; return p; }
+    const size_t avail = budget > fixed(p.TC) ? budget - fixed(p.TC) : 0;
+    int gc = (int)((avail / ((size_t)tb.NKG * 16) - 1) / 2) / RG * RG;
+    gc = std::max(RG, std::min(gc, tb.G8));
+    p.GC = gc;
+    p.resident = 0;
+    p.smem = (size_t)tb.NKG * (2 * gc + 1) * 16 + fixed(p.TC);
+    return p;
+}
+
+int launch_emit_batch(const EmitBatch &B, size_t smem, int num_sms, cudaStream_t st) {
+    if (B.ntiles <= 0) return DUST_OK;
+    DUST_CUDA_TRY(cudaFuncSetAttribute(k_solve_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    DUST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_emit, NTH, smem));
+    per_sm = std::max(per_sm, 1);
+    const int64_t grid = std::min<int64_t>(B.ntiles, (int64_t)num_sms * per_sm);
+    k_solve_emit<<<(unsigned)grid, NTH, smem, st>>>(B);
+    DUST_CUDA_TRY(cudaGetLastError());
+    return DUST_OK;
+}
+
+void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const float *S, const float *n, float *T,
+                   float *L, int64_t ld, double *resid, uint8_t *flags, EmitReq &r) {
+    r.tb = ctx->tb;
+    r.C = C;
+    r.ld = ld;
+    r.S = S;
+    r.n = n;
+    r.T = T;
+    r.L = L;
+    r.resid = resid;
+    r.flags = flags;
+    r.TC = p.TC;
+    r.GC = p.GC;
+    r.resident = p.resident;
+    r.mode = ((L || resid) ? EMIT_ON : 0) | (resid ? EMIT_RESID : 0) | (L ? EMIT_STORE_L : 0);
+}
+
+int launch_solve_emit(const dust_ctx *ctx, int64_t C, const float *S, const float *n, float *T, float *L,
+                      int64_t ld, double *resid, uint8_t *flags, cudaStream_t st) {
     if (C <= 0) return DUST_OK;
-    Plan p = make_plan(ctx, L || resid);
-    if (p.R == 2) return launch_r<2>(ctx, p, C, S, n, T, L, ld, resid, flags, st);
-    return launch_r<4>(ctx, p, C, S, n, T, L, ld, resid, flags, st);
+    const EmitPlan p = plan_emit(ctx, L || resid);
+    EmitBatch B;
+    B.nreq = 1;
+    fill_emit_req(ctx, p, C, S, n, T, L, ld, resid, flags, B.req[0]);
+    B.req[0].tile_begin = 0;
+    B.ntiles = (C + p.TC - 1) / p.TC;
+    return launch_emit_batch(B, p.smem, ctx->num_sms, st);
 }
 
 }  // namespace dust

@@ -76,6 +76,21 @@ def test_null_arguments(L):
     L.dust_ctx_destroy(None)
 
 
+def test_server_null_arguments(L):
+    assert L.dust_server_create(None, 1 << 30, 4, 0) == _lib.DUST_EINVAL
+    out = ctypes.c_void_p()
+    assert L.dust_server_create(ctypes.byref(out), 1000, 4, 0) == _lib.DUST_EINVAL  # budget < 1 MiB
+    assert L.dust_server_create(ctypes.byref(out), 1 << 30, 0, 0) == _lib.DUST_EINVAL
+    t = ctypes.c_uint64()
+    assert L.dust_serve_submit(None, None, 1, None, 4, None, None, None, None, None, ctypes.byref(t)) == \
+        _lib.DUST_EINVAL
+    assert L.dust_serve_poll(None, 1, None, None) == _lib.DUST_EINVAL
+    assert L.dust_serve_wait(None, 1, 1.0, None) == _lib.DUST_EINVAL
+    assert L.dust_serve_cancel(None, 1) == _lib.DUST_EINVAL
+    assert L.dust_server_stats(None, None) == _lib.DUST_EINVAL
+    L.dust_server_destroy(None)
+
+
 def test_python_wrapper_raises(L):
     with pytest.raises(_lib.DustError) as e:
         _lib.dust_ctx_create(1, 0, 0, 1, 0, 2.0, 3000.0, 0, 0, 0)

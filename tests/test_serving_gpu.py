@@ -1,0 +1,136 @@
+"""Serving (continuous batching) on the GPU: every request's result is bitwise
+the result of solving it alone, whatever else shares its rounds; admission
+respects the HBM budget; cancellation and error paths behave."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+
+
+def _request_data(K, G, C, snapshot):
+    cfg = synth.workloads.serve_snapshot_config(snapshot, K, G, max(C, 8))
+    wl = synth.make_workload(cfg, cells=np.arange(C))
+    return wl
+
+
+def _padded(J):
+    from paper_0907_3768_gb300 import padded_rows
+
+    return padded_rows(torch.from_numpy(J).cuda())
+
+
+def _mix():
+    """Requests over three grids / grain sets and all three precisions."""
+    from paper_0907_3768_gb300 import Context
+
+    shapes = [(100, 48, "bf16x3"), (350, 96, "fp32"), (500, 240, "fp16x3"), (200, 96, "bf16x3")]
+    ctxs, reqs = {}, []
+    rng = np.random.default_rng(11)
+    for i in range(10):
+        K, G, prec = shapes[i % len(shapes)]
+        C = int(np.exp(rng.uniform(np.log(300), np.log(40000))))
+        wl = _request_data(K, G, C, snapshot=i % 5)
+        key = (K, G, prec, i % 5)
+        if key not in ctxs:
+            ctxs[key] = Context.from_workload(wl, precision=prec)
+        reqs.append((ctxs[key], _padded(wl.J), torch.from_numpy(wl.n).cuda()))
+    return ctxs, reqs
+
+
+def test_results_identical_alone_and_in_the_mix():
+    from paper_0907_3768_gb300 import Server
+
+    ctxs, reqs = _mix()
+    alone = []
+    for ctx, J, n in reqs:
+        out = ctx.solve(J, n)
+        torch.cuda.synchronize()
+        alone.append({k: v.clone() for k, v in out.items() if k in ("T", "L", "resid", "flags")})
+    with Server(hbm_budget_bytes=8 << 30, max_inflight=6) as srv:
+        tickets = [ctx.submit(srv, J, n) for ctx, J, n in reqs]
+        for t, _ in tickets:
+            srv.wait(t, 60000.0)
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["rounds"] >= 1 and st["p99_ms"] >= st["p50_ms"] > 0.0
+    for (t, out), ref in zip(tickets, alone):
+        for k in ("T", "L", "resid", "flags"):
+            assert torch.equal(out[k], ref[k]), k
+    for c in ctxs.values():
+        assert c.check() == 0
+        c.close()
+
+
+def test_admission_by_footprint_and_ebusy():
+    from paper_0907_3768_gb300 import DustError, Server, _lib
+
+    ctxs, reqs = _mix()
+    # budget for roughly one large request at a time: all still complete
+    with Server(hbm_budget_bytes=600 << 20, max_inflight=32) as srv:
+        ok = []
+        for ctx, J, n in reqs:
+            try:
+                ok.append(ctx.submit(srv, J, n))
+            except DustError as e:
+                assert e.code == _lib.DUST_EBUSY
+        for t, _ in ok:
+            srv.wait(t, 60000.0)
+        st = srv.stats()
+        assert st["completed"] == len(ok) and st["hbm_in_use"] == 0
+    # a request larger than the whole budget can never be admitted
+    ctx, J, n = reqs[-1]
+    with Server(hbm_budget_bytes=1 << 20, max_inflight=2) as srv:
+        with pytest.raises(DustError) as e:
+            ctx.submit(srv, J, n)
+        assert e.value.code == _lib.DUST_EBUSY
+    for c in ctxs.values():
+        c.close()
+
+
+def test_cancel_poll_and_unknown_tickets():
+    from paper_0907_3768_gb300 import DustError, Server, _lib
+
+    ctxs, reqs = _mix()
+    with Server(hbm_budget_bytes=8 << 30, max_inflight=1) as srv:
+        subs = [ctx.submit(srv, J, n) for ctx, J, n in reqs[:4]]
+        srv.cancel(subs[-1][0])           # still queued behind max_inflight = 1
+        for t, _ in subs[:3]:
+            srv.wait(t, 60000.0)
+        state, _ = srv.poll(subs[-1][0])
+        assert state == "cancelled"
+        with pytest.raises(DustError) as e:
+            srv.poll(subs[0][0])          # released by its wait
+        assert e.value.code == _lib.DUST_ENOTFOUND
+        st = srv.stats()
+        assert st["completed"] == 3 and st["cancelled"] == 1
+    for c in ctxs.values():
+        c.close()
+
+
+def test_zero_cell_request_and_shutdown_with_queue():
+    from paper_0907_3768_gb300 import Server
+
+    ctxs, reqs = _mix()
+    ctx, J, n = reqs[0]
+    srv = Server(hbm_budget_bytes=8 << 30, max_inflight=2)
+    t0, _ = ctx.submit(srv, J[:0], n[:0])
+    assert srv.poll(t0)[0] == "done"
+    for ctx, J, n in reqs:
+        ctx.submit(srv, J, n)
+    srv.close()                          # finishes admitted requests, cancels the rest
+    torch.cuda.synchronize()
+    for c in ctxs.values():
+        assert c.check() == 0
+        c.close()
