@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2^20-cell, K=500, G=240 solve")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-load", type=float, default=0.7, help="arrival rate / saturated throughput")
     return ap.parse_args()
@@ -282,9 +283,12 @@ def run_ours(args):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], line["err_vs_oracle"] = cpu_baseline(args, wl, res)
-    if not args.no_serving:
-        del out_main, res, Jbuf, J, n
+    del out_main, res, Jbuf, J, n
+    torch.cuda.empty_cache()
+    if not args.no_large:
+        line["large"] = run_large(args, dev, local, ex2_rate)
         torch.cuda.empty_cache()
+    if not args.no_serving:
         line["serving"] = run_serving(args, dev, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -348,6 +352,65 @@ def cpu_baseline(args, wl_full, res):
                    "resid_max": float(np.abs(rs).max()), "flags_equal": bool((fl == ref["flags"]).all()),
                    "cells": nc}
     return base, errs
+
+
+# ------------------------------------------------------------------ large solve
+def run_large(args, dev, local, ex2_rate):
+    """The 2^20-cell, 500-wavelength, 240-grain solve (10 % near-opaque cells):
+    full-path and temperature-only times per precision, with the per-kernel
+    split and the rooflines of both kernels."""
+    import json as _json  # noqa: F401
+    import torch
+
+    import synth
+    from paper_0907_3768_gb300 import Context, _lib
+
+    wl = synth.make_workload(3)
+    C, K, G = wl.n_cells_total, wl.K, wl.G
+    ld = (K + 3) // 4 * 4
+    Jb = torch.zeros((C, ld), dtype=torch.float32, device=dev)
+    Jb[:, :K] = torch.from_numpy(wl.J).to(dev)
+    J, n = Jb[:, :K], torch.from_numpy(wl.n).to(dev)
+    del wl
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "2^20 cells x 500 wavelengths (0.05-2000 um) x 240 grains, 10% near-opaque cells"}
+    steps = max(3, min(args.steps, 10))
+    for prec in ("bf16x3", "fp32"):
+        ctx = Context.from_workload(synth.make_workload(3, cells=[0]), precision=prec, device=local)
+        r = {}
+        for mode, wantL in (("full", True), ("T_only", False)):
+            o = ctx.alloc_outputs(C, ld, wantL, wantL, True)
+            for _ in range(2):
+                ctx.solve(J, n, out=o, stream=stream)
+            torch.cuda.synchronize()
+            _lib.dust_ctx_profile_read(ctx.handle)
+            _lib.dust_ctx_profile(ctx.handle, True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.solve(J, n, out=o, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            a, b, cnt = _lib.dust_ctx_profile_read(ctx.handle)
+            _lib.dust_ctx_profile(ctx.handle, False)
+            ms = e0.elapsed_time(e1) / steps
+            r[mode] = {"ms_step": round(ms, 4), "ms_absorb": round(a / cnt, 4), "ms_solve_emit": round(b / cnt, 4),
+                       "solves_per_s": C * G / (ms * 1e-3), "sed_cells_per_s": C / (ms * 1e-3) if wantL else None}
+            del o
+        assert ctx.check() == 0
+        ctx.close()
+        ms_a, ms_b = r["full"]["ms_absorb"], r["full"]["ms_solve_emit"]
+        r["roofline_solve_emit"] = {"bound": "alu", "unit": "G Planck terms/s",
+                                    "achieved": round(C * G * K / (ms_b * 1e-3) / 1e9, 1),
+                                    "peak": round(ex2_rate / 1e9, 1),
+                                    "frac": round(C * G * K / (ms_b * 1e-3) / ex2_rate, 4)}
+        gbytes = (C * K * 4 + C * ((G + 15) // 16 * 16) * 4) / 1e9
+        r["roofline_absorb"] = {"bound": "hbm", "unit": "GB/s", "achieved": round(gbytes / (ms_a * 1e-3), 1),
+                                "peak": 6684.8, "frac": round(gbytes / (ms_a * 1e-3) / 6684.8, 4),
+                                "tensor_TFLOPs_executed": round((3 if prec != "fp32" else 1) * 2 * C * G * K /
+                                                                (ms_a * 1e-3) / 1e12, 1)}
+        out[prec] = r
+    return out
 
 
 # ------------------------------------------------------------------ serving

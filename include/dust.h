@@ -71,7 +71,7 @@ enum dust_flag {
 
 /* Create a context for one wavelength grid and one set of grains on `device`.
  *
- *  K, lambda[K], w[K]  host FP64, 2 <= K <= 4096: wavelengths (strictly increasing, > 0) and
+ *  K, lambda[K], w[K]  host FP64, 2 <= K <= 2048: wavelengths (strictly increasing, > 0) and
  *                      quadrature weights (>= 0) such that sum_k w_k f(lambda_k)
  *                      approximates the integral over wavelength (the paper's
  *                      Delta lambda_l, Eqs. 6-8).

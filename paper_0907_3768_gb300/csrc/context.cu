@@ -431,7 +431,7 @@ int dust_ctx_create(dust_ctx **out, int K, const double *lambda, const double *w
     if (!out) return set_error(DUST_EINVAL, "out is NULL");
     *out = nullptr;
     if (!lambda || !w || !c_abs) return set_error(DUST_EINVAL, "lambda, w and c_abs must be non-NULL");
-    if (K < 2 || K > 4096) return set_error(DUST_EINVAL, "K=%d outside [2, 4096]", K);
+    if (K < 2 || K > 2048) return set_error(DUST_EINVAL, "K=%d outside [2, 2048]", K);
     if (G < 1 || G > 512) return set_error(DUST_EINVAL, "G=%d outside [1, 512]", G);
     if (!(T_min > 0.0) || !(T_max > T_min) || !std::isfinite(T_max))
         return set_error(DUST_EINVAL, "need 0 < T_min < T_max < inf");

@@ -101,7 +101,7 @@ struct TcBatch {
     TcReq req[MAXREQ];
     int nreq;
     int64_t ntiles;
-    int GsMax, ns1, ns2, tmem_cols, off_exp, j_off;
+    int GsMax, ns1, ns2, tmem_cols, nacc, off_exp, j_off;
     int *status;
 };
 

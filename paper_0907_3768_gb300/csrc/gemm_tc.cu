@@ -4,22 +4,26 @@
 // in tensor memory).  The paper's kernel 2 (Section 4.2) is the same matrix
 // product on CUDA cores in FP32.
 //
-// One persistent CTA per SM walks 128-cell tiles.  Warp roles:
-//   warp 0      TMA producer: FP32 tiles of J (128 cells x 32 wavelengths,
-//               128-byte swizzle) into a ring of staging buffers, and the
-//               pre-split 16-bit W chunk images (bulk copies) next to the
-//               converted A operand.
-//   warp 1      owns the TMEM accumulator (128 lanes x Gs columns FP32) and
-//               issues tcgen05.mma from one thread.
-//   warps 2-5   one thread per cell row: per-cell power-of-two exponent of
+// One persistent CTA per SM walks 128-cell tiles of a work list of requests.
+// Warp roles:
+//   warp 0      J producer: FP32 tiles of J (128 cells x 32 wavelengths,
+//               128-byte swizzle) by TMA into a ring of staging buffers; it
+//               runs as far ahead as that ring allows.
+//   warp 1      owns tensor memory (two accumulators of 128 lanes x Gs FP32
+//               columns when they fit) and issues tcgen05.mma from one thread.
+//   warp 2      W producer: the pre-split 16-bit W chunk of each K step by a
+//               bulk copy next to the converted A operand.
+//   warps 3-6   one thread per cell row: per-cell power-of-two exponent of
 //               max_k J[c,k] (first pass over the tile, FP16 only: J spans
-//               ~8 decades), conversion of J 2^-e into hi/lo 16-bit values
-//               in the K-major core-matrix layout (second pass), then the
-//               epilogue: TMEM -> registers -> S = acc 2^(e - offsets).
-// Every mbarrier wait is bounded; on expiry the kernel records
-// DUST_ETIMEOUT in the context's status word and winds down.
+//               ~8 decades), conversion of J 2^-e into hi/lo 16-bit values in
+//               the K-major core-matrix layout (second pass).
+//   warps 7-10  epilogue: tensor memory -> registers -> S = acc 2^(e - offsets),
+//               overlapped with the next tile's MMAs in the other accumulator.
+// Every mbarrier wait is bounded; on expiry the kernel records DUST_ETIMEOUT
+// in the status word and winds down.
 #include "dust_internal.cuh"
 
+#include <algorithm>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -27,8 +31,8 @@
 namespace dust {
 namespace {
 
-constexpr int BM = 128;               // cells per tile (UMMA M)
-constexpr int NTHREADS = 192;
+constexpr int BM = 128;                    // cells per tile (UMMA M)
+constexpr int NTHREADS = 352;              // 11 warps
 constexpr int STAGE1_BYTES = BM * KC * 4;  // FP32 staging tile: 16 KB
 constexpr int A_BYTES = BM * KC * 2;       // one 16-bit A part: 8 KB
 
@@ -170,9 +174,19 @@ __device__ __forceinline__ int tc_req_of(const TcBatch &p, int64_t tile, int ri)
     return ri;
 }
 
+// Waits (bounded, ignoring aborts) for the last copy issued into each slot of
+// a ring of `ns` slots after `n` copies, so none lands after the CTA exits.
+__device__ __forceinline__ void drain_ring(uint64_t *full, int ns, int64_t n, int *status) {
+    for (int s = 0; s < ns; ++s) {
+        const int64_t last = n - 1 - ((n - 1 - s) % ns + ns) % ns;
+        if (last >= 0 && last % ns == s) mbar_drain(&full[s], (uint32_t)((last / ns) & 1), status);
+    }
+}
+
 // TcBatch fields: GsMax sets the ring layout, ns1 / ns2 the ring depths,
-// j_off scales J to [2^(j_off-1), 2^j_off) per cell, off_exp is the W image
-// scale folded back in the epilogue.
+// nacc the accumulators (tmem_cols each), j_off scales J to
+// [2^(j_off-1), 2^j_off) per cell, off_exp is the W image scale folded back
+// in the epilogue.
 template <bool BF16, bool TWO_PASS>
 __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__ TcBatch p) {
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
@@ -183,19 +197,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
     unsigned char *stB = stA + (size_t)p.ns2 * 2 * A_BYTES;
     uint64_t *bars = (uint64_t *)(stB + (size_t)p.ns2 * B_BYTES);
     uint64_t *full1 = bars, *empty1 = full1 + p.ns1;
-    uint64_t *a_full = empty1 + p.ns1, *a_empty = a_full + p.ns2, *b_full = a_empty + p.ns2;
-    uint64_t *acc_full = b_full + p.ns2, *acc_empty = acc_full + 1, *drain = acc_empty + 1;
-    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    uint64_t *a_full = empty1 + p.ns1, *b_full = a_full + p.ns2, *ab_empty = b_full + p.ns2;
+    uint64_t *acc_full = ab_empty + p.ns2, *acc_empty = acc_full + 2;
+    uint64_t *e_full = acc_empty + 2, *e_empty = e_full + 2, *drain = e_empty + 2;
+    int *e_smem = (int *)(drain + 1);                 // [2][BM] per-cell exponents
+    uint32_t *tmem_slot = (uint32_t *)(e_smem + 2 * BM);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ntiles = p.ntiles;
+    const int nacc = p.nacc;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < p.ns1; ++s) { mbar_init(&full1[s], 1); mbar_init(&empty1[s], 4); }
-        for (int s = 0; s < p.ns2; ++s) { mbar_init(&a_full[s], 4); mbar_init(&a_empty[s], 1); mbar_init(&b_full[s], 1); }
-        mbar_init(acc_full, 1);
-        mbar_init(acc_empty, 4);
+        for (int s = 0; s < p.ns2; ++s) { mbar_init(&a_full[s], 4); mbar_init(&b_full[s], 1); mbar_init(&ab_empty[s], 1); }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+            mbar_init(&e_full[b], 4);
+            mbar_init(&e_empty[b], 4);
+        }
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -203,7 +224,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(tmem_slot)), "r"(p.tmem_cols) : "memory");
+                     ::"r"(smem_u32(tmem_slot)), "r"(p.tmem_cols * nacc) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
@@ -212,19 +233,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ------------------------------------------------------------ producer
+        // ------------------------------------------------------------ J producer
         if (lane == 0) {
-            int s1 = 0, sa = 0;
-            uint32_t ph1 = 0, pha = 0;
-            int64_t n1 = 0, n2 = 0;  // copies issued into each ring
+            int s1 = 0, ri = 0;
+            uint32_t ph1 = 0;
+            int64_t n1 = 0;
             bool ok = true;
-            int ri = 0;
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 ri = tc_req_of(p, tile, ri);
                 const TcReq &q = p.req[ri];
                 const CUtensorMap *tm = &p.tm[ri];
                 const int row0 = (int)((tile - q.tile_begin) * BM);
-                const uint32_t wbytes = (uint32_t)q.Gs * KC * 4;  // this request's hi + lo chunk
                 for (int pass = TWO_PASS ? 0 : 1; pass < 2 && ok; ++pass) {
                     for (int kc = 0; kc < q.nkc && ok; ++kc) {
                         if (!(ok = mbar_wait(&empty1[s1], ph1 ^ 1, abort_flag, p.status))) break;
@@ -232,41 +251,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
                         tma_load_2d(st1 + (size_t)s1 * STAGE1_BYTES, tm, kc * KC, row0, &full1[s1]);
                         ++n1;
                         if (++s1 == p.ns1) { s1 = 0; ph1 ^= 1; }
-                        if (pass == 1) {
-                            if (!(ok = mbar_wait(&a_empty[sa], pha ^ 1, abort_flag, p.status))) break;
-                            mbar_expect_tx(&b_full[sa], wbytes);
-                            bulk_load(stB + (size_t)sa * B_BYTES, q.Wimg + (size_t)kc * (wbytes / 2), wbytes,
-                                      &b_full[sa]);
-                            ++n2;
-                            if (++sa == p.ns2) { sa = 0; pha ^= 1; }
-                        }
                     }
                 }
             }
-            if (!ok) {
-                // after an abort, let the copies already issued land before the CTA exits
-                for (int s = 0; s < p.ns1; ++s) {
-                    int64_t last = n1 - 1 - ((n1 - 1 - s) % p.ns1 + p.ns1) % p.ns1;
-                    if (last >= 0 && last % p.ns1 == s) mbar_drain(&full1[s], (uint32_t)((last / p.ns1) & 1), p.status);
-                }
-                for (int s = 0; s < p.ns2; ++s) {
-                    int64_t last = n2 - 1 - ((n2 - 1 - s) % p.ns2 + p.ns2) % p.ns2;
-                    if (last >= 0 && last % p.ns2 == s) mbar_drain(&b_full[s], (uint32_t)((last / p.ns2) & 1), p.status);
+            if (!ok) drain_ring(full1, p.ns1, n1, p.status);
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------------------ W producer
+        if (lane == 0) {
+            int sa = 0, ri = 0;
+            uint32_t pha = 0;
+            int64_t n2 = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                ri = tc_req_of(p, tile, ri);
+                const TcReq &q = p.req[ri];
+                const uint32_t wbytes = (uint32_t)q.Gs * KC * 4;  // this request's hi + lo chunk
+                for (int kc = 0; kc < q.nkc && ok; ++kc) {
+                    if (!(ok = mbar_wait(&ab_empty[sa], pha ^ 1, abort_flag, p.status))) break;
+                    mbar_expect_tx(&b_full[sa], wbytes);
+                    bulk_load(stB + (size_t)sa * B_BYTES, q.Wimg + (size_t)kc * (wbytes / 2), wbytes, &b_full[sa]);
+                    ++n2;
+                    if (++sa == p.ns2) { sa = 0; pha ^= 1; }
                 }
             }
+            if (!ok) drain_ring(b_full, p.ns2, n2, p.status);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             int sa = 0, ri = 0;
-            uint32_t pha = 0, phacc = 0;
+            uint32_t pha = 0;
+            int64_t it = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
                 ri = tc_req_of(p, tile, ri);
                 const int Gs = p.req[ri].Gs, nkc = p.req[ri].nkc;
+                const int b = (int)(it % nacc);
+                const uint32_t ub = (uint32_t)((it / nacc) & 1);
+                const uint32_t d_tmem = tmem + (uint32_t)(b * p.tmem_cols);
                 const uint32_t idesc_full = instr_desc(BF16, BM, Gs <= 256 ? Gs : 256);
                 const uint32_t idesc_tail = instr_desc(BF16, BM, Gs > 256 ? Gs - 256 : 16);
-                if (!(ok = mbar_wait(acc_empty, phacc ^ 1, abort_flag, p.status))) break;
+                if (!(ok = mbar_wait(&acc_empty[b], ub ^ 1, abort_flag, p.status))) break;
                 tc_fence_after();
                 for (int kc = 0; kc < nkc && ok; ++kc) {
                     if (!(ok = mbar_wait(&a_full[sa], pha, abort_flag, p.status))) break;
@@ -282,31 +308,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
                             const uint32_t aoff = (part == 1 ? A_BYTES : 0) + ks * 256;
                             const uint32_t boff = (part == 2 ? Gs * KC * 2 : 0) + ks * 256;
                             const uint32_t acc = (kc | ks | part) ? 1u : 0u;
-                            tc_mma(tmem, smem_desc(a_base + aoff, 128, 512), smem_desc(b_base + boff, 128, 512),
+                            tc_mma(d_tmem, smem_desc(a_base + aoff, 128, 512), smem_desc(b_base + boff, 128, 512),
                                    idesc_full, acc);
                             if (Gs > 256)
-                                tc_mma(tmem + 256, smem_desc(a_base + aoff, 128, 512),
+                                tc_mma(d_tmem + 256, smem_desc(a_base + aoff, 128, 512),
                                        smem_desc(b_base + boff + 32 * 512, 128, 512), idesc_tail, acc);
                         }
                     }
-                    tc_commit(&a_empty[sa]);
+                    tc_commit(&ab_empty[sa]);
                     if (++sa == p.ns2) { sa = 0; pha ^= 1; }
                 }
-                if (ok) tc_commit(acc_full);
-                phacc ^= 1;
+                if (ok) tc_commit(&acc_full[b]);
             }
-            // drain every MMA still in flight before the accumulator is freed
+            // drain every MMA still in flight before tensor memory is freed
             tc_commit(drain);
             mbar_drain(drain, 0, p.status);
         }
-    } else {
-        // ------------------------------------------------------------ converters + epilogue
-        const int quad = warp & 3;           // TMEM lane quarter this warp may access
-        const int r = quad * 32 + lane;      // tile row owned by this thread
+    } else if (warp < 7) {
+        // ------------------------------------------------------------ converters
+        const int r = (warp - 3) * 32 + lane;  // tile row owned by this thread
         int s1 = 0, sa = 0, ri = 0;
-        uint32_t ph1 = 0, pha = 0, phacc = 0;
+        uint32_t ph1 = 0, pha = 0;
+        int64_t it = 0;
         bool ok = true;
-        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
             ri = tc_req_of(p, tile, ri);
             const TcReq &q = p.req[ri];
             int e = 0;
@@ -327,11 +352,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
                 if (!ok) break;
                 if (mx > 0.f && mx < INFINITY) frexpf(mx, &e);
                 e = min(max(e, p.j_off - 126), p.j_off + 126);  // keep 2^(j_off - e) a normal float
+                // hand the exponent to the epilogue
+                const int b = (int)(it % nacc);
+                const uint32_t ub = (uint32_t)((it / nacc) & 1);
+                if (!(ok = mbar_wait(&e_empty[b], ub ^ 1, abort_flag, p.status))) break;
+                e_smem[b * BM + r] = e;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&e_full[b]);
             }
             const float scale = __int_as_float((127 - e + p.j_off) << 23);  // 2^(j_off - e)
             for (int kc = 0; kc < q.nkc; ++kc) {
                 if (!(ok = mbar_wait(&full1[s1], ph1, abort_flag, p.status))) break;
-                if (!(ok = mbar_wait(&a_empty[sa], pha ^ 1, abort_flag, p.status))) break;
+                if (!(ok = mbar_wait(&ab_empty[sa], pha ^ 1, abort_flag, p.status))) break;
                 const unsigned char *src = st1 + (size_t)s1 * STAGE1_BYTES + r * 128;
                 unsigned char *dhi = stA + (size_t)sa * 2 * A_BYTES + (r >> 3) * 512 + (r & 7) * 16;
                 unsigned char *dlo = dhi + A_BYTES;
@@ -353,17 +385,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
                 if (++s1 == p.ns1) { s1 = 0; ph1 ^= 1; }
                 if (++sa == p.ns2) { sa = 0; pha ^= 1; }
             }
-            if (!ok) break;
-            // epilogue
-            if (!(ok = mbar_wait(acc_full, phacc, abort_flag, p.status))) break;
-            phacc ^= 1;
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quad = warp & 3;        // tensor-memory lane quarter of this warp
+        const int r = quad * 32 + lane;   // tile row
+        int ri = 0;
+        int64_t it = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+            ri = tc_req_of(p, tile, ri);
+            const TcReq &q = p.req[ri];
+            const int b = (int)(it % nacc);
+            const uint32_t ub = (uint32_t)((it / nacc) & 1);
+            int e = 0;
+            if (TWO_PASS) {
+                if (!(ok = mbar_wait(&e_full[b], ub, abort_flag, p.status))) break;
+                e = e_smem[b * BM + r];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&e_empty[b]);
+            }
+            if (!(ok = mbar_wait(&acc_full[b], ub, abort_flag, p.status))) break;
             tc_fence_after();
             const int64_t row = (tile - q.tile_begin) * BM + r;
             const int ex = e - p.j_off - p.off_exp;
             float *dst = q.S + row * q.Gs;
+            const uint32_t tbase = tmem + (uint32_t)(b * p.tmem_cols) + ((uint32_t)(quad * 32) << 16);
             for (int c0 = 0; c0 < q.Gs; c0 += 16) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + c0, v);
+                tmem_ld16(tbase + c0, v);
                 if (row < q.C) {
 #pragma unroll
                     for (int i = 0; i < 16; i += 4)
@@ -374,14 +424,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty);
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols * nacc)
                      : "memory");
     }
 }
@@ -434,7 +484,7 @@ int make_tc_req(const dust_ctx *ctx, int precision, int64_t C, const float *J, i
     return DUST_OK;
 }
 
-// Tile offsets, ring depths and tensor-memory width of a filled batch.
+// Tile offsets, ring depths and tensor-memory layout of a filled batch.
 int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem) {
     const bool bf16 = precision == DUST_PREC_BF16X3;
     int64_t t = 0;
@@ -449,14 +499,18 @@ int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem) 
     int cols = 32;
     while (cols < gmax) cols <<= 1;
     B.tmem_cols = cols;
+    B.nacc = 2 * cols <= 512 ? 2 : 1;  // double-buffer the accumulator when it fits
     // FP16 keeps J in [2^14, 2^15) and W in (2^13, 2^14] (the W image is
     // built with 2^14 folded in); BF16 has FP32's exponent range and needs none.
     B.j_off = bf16 ? 0 : 15;
     B.off_exp = bf16 ? 0 : 14;
     const size_t b_bytes = (size_t)gmax * KC * 4;
-    const size_t budget = (smem_optin ? smem_optin : 232448) - 1024 - 256;
+    const size_t budget = (smem_optin ? smem_optin : 232448) - 1024;
     int ns2 = 4, ns1 = 6;
-    auto need = [&](int a, int b) { return (size_t)a * STAGE1_BYTES + (size_t)b * (2 * A_BYTES + b_bytes) + 256; };
+    auto need = [&](int a, int b) {
+        return (size_t)a * STAGE1_BYTES + (size_t)b * (2 * A_BYTES + b_bytes) + (size_t)(2 * a + 3 * b + 9) * 8 +
+               2 * BM * 4 + 16;
+    };
     while (need(ns1, ns2) > budget && ns1 > 3) --ns1;
     while (need(ns1, ns2) > budget && ns2 > 2) --ns2;
     while (need(ns1, ns2) > budget && ns1 > 2) --ns1;

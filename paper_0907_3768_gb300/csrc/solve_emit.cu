@@ -35,7 +35,6 @@ namespace dust {
 namespace {
 
 constexpr int NTH = 256;
-constexpr int R = 2;    // phase-2 work items per thread
 constexpr int NB = 4;   // solves in flight per thread in phase 1
 constexpr double FOUR_PI = 12.566370614359172954;
 
@@ -65,56 +64,59 @@ __device__ __forceinline__ float hermite(float p0, float d0, float p1, float d1,
     return p0 + x * (d0 + x * (c2 + x * c3));
 }
 
-// Equilibrium temperatures of NB grains at once (independent loads in
-// flight together).  s: scaled absorbed power (A / P_g(T_min) = s 2^f_g).
-__device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[NB], const bool (&ok)[NB],
-                                            const float (&s)[NB], const float4 (&gq)[NB], float (&T)[NB],
-                                            int (&fl)[NB]) {
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Equilibrium temperatures of NB grains at once, branch-free: every lane runs
+// the table lookup on y clamped into the table, and the clamp / invalid cases
+// are selected at the end.  s: scaled absorbed power (A / P_g(T_min) = s 2^f_g).
+__device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[NB], const float (&s)[NB],
+                                            const float4 (&gq)[NB], float (&T)[NB], int (&fl)[NB]) {
     float y[NB], ty[NB];
     int m[NB];
-    bool act[NB];
     float4 iv[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        act[i] = false;
-        fl[i] = DUST_FLAG_OK;
-        T[i] = tb.Tmin;
-        y[i] = 0.f;
-        m[i] = 0;
-        ty[i] = 0.f;
-        if (!ok[i]) continue;
-        if (!(s[i] >= 0.f) || isinf(s[i])) { fl[i] = DUST_FLAG_INVALID; T[i] = __int_as_float(0x7fc00000); continue; }
-        if (s[i] == 0.f) { fl[i] = DUST_FLAG_LOW; continue; }
-        y[i] = log2f(s[i]) + gq[i].x;
-        if (y[i] < 0.f) { fl[i] = DUST_FLAG_LOW; continue; }
-        if (y[i] > gq[i].y) { fl[i] = DUST_FLAG_HIGH; T[i] = tb.Tmax; continue; }
-        act[i] = true;
-        const float fy = y[i] * gq[i].z;
+        // log2 s = e + log2 m with the exponent split off exactly and m in
+        // [1/2, 1), where lg2.approx is good to ~2^-22 absolute; the
+        // temperature error this causes is below 1e-7
+        const int bits = __float_as_int(s[i]);
+        const float mant = __int_as_float((bits & 0x007fffff) | 0x3f000000);
+        y[i] = (s[i] > 0.f) ? (float)(((bits >> 23) & 0xff) - 126) + lg2_approx(mant) + gq[i].x : -INFINITY;
+        const bool bad = !(s[i] >= 0.f) || isinf(s[i]);
+        fl[i] = bad ? DUST_FLAG_INVALID : (y[i] < 0.f ? DUST_FLAG_LOW : (y[i] > gq[i].y ? DUST_FLAG_HIGH : DUST_FLAG_OK));
+        const float yc = fminf(fmaxf(y[i], 0.f), gq[i].y);  // NaN -> 0
+        y[i] = yc;
+        const float fy = yc * gq[i].z;
         m[i] = min((int)fy, tb.NI - 2);
         ty[i] = fminf(fy - (float)m[i], 1.f);
     }
 #pragma unroll
-    for (int i = 0; i < NB; ++i)
-        iv[i] = act[i] ? __ldg(tb.inv + (size_t)g[i] * (tb.NI - 1) + m[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < NB; ++i) iv[i] = __ldg(tb.inv + (size_t)g[i] * (tb.NI - 1) + m[i]);
     int j[NB];
     float tau[NB], tn[NB];
     float4 f4[NB];
+    const float inv_h2 = 1.f / tb.h2;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const float ug = hermite(iv[i].x, iv[i].y, iv[i].z, iv[i].w, ty[i]);
-        const float fj = (ug - tb.log2Tmin) / tb.h2;
+        const float fj = (ug - tb.log2Tmin) * inv_h2;
         j[i] = min(max((int)floorf(fj), 0), tb.NT - 2);
         tau[i] = fminf(fmaxf(fj - (float)j[i], 0.f), 1.f);
     }
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        f4[i] = act[i] ? __ldg(tb.fw + (size_t)g[i] * (tb.NT - 1) + j[i]) : make_float4(0.f, 1.f, 1.f, 1.f);
-        tn[i] = act[i] ? __ldg(tb.Tnode + j[i]) : 1.f;
+        f4[i] = __ldg(tb.fw + (size_t)g[i] * (tb.NT - 1) + j[i]);
+        tn[i] = __ldg(tb.Tnode + j[i]);
     }
+    const float L1 = 0.69314718056f, L2 = 0.24022650695f, L3 = 0.05550410866f;  // (ln 2)^k / k!
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        if (!act[i]) continue;
-        // bracketing interval t_j <= y <= t_j+1 (the guess is almost always right)
+        // bracketing interval t_j <= y <= t_j+1 (the guess is right unless y
+        // sits within rounding of a node)
         for (int a = 0; a < 4; ++a) {
             if (y[i] < f4[i].x && j[i] > 0) { --j[i]; tau[i] = 1.f; }
             else if (y[i] > f4[i].z && j[i] < tb.NT - 2) { ++j[i]; tau[i] = 0.f; }
@@ -122,21 +124,26 @@ __device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[
             f4[i] = __ldg(tb.fw + (size_t)g[i] * (tb.NT - 1) + j[i]);
             tn[i] = __ldg(tb.Tnode + j[i]);
         }
-        // Newton on the Hermite cubic q(tau) = t(u_j + tau h2) - t_j = y - t_j
+        // two Newton steps on the Hermite cubic q(tau) = t(u_j + tau h2) - t_j = y - t_j
+        // from the inverse-table guess; a step leaving the bracket bisects instead
         const float r = y[i] - f4[i].x, d = f4[i].z - f4[i].x, m0 = f4[i].y, m1 = f4[i].w;
         const float c2 = 3.f * d - 2.f * m0 - m1, c3 = m0 + m1 - 2.f * d;
         float lo = 0.f, hi = 1.f, t = tau[i];
-        for (int it = 0; it < 4; ++it) {
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
             const float q = t * (m0 + t * (c2 + t * c3)) - r;
             const float dq = m0 + t * (2.f * c2 + 3.f * t * c3);
-            if (q < 0.f) lo = t; else hi = t;
-            float nt = t - q / dq;
-            if (!(nt >= lo && nt <= hi)) nt = 0.5f * (lo + hi);  // bracketed fallback
-            const float step = fabsf(nt - t);
-            t = nt;
-            if (step * tb.h2 < 2e-7f) break;
+            lo = q < 0.f ? t : lo;
+            hi = q < 0.f ? hi : t;
+            const float nt = t - q * rcp_approx(dq);
+            t = (nt >= lo && nt <= hi) ? nt : 0.5f * (lo + hi);
         }
-        T[i] = tn[i] * exp2f(t * tb.h2);
+        // T = T_j 2^(tau h2), 2^x by its Taylor series (|x| <= h2, error < 1e-12)
+        const float x = t * tb.h2;
+        const float Tv = tn[i] * fmaf(x, fmaf(x, fmaf(x, L3, L2), L1), 1.f);
+        T[i] = fl[i] == DUST_FLAG_OK ? Tv
+             : fl[i] == DUST_FLAG_LOW ? tb.Tmin
+             : fl[i] == DUST_FLAG_HIGH ? tb.Tmax : __int_as_float(0x7fc00000);
     }
 }
 
@@ -154,10 +161,14 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     int cur = -1;
-    // per-request shared-memory layout (byte offsets) and thread state
+    // per-request shared-memory layout (byte offsets) and thread state.  The
+    // emission item of a thread is one k-group (8 wavelengths) of two
+    // neighbouring cells; items run k-group-major over the threads, so the
+    // lanes of a warp share few k-groups (Chat loads are near-broadcasts) and
+    // one 16-byte load fetches (1/T, n) of both cells of a pair.
     int oTN = 0, oS = 0, oN = 0, oM = 0, oAbs = 0, oEm = 0;
-    int TNS = 0, CST = 0;
-    int icell[R], ikg[R];
+    int TNP = 0, CST = 0;
+    int ipair = 0, ikg = 0;
 
     for (int64_t tile = blockIdx.x; tile < B.ntiles; tile += gridDim.x) {
         int ri = cur < 0 ? 0 : cur;
@@ -166,27 +177,25 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
         const DevTables &tb = q.tb;
         const int G = tb.G, G8 = tb.G8, NKG = tb.NKG, K = tb.K, Gs = tb.Gs, TC = q.TC;
         const bool emit = (q.mode & EMIT_ON) != 0, rs = (q.mode & EMIT_RESID) != 0;
+        const int NP = TC / 2;  // cell pairs per tile
         if (ri != cur) {
-            TNS = 2 * G8 + 2;
+            TNP = 4 * G8 + 4;
             CST = 2 * (q.resident ? G8 : q.GC) + 1;
             __syncthreads();  // the previous request is done with shared memory
             cur = ri;
             oTN = emit ? NKG * CST * 16 : 0;
-            oS = oTN + (TC + 1) * TNS * 4;
+            oS = oTN + (emit ? (NP + 1) * TNP * 4 : 0);
             oN = oS + TC * G8 * 4;
             oM = oN + TC * G8 * 4;
             oAbs = oM + ((TC + 1) & ~1) * 4;
             oEm = oAbs + TC * 8;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int it = r * NTH + tid;
-                const bool okit = it < TC * NKG;
-                icell[r] = okit ? it / NKG : TC;  // idle items read the dummy row TC
-                ikg[r] = okit ? it % NKG : 0;
-            }
-            float *dummy = reinterpret_cast<float *>(smem_raw + oTN) + (size_t)TC * TNS;
-            for (int g = tid; g < G8; g += NTH)
-                *reinterpret_cast<float2 *>(dummy + 2 * g) = make_float2(1.f / tb.Tmax, 0.f);
+            const bool okit = tid < NP * NKG;
+            ikg = okit ? tid / NP : 0;
+            ipair = okit ? tid - ikg * NP : NP;  // idle threads read the dummy pair row NP
+            float *dummy = reinterpret_cast<float *>(smem_raw + oTN) + (size_t)NP * TNP;
+            if (emit)
+                for (int g = tid; g < G8; g += NTH)
+                    *reinterpret_cast<float4 *>(dummy + 4 * g) = make_float4(1.f / tb.Tmax, 0.f, 1.f / tb.Tmax, 0.f);
             if (emit && q.resident) {
                 const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
                 float4 *dst = reinterpret_cast<float4 *>(smem_raw);
@@ -226,6 +235,7 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
         }
         __syncthreads();
         // ---- phase 1: temperatures, NB pairs per thread per round
+        const float invG8 = 1.f / (float)G8;
         for (int p0 = 0; p0 < npair; p0 += NTH * NB) {
             int gi[NB], pi[NB], ci[NB];
             bool ok[NB];
@@ -236,15 +246,17 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
             for (int i = 0; i < NB; ++i) {
                 pi[i] = p0 + tid + NTH * i;
                 const bool in = pi[i] < npair;
-                ci[i] = in ? pi[i] / G8 : 0;
+                // p / G8 through a float reciprocal: exact, (p + 1/2) / G8 is >= 1/(2 G8)
+                // away from an integer and p < 2^15
+                ci[i] = in ? (int)(((float)pi[i] + 0.5f) * invG8) : 0;
                 gi[i] = in ? pi[i] - ci[i] * G8 : 0;
                 ok[i] = in && ci[i] < nc && gi[i] < G;
-                s[i] = in ? sS[pi[i]] : 0.f;
+                s[i] = ok[i] ? sS[pi[i]] : 0.f;
                 nv[i] = in ? sN[pi[i]] : 0.f;
-                gq[i] = ok[i] ? __ldg(reinterpret_cast<const float4 *>(tb.gp) + gi[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
                 if (!ok[i]) gi[i] = 0;
+                gq[i] = __ldg(reinterpret_cast<const float4 *>(tb.gp) + gi[i]);
             }
-            solve_batch(tb, gi, ok, s, gq, Tv, fl);
+            solve_batch(tb, gi, s, gq, Tv, fl);
 #pragma unroll
             for (int i = 0; i < NB; ++i) {
                 if (pi[i] >= npair) continue;
@@ -267,7 +279,9 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
                         rl = fmaf(xh, gr.x, -rh) + fmaf(xh, gr.y, xl * gr.x);
                     }
                 }
-                if (emit) *reinterpret_cast<float2 *>(sTN + (size_t)c * TNS + 2 * g) = make_float2(invT, nn);
+                if (emit)
+                    *reinterpret_cast<float2 *>(sTN + (size_t)(c >> 1) * TNP + 4 * g + 2 * (c & 1)) =
+                        make_float2(invT, nn);
                 if (rs) { sS[pi[i]] = rh; sN[pi[i]] = rl; }  // this thread's own slots
             }
         }
@@ -285,15 +299,14 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
             }
         }
         if (!emit) continue;
-        // ---- phase 2: emission
-        float2 acc[R][4], nax2[R][4];
+        // ---- phase 2: emission (two cells x 8 wavelengths per thread)
+        float2 acc[2][4], nax2[4];
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                acc[r][p] = make_float2(0.f, 0.f);
-                nax2[r][p] = __ldg(reinterpret_cast<const float2 *>(tb.nax + ikg[r] * KQ) + p);
-            }
+        for (int p = 0; p < 4; ++p) {
+            acc[0][p] = make_float2(0.f, 0.f);
+            acc[1][p] = make_float2(0.f, 0.f);
+            nax2[p] = __ldg(reinterpret_cast<const float2 *>(tb.nax + ikg * KQ) + p);
+        }
         const int GC = q.resident ? G8 : q.GC;
         for (int g0 = 0; g0 < G8; g0 += GC) {
             const int gn = min(GC, G8 - g0);
@@ -307,32 +320,30 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
             }
             __syncthreads();
             const int goff = q.resident ? g0 : 0;
+            const float4 *tnp = reinterpret_cast<const float4 *>(sTN + (size_t)ipair * TNP) + g0;
+            const float4 *cp = sC + (size_t)ikg * CST + 2 * goff;
             for (int gg0 = 0; gg0 < gn; gg0 += RG) {
-                const float2 *tnp[R];
-                const float4 *cp[R];
-                float2 N[R][4], D[R][4];
+                float2 N[2][4], D[2][4];
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    tnp[r] = reinterpret_cast<const float2 *>(sTN + (size_t)icell[r] * TNS) + g0 + gg0;
-                    cp[r] = sC + (size_t)ikg[r] * CST + 2 * (goff + gg0);
+                for (int r = 0; r < 2; ++r)
 #pragma unroll
                     for (int p = 0; p < 4; ++p) { N[r][p] = make_float2(0.f, 0.f); D[r][p] = make_float2(1.f, 1.f); }
-                }
 #pragma unroll
                 for (int u = 0; u < RG; ++u) {
+                    const float4 tn = tnp[gg0 + u];  // (1/T, n) of both cells
+                    const float4 ca = cp[2 * (gg0 + u)], cb = cp[2 * (gg0 + u) + 1];
+                    const float2 cw[4] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w), make_float2(cb.x, cb.y),
+                                          make_float2(cb.z, cb.w)};
+                    const float2 iTa = make_float2(tn.x, tn.x), na = make_float2(tn.y, tn.y);
+                    const float2 iTb = make_float2(tn.z, tn.z), nb = make_float2(tn.w, tn.w);
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float2 tn = tnp[r][u];
-                        const float4 ca = cp[r][2 * u], cb = cp[r][2 * u + 1];
-                        const float2 iT = make_float2(tn.x, tn.x), nn = make_float2(tn.y, tn.y);
-                        emit_pair(nax2[r][0], iT, nn, make_float2(ca.x, ca.y), N[r][0], D[r][0]);
-                        emit_pair(nax2[r][1], iT, nn, make_float2(ca.z, ca.w), N[r][1], D[r][1]);
-                        emit_pair(nax2[r][2], iT, nn, make_float2(cb.x, cb.y), N[r][2], D[r][2]);
-                        emit_pair(nax2[r][3], iT, nn, make_float2(cb.z, cb.w), N[r][3], D[r][3]);
+                    for (int p = 0; p < 4; ++p) {
+                        emit_pair(nax2[p], iTa, na, cw[p], N[0][p], D[0][p]);
+                        emit_pair(nax2[p], iTb, nb, cw[p], N[1][p], D[1][p]);
                     }
                 }
 #pragma unroll
-                for (int r = 0; r < R; ++r)
+                for (int r = 0; r < 2; ++r)
 #pragma unroll
                     for (int p = 0; p < 4; ++p) {
                         acc[r][p].x = fmaf(N[r][p].x, rcp_approx(D[r][p].x), acc[r][p].x);
@@ -344,13 +355,13 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
         // sum_k w_k L_k of an item is accumulated error-free in float-float
         // (products split by FMA, sums by two-sum).
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int c = icell[r];
+        for (int r = 0; r < 2; ++r) {
+            const int c = 2 * ipair + r;
             if (c >= nc) continue;
             const int64_t cell = c0 + c;
             const int mc = sM[c];
             float sh = 0.f, sl = 0.f;
-            const int kb = ikg[r] * KQ;
+            const int kb = ikg * KQ;
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
 #pragma unroll
@@ -371,7 +382,7 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
                     }
                 }
             }
-            if (rs) sEm[c * NKG + ikg[r]] = make_float2(sh, sl);
+            if (rs) sEm[c * NKG + ikg] = make_float2(sh, sl);
         }
         if (rs) {
             __syncthreads();
@@ -395,14 +406,23 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
 EmitPlan plan_emit(const dust_ctx *ctx, bool emit) {
     const DevTables &tb = ctx->tb;
     EmitPlan p{};
-    p.TC = emit ? (R * NTH) / tb.NKG : 64;
-    p.TC = std::max(1, std::min(p.TC, 64));
     const size_t budget = 113 * 1024;  // two CTAs per SM
-    auto fixed = [&](int TC) {  // sTN (+ dummy row), sS, sN, sM, sAbs, sEm
-        return (size_t)(TC + 1) * (2 * tb.G8 + 2) * 4 + (size_t)2 * TC * tb.G8 * 4 + (size_t)((TC + 1) & ~1) * 4 +
-               (size_t)TC * 8 + (size_t)TC * tb.NKG * 8 + 64;
+    // temperatures only: S and n of the tile, as many cells as fit (<= 64, even)
+    if (!emit) {
+        int tc = (int)std::min<size_t>(64, (budget - 4096) / ((size_t)8 * tb.G8 + 12)) & ~1;
+        p.TC = std::max(2, tc);
+        p.GC = tb.G8;
+        p.resident = 0;
+        p.smem = (size_t)2 * p.TC * tb.G8 * 4 + (size_t)((p.TC + 1) & ~1) * 4 + (size_t)p.TC * 8 +
+                 (size_t)p.TC * tb.NKG * 8 + 64;
+        return p;
+    }
+    const int NP = std::max(1, std::min(32, NTH / tb.NKG));  // cell pairs per tile
+    p.TC = 2 * NP;
+    auto fixed = [&](int TC) {  // sTN (+ dummy pair row), sS, sN, sM, sAbs, sEm
+        return (size_t)(TC / 2 + 1) * (4 * tb.G8 + 4) * 4 + (size_t)2 * TC * tb.G8 * 4 +
+               (size_t)((TC + 1) & ~1) * 4 + (size_t)TC * 8 + (size_t)TC * tb.NKG * 8 + 64;
     };
-    if (!emit) { p.GC = tb.G8; p.resident = 0; p.smem = fixed(p.TC); return p; }
     const size_t full = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + fixed(p.TC);
     if (full <= budget) { p.GC = tb.G8; p.resident = 1; p.smem = full; return p; }
     const size_t avail = budget > fixed(p.TC) ? budget - fixed(p.TC) : 0;
