@@ -152,6 +152,29 @@ int dust_solve_prec(dust_ctx *ctx, int precision, int64_t n_cells, const float *
 int dust_solve_host(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n,
                     float *T, float *L, double *resid, uint8_t *flags);
 
+/* dust_solve without any device allocation (the paper has no counterpart).
+ * For callers that may not allocate device memory: device memory owned by a
+ * host framework's pool, real-time loops that cannot take cudaMalloc's
+ * implicit device synchronisation, memory-capped embeddings.  Same arguments,
+ * layouts, ownership and errors as dust_solve with the context's current
+ * precision; the caller still provides every input and output buffer.  The
+ * scratch of absorbed powers lives in one fixed 64 MiB array in the
+ * library's device data, which every GPU that loads the library holds until
+ * the process exits, so n_cells may not exceed dust_noalloc_max_cells(ctx)
+ * (= 2^24 / G rounded up to 16; 174762 cells for 96 grains): larger batches
+ * get DUST_EINVAL and must be split.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, no allocation); make that
+ * first call before any stream capture.  All calls share the array: calls
+ * whose work overlaps on the GPU (different streams, or different contexts on
+ * one device) race on it and must be serialised by the caller.  Nothing is
+ * left to clear between calls (every scratch value a call reads, it writes
+ * first). */
+int dust_solve_noalloc(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n,
+                       float *T, float *L, double *resid, uint8_t *flags, void *stream);
+
+/* Largest n_cells dust_solve_noalloc accepts for this context (0 if ctx is NULL). */
+size_t dust_noalloc_max_cells(const dust_ctx *ctx);
+
 /* Read and clear the context's device status word (a dust_status: DUST_OK,
  * or DUST_ETIMEOUT if a bounded wait inside a kernel gave up since the last
  * call).  Synchronises the device. */

@@ -40,6 +40,8 @@ _SIGS = {
     "dust_ctx_profile": (_i, [_p, _i]),
     "dust_ctx_profile_read": (_i, [_p, _p, _p, _p]),
     "dust_diag_throughput": (_i, [_i, _p, _p]),
+    "dust_solve_noalloc": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
+    "dust_noalloc_max_cells": (_sz, [_p]),
     "dust_server_create": (_i, [ctypes.POINTER(_p), _sz, _i, _i]),
     "dust_serve_submit": (_i, [_p, _p, _i64, _p, _i64, _p, _p, _p, _p, _p, ctypes.POINTER(ctypes.c_uint64)]),
     "dust_serve_poll": (_i, [_p, ctypes.c_uint64, _p, _p]),
@@ -139,6 +141,14 @@ def dust_ctx_profile_read(ctx):
     cnt = ctypes.c_int64()
     check(lib().dust_ctx_profile_read(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(cnt)))
     return a.value, b.value, cnt.value
+
+
+def dust_solve_noalloc(ctx, n_cells, J, ld, n, T, L, resid, flags, stream):
+    return check(lib().dust_solve_noalloc(ctx, n_cells, J, ld, n, T, L, resid, flags, stream))
+
+
+def dust_noalloc_max_cells(ctx):
+    return lib().dust_noalloc_max_cells(ctx)
 
 
 def dust_diag_throughput(device=0):

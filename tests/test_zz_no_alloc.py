@@ -1,0 +1,73 @@
+"""The allocation-free entry point (dust_solve_noalloc) against dust_solve.
+
+Some callers cannot allocate device memory (their device memory belongs to a
+host framework's pool, or a real-time loop cannot take cudaMalloc's implicit
+synchronisation); dust_solve_noalloc serves them with a fixed scratch array
+in the library's device data.  Here it must reproduce dust_solve on two calls
+in a row with different batches (the second call reuses the array the first
+one left behind), and refuse a batch larger than its array.  This file is
+named so that pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+import synth
+from metrics import l_err, t_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+
+
+def _noalloc(ctx, J, n):
+    from paper_0907_3768_gb300 import _lib
+
+    C, ld = J.shape[0], J.stride(0)
+    out = ctx.alloc_outputs(C, ld)
+    _lib.dust_solve_noalloc(ctx.handle, C, J.data_ptr(), ld, n.data_ptr(), out["T"].data_ptr(),
+                            out["L_buf"].data_ptr(), out["resid"].data_ptr(), out["flags"].data_ptr(),
+                            torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_noalloc_matches_dust_solve_on_two_calls(prec):
+    from paper_0907_3768_gb300 import Context
+
+    wl = synth.make_workload(1, cells=np.arange(60000))
+    J = torch.from_numpy(wl.J).cuda()
+    n = torch.from_numpy(wl.n).cuda()
+    batches = [(J[:50000], n[:50000]), (J[13:21013], n[13:21013])]  # second call: other cells, fewer of them
+    with Context.from_workload(wl, precision=prec) as ctx:
+        for Jb, nb in batches:
+            ref = ctx.solve(Jb, nb)
+            torch.cuda.synchronize()
+            got = _noalloc(ctx, Jb, nb)
+            T, Tr = got["T"].cpu().numpy(), ref["T"].cpu().numpy().astype(np.float64)
+            assert t_err(T, Tr).max() <= 1e-5
+            assert l_err(got["L"].cpu().numpy(), ref["L"].cpu().numpy().astype(np.float64)).max() <= 1e-4
+            np.testing.assert_array_equal(got["flags"].cpu().numpy(), ref["flags"].cpu().numpy())
+            np.testing.assert_allclose(got["resid"].cpu().numpy(), ref["resid"].cpu().numpy(), rtol=0, atol=1e-9)
+        assert ctx.check() == 0
+
+
+def test_noalloc_rejects_batches_beyond_its_array():
+    from paper_0907_3768_gb300 import Context, DustError, _lib
+
+    wl = synth.make_workload(0, cells=np.arange(4))
+    with Context.from_workload(wl) as ctx:
+        cap = _lib.dust_noalloc_max_cells(ctx.handle)
+        assert cap == (16 << 20) // 16  # G = 16 grains: one 16-column scratch row per cell
+        J = torch.zeros((1, wl.K), device="cuda")
+        with pytest.raises(DustError) as e:
+            _lib.dust_solve_noalloc(ctx.handle, cap + 1, J.data_ptr(), wl.K, J.data_ptr(), J.data_ptr(), 0, 0, 0, 0)
+        assert e.value.code == _lib.DUST_EINVAL and "split the batch" in str(e.value)
