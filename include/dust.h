@@ -158,11 +158,12 @@ int dust_solve_host(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, 
  * implicit device synchronisation, memory-capped embeddings.  Same arguments,
  * layouts, ownership and errors as dust_solve with the context's current
  * precision; the caller still provides every input and output buffer.  The
- * scratch of absorbed powers lives in one fixed 64 MiB array in the
- * library's device data, which every GPU that loads the library holds until
- * the process exits, so n_cells may not exceed dust_noalloc_max_cells(ctx)
- * (= 2^24 / G rounded up to 16; 174762 cells for 96 grains): larger batches
- * get DUST_EINVAL and must be split.  The first call on a device looks up the
+ * scratch (absorbed powers, then the solve's per-grain and per-cell results
+ * for the emission: about 4 Gs + 8 G8 + 16 bytes per cell, Gs = G rounded up
+ * to 16, G8 to 8) lives in one fixed 64 MiB array in the library's device
+ * data, which every GPU that loads the library holds until the process
+ * exits, so n_cells may not exceed dust_noalloc_max_cells(ctx) (57456 cells
+ * for 96 grains): larger batches get DUST_EINVAL and must be split.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, no allocation); make that
  * first call before any stream capture.  All calls share the array: calls
  * whose work overlaps on the GPU (different streams, or different contexts on
@@ -181,13 +182,14 @@ size_t dust_noalloc_max_cells(const dust_ctx *ctx);
 int dust_ctx_check(dust_ctx *ctx, int *device_status);
 
 /* Per-kernel device timing.  While enabled, every solve on this context
- * records CUDA events on its stream before the absorption kernel, between
- * the two kernels and after the solve/emission kernel.
+ * records CUDA events on its stream before the absorption kernel (Eq. 6),
+ * before the temperature solve (Eq. 7), before the emission and residual
+ * (Eqs. 8-10; empty when neither L nor resid is wanted) and after it.
  * dust_ctx_profile_read synchronises on the recorded events and returns the
- * summed milliseconds of each kernel and the number of solves since the last
- * read (any output may be NULL), then forgets them. */
+ * summed milliseconds of each of the three stages and the number of solves
+ * since the last read (any output may be NULL), then forgets them. */
 int dust_ctx_profile(dust_ctx *ctx, int enable);
-int dust_ctx_profile_read(dust_ctx *ctx, double *ms_absorb, double *ms_solve_emit,
+int dust_ctx_profile_read(dust_ctx *ctx, double *ms_absorb, double *ms_solve, double *ms_emit,
                           int64_t *n_solves);
 
 /* ------------------------------------------------------------------ serving

@@ -38,7 +38,7 @@ _SIGS = {
     "dust_solve_host": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p]),
     "dust_ctx_check": (_i, [_p, _p]),
     "dust_ctx_profile": (_i, [_p, _i]),
-    "dust_ctx_profile_read": (_i, [_p, _p, _p, _p]),
+    "dust_ctx_profile_read": (_i, [_p, _p, _p, _p, _p]),
     "dust_diag_throughput": (_i, [_i, _p, _p]),
     "dust_solve_noalloc": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
     "dust_noalloc_max_cells": (_sz, [_p]),
@@ -137,10 +137,10 @@ def dust_ctx_profile(ctx, enable):
 
 
 def dust_ctx_profile_read(ctx):
-    a, b = ctypes.c_double(), ctypes.c_double()
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     cnt = ctypes.c_int64()
-    check(lib().dust_ctx_profile_read(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(cnt)))
-    return a.value, b.value, cnt.value
+    check(lib().dust_ctx_profile_read(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(cnt)))
+    return a.value, b.value, c.value, cnt.value
 
 
 def dust_solve_noalloc(ctx, n_cells, J, ld, n, T, L, resid, flags, stream):

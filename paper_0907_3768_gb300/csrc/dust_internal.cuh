@@ -65,20 +65,37 @@ constexpr int MAXREQ = 32;
 
 enum EmitMode { EMIT_ON = 1, EMIT_RESID = 2, EMIT_STORE_L = 4 };
 
-// One request of the solve/emission kernel.
+// Per-cell record passed from the solve to the emission: exponent m_c of
+// max_g n[c,g] and the absorbed power sum_g n Pe (residual denominator / 4 pi).
+struct CellInfo {
+    int mc, pad;
+    double absorbed;
+};
+
+// A request's scratch: S [C][Gs] FP32, then (emission only) the pairs
+// (1/T, n 2^-m_c) [C][G8] and one CellInfo per cell, each 16-byte aligned.
+struct ScratchView {
+    float *S;
+    float2 *prep;
+    CellInfo *cell;
+};
+
+// One request of the solve / emission kernels.
 struct EmitReq {
     DevTables tb;
-    int64_t C, ld, tile_begin;
+    int64_t C, ld, tile_begin, cell_begin;
     const float *S, *n;
     float *T, *L;
     double *resid;
     uint8_t *flags;
+    float2 *prep;
+    CellInfo *cell;
     int TC, GC, resident, mode;
 };
 
 struct EmitBatch {
     int nreq;
-    int64_t ntiles;
+    int64_t ntiles, ncells;
     EmitReq req[MAXREQ];
 };
 
@@ -179,9 +196,12 @@ int launch_gemm_simt(const dust_ctx *ctx, int64_t C, const float *J, int64_t ld,
                      cudaStream_t st);
 int launch_gemm_tc(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld,
                    float *S, cudaStream_t st);
-int launch_solve_emit(const dust_ctx *ctx, int64_t C, const float *S, const float *n, float *T,
+int launch_solve_emit(const dust_ctx *ctx, int64_t C, const ScratchView &sv, const float *n, float *T,
                       float *L, int64_t ld, double *resid, uint8_t *flags, cudaStream_t st);
 EmitPlan plan_emit(const dust_ctx *ctx, bool emit);
+// Scratch bytes of a request of C cells and its layout at `base`.
+size_t scratch_bytes(const dust_ctx *ctx, int64_t C, bool emit);
+ScratchView scratch_view(const dust_ctx *ctx, int64_t C, void *base);
 // Tensor-core batches: one request entry (encodes its TMA descriptor), the
 // ring geometry of a batch, and the launch.  All requests of one launch share
 // the precision.
@@ -192,16 +212,20 @@ int launch_tc_batch(const TcBatch &B, int precision, size_t smem, int num_sms, c
 // FP32 SIMT batches.
 void make_simt_req(const dust_ctx *ctx, int64_t C, const float *J, int64_t ld, float *S, SimtReq &r);
 int launch_simt_batch(SimtBatch &B, cudaStream_t st);
-void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const float *S, const float *n,
+void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const ScratchView &sv, const float *n,
                    float *T, float *L, int64_t ld, double *resid, uint8_t *flags, EmitReq &r);
-int launch_emit_batch(const EmitBatch &B, size_t smem, int num_sms, cudaStream_t st);
+// Numbers cells and tiles, then launches the solve over every request and the
+// emission over those that want L or resid; `between` (optional) is recorded
+// on `st` between the two kernels.
+int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, cudaEvent_t between = nullptr);
 
-// Grow the context's scratch to hold `cells` rows (synchronises `st` first).
+// Grow the context's scratch to hold `cells` cells (synchronises `st` first).
 int ensure_scratch(dust_ctx *ctx, int64_t cells, cudaStream_t st);
 
-// The whole path on device buffers with scratch S of at least C x Gs floats.
+// The whole path on device buffers with scratch of scratch_bytes(ctx, C, true)
+// bytes at `scratch`.
 int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld,
-                 const float *n, float *T, float *L, double *resid, uint8_t *flags, float *S,
+                 const float *n, float *T, float *L, double *resid, uint8_t *flags, void *scratch,
                  cudaStream_t st);
 
 // Bounded spin budget for device-side waits: a wait that exceeds it records

@@ -13,9 +13,9 @@
 
 namespace {
 
-// 64 MiB of FP32 scratch, resident on every device that loads the library.
-constexpr size_t NOALLOC_SCRATCH_FLOATS = (size_t)16 << 20;
-static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH_FLOATS];
+// 64 MiB of scratch, resident on every device that loads the library.
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)64 << 20;
+static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH_BYTES / sizeof(float)];
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_addr_mu;
@@ -58,7 +58,13 @@ int check_ptr(const void *p, int device, const char *name) {
 
 extern "C" size_t dust_noalloc_max_cells(const dust_ctx *ctx) {
     if (!ctx) return 0;
-    return NOALLOC_SCRATCH_FLOATS / (size_t)ctx->tb.Gs;
+    // largest C whose scratch (with the emission's part) fits the array
+    size_t lo = 0, hi = NOALLOC_SCRATCH_BYTES;
+    while (hi - lo > 1) {
+        const size_t mid = (lo + hi) / 2;
+        if (dust::scratch_bytes(ctx, (int64_t)mid, true) <= NOALLOC_SCRATCH_BYTES) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
 extern "C" int dust_solve_noalloc(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n,
@@ -69,12 +75,14 @@ extern "C" int dust_solve_noalloc(dust_ctx *ctx, int64_t n_cells, const float *J
     if (n_cells < 0) return set_error(DUST_EINVAL, "n_cells < 0");
     if (ld < ctx->K) return set_error(DUST_EINVAL, "ld=%lld < K=%d", (long long)ld, ctx->K);
     if (n_cells == 0) return DUST_OK;
-    if ((size_t)n_cells * (size_t)ctx->tb.Gs > NOALLOC_SCRATCH_FLOATS)
+    // one limit for every mode (the emission's scratch included), so that
+    // whether a batch is accepted never depends on which outputs it wants
+    const size_t max_cells = dust_noalloc_max_cells(ctx);
+    if ((size_t)n_cells > max_cells)
         return set_error(DUST_EINVAL,
-                         "n_cells=%lld needs %zu scratch floats; this entry point has %zu (at most %zu cells "
+                         "n_cells=%lld needs %zu scratch bytes; this entry point has %zu (at most %zu cells "
                          "for this context): split the batch",
-                         (long long)n_cells, (size_t)n_cells * ctx->tb.Gs, NOALLOC_SCRATCH_FLOATS,
-                         NOALLOC_SCRATCH_FLOATS / (size_t)ctx->tb.Gs);
+                         (long long)n_cells, scratch_bytes(ctx, n_cells, true), NOALLOC_SCRATCH_BYTES, max_cells);
     if (!J || !n || !T) return set_error(DUST_EINVAL, "J, n and T must be non-NULL");
     if (precision != DUST_PREC_FP32 && (ld % 4 != 0 || ((uintptr_t)J & 15) != 0))
         return set_error(DUST_EINVAL, "tensor-core precisions need ld %% 4 == 0 and a 16-byte aligned J");
@@ -93,11 +101,13 @@ extern "C" int dust_solve_noalloc(dust_ctx *ctx, int64_t n_cells, const float *J
     rc = scratch_address(ctx->device, &S);
     if (rc == DUST_OK) {
         cudaStream_t st = (cudaStream_t)stream;
-        // every scratch element a launch reads is written by its absorption
-        // kernel first, so nothing needs clearing between calls
-        rc = precision == DUST_PREC_FP32 ? launch_gemm_simt(ctx, n_cells, J, ld, S, st)
-                                         : launch_gemm_tc(ctx, precision, n_cells, J, ld, S, st);
-        if (rc == DUST_OK) rc = launch_solve_emit(ctx, n_cells, S, n, T, L, ld, resid, flags, st);
+        // every scratch value a launch reads is written earlier in the same
+        // call (S by the absorption kernel, the pairs and cell records by the
+        // solve), so nothing needs clearing between calls
+        const ScratchView sv = scratch_view(ctx, n_cells, S);
+        rc = precision == DUST_PREC_FP32 ? launch_gemm_simt(ctx, n_cells, J, ld, sv.S, st)
+                                         : launch_gemm_tc(ctx, precision, n_cells, J, ld, sv.S, st);
+        if (rc == DUST_OK) rc = launch_solve_emit(ctx, n_cells, sv, n, T, L, ld, resid, flags, st);
     }
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     return rc;

@@ -130,8 +130,8 @@ struct dust_server {
 namespace {
 
 size_t footprint_of(const dust_ctx *ctx, int64_t C, int64_t ld, bool L, bool resid, bool flags) {
-    const size_t G = ctx->G, Gs = ctx->tb.Gs;
-    size_t b = (size_t)C * ld * 4 + (size_t)C * G * 4 * 2 + (size_t)C * Gs * 4;  // J, n, T, scratch
+    const size_t G = ctx->G;
+    size_t b = (size_t)C * ld * 4 + (size_t)C * G * 4 * 2 + scratch_bytes(ctx, C, L || resid);  // J, n, T, scratch
     if (L) b += (size_t)C * ld * 4;
     if (resid) b += (size_t)C * 8;
     if (flags) b += (size_t)C * G;
@@ -206,6 +206,12 @@ std::vector<Part> build_round(dust_server *s) {
     return parts;
 }
 
+// Scratch of one part: rows c0.. of its request's S, (1/T, n) pairs and cell records.
+ScratchView part_view(const Part &p) {
+    const ScratchView v = scratch_view(p.r->ctx, p.r->C, p.r->S);
+    return {v.S + p.c0 * p.r->ctx->tb.Gs, v.prep + p.c0 * p.r->ctx->tb.G8, v.cell + p.c0};
+}
+
 int launch_round(dust_server *s, const std::vector<Part> &parts) {
     // absorption GEMMs, one launch per precision
     for (int prec = DUST_PREC_FP32; prec <= DUST_PREC_FP16X3; ++prec) {
@@ -215,7 +221,7 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
             for (const Part &p : parts) {
                 if (p.r->precision != prec) continue;
                 ServeReq *r = p.r;
-                make_simt_req(r->ctx, p.cn, r->J + p.c0 * r->ld, r->ld, r->S + p.c0 * r->ctx->tb.Gs, B.req[B.nreq++]);
+                make_simt_req(r->ctx, p.cn, r->J + p.c0 * r->ld, r->ld, part_view(p).S, B.req[B.nreq++]);
             }
             if (B.nreq) {
                 int rc = launch_simt_batch(B, s->st);
@@ -230,8 +236,8 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
                 if (p.r->precision != prec) continue;
                 ServeReq *r = p.r;
                 if (!B.status) B.status = r->ctx->tb.status;
-                int rc = make_tc_req(r->ctx, prec, p.cn, r->J + p.c0 * r->ld, r->ld, r->S + p.c0 * r->ctx->tb.Gs,
-                                     B.req[B.nreq], B.tm[B.nreq]);
+                int rc = make_tc_req(r->ctx, prec, p.cn, r->J + p.c0 * r->ld, r->ld, part_view(p).S, B.req[B.nreq],
+                                     B.tm[B.nreq]);
                 if (rc != DUST_OK) return rc;
                 B.nreq++;
             }
@@ -248,24 +254,21 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
     EmitBatch E;
     E.nreq = 0;
     size_t smem = 0;
-    int64_t t = 0;
+    bool emit = false;
     for (const Part &p : parts) {
         ServeReq *r = p.r;
         dust_ctx *ctx = r->ctx;
-        const int G = ctx->G, Gs = ctx->tb.Gs;
+        const int G = ctx->G;
         const EmitPlan pl = plan_emit(ctx, r->L || r->resid);
-        EmitReq &e = E.req[E.nreq++];
-        fill_emit_req(ctx, pl, p.cn, r->S + p.c0 * Gs, r->n + p.c0 * G, r->T + p.c0 * G,
+        fill_emit_req(ctx, pl, p.cn, part_view(p), r->n + p.c0 * G, r->T + p.c0 * G,
                       r->L ? r->L + p.c0 * r->ld : nullptr, r->ld, r->resid ? r->resid + p.c0 : nullptr,
-                      r->flags ? r->flags + p.c0 * G : nullptr, e);
-        e.tile_begin = t;
-        t += (p.cn + pl.TC - 1) / pl.TC;
+                      r->flags ? r->flags + p.c0 * G : nullptr, E.req[E.nreq++]);
         smem = std::max(smem, pl.smem);
+        emit = emit || r->L || r->resid;
     }
-    E.ntiles = t;
     int rc = launch_emit_batch(E, smem, s->num_sms, s->st);
     if (rc != DUST_OK) return rc;
-    s->launches++;
+    s->launches += emit ? 2 : 1;
     return DUST_OK;
 }
 
@@ -407,7 +410,7 @@ int dust_serve_submit(dust_server *s, dust_ctx *ctx, int64_t n_cells, const floa
     r->C = n_cells;
     r->ld = ld;
     r->J = J; r->n = n; r->T = T; r->L = L; r->resid = resid; r->flags = flags;
-    r->s_bytes = (size_t)std::max<int64_t>(n_cells, 1) * ctx->tb.Gs * 4;
+    r->s_bytes = scratch_bytes(ctx, std::max<int64_t>(n_cells, 1), L || resid);
     r->t_submit = now_ms();
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -70,7 +70,7 @@ int ensure_scratch(dust_ctx *ctx, int64_t cells, cudaStream_t st) {
     if ((size_t)cells <= ctx->S_cap) return DUST_OK;
     DUST_CUDA_TRY(cudaStreamSynchronize(st));
     if (ctx->S) { cudaFree(ctx->S); ctx->S = nullptr; ctx->S_cap = 0; }
-    DUST_CUDA_TRY(cudaMalloc(&ctx->S, sizeof(float) * (size_t)cells * ctx->tb.Gs));
+    DUST_CUDA_TRY(cudaMalloc(&ctx->S, scratch_bytes(ctx, cells, true)));
     ctx->S_cap = (size_t)cells;
     return DUST_OK;
 }
@@ -89,21 +89,26 @@ cudaEvent_t prof_event(dust_ctx *ctx) {
 }  // namespace
 
 int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, const float *n,
-                 float *T, float *L, double *resid, uint8_t *flags, float *S, cudaStream_t st) {
+                 float *T, float *L, double *resid, uint8_t *flags, void *scratch, cudaStream_t st) {
     if (C == 0) return DUST_OK;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    const ScratchView sv = scratch_view(ctx, C, scratch);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (ctx->prof_on)
-        for (int i = 0; i < 3; ++i) ev[i] = prof_event(ctx);
-    const bool prof = ev[0] && ev[1] && ev[2];
+        for (int i = 0; i < 4; ++i) ev[i] = prof_event(ctx);
+    const bool prof = ev[0] && ev[1] && ev[2] && ev[3];
     if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[0], st));
-    int rc = precision == DUST_PREC_FP32 ? launch_gemm_simt(ctx, C, J, ld, S, st)
-                                         : launch_gemm_tc(ctx, precision, C, J, ld, S, st);
+    int rc = precision == DUST_PREC_FP32 ? launch_gemm_simt(ctx, C, J, ld, sv.S, st)
+                                         : launch_gemm_tc(ctx, precision, C, J, ld, sv.S, st);
     if (rc == DUST_OK) {
         if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[1], st));
-        rc = launch_solve_emit(ctx, C, S, n, T, L, ld, resid, flags, st);
-        if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[2], st));
+        const EmitPlan p = plan_emit(ctx, L || resid);
+        EmitBatch B;
+        B.nreq = 1;
+        fill_emit_req(ctx, p, C, sv, n, T, L, ld, resid, flags, B.req[0]);
+        rc = launch_emit_batch(B, p.smem, ctx->num_sms, st, prof ? ev[2] : nullptr);
+        if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[3], st));
     }
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
         if (!ev[i]) continue;
         if (prof && rc == DUST_OK) ctx->prof_marks.push_back(ev[i]);
         else ctx->prof_pool.push_back(ev[i]);
@@ -146,7 +151,7 @@ int dust_solve_host(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, 
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard dg(ctx->device);
     if (dg.rc != DUST_OK) return dg.rc;
-    const int G = ctx->G, Gs = ctx->tb.Gs;
+    const int G = ctx->G;
     // chunks of at least 8192 cells, about 8 of them for large batches
     int64_t chunk = std::max<int64_t>(8192, (n_cells + 7) / 8);
     chunk = (chunk + 127) / 128 * 128;
@@ -168,7 +173,7 @@ int dust_solve_host(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, 
             DUST_CUDA_TRY(cudaMalloc(&hs.L[i], sizeof(float) * chunk * ld));
             DUST_CUDA_TRY(cudaMalloc(&hs.r[i], sizeof(double) * chunk));
             DUST_CUDA_TRY(cudaMalloc(&hs.f[i], sizeof(uint8_t) * chunk * G));
-            DUST_CUDA_TRY(cudaMalloc(&hs.S[i], sizeof(float) * chunk * Gs));
+            DUST_CUDA_TRY(cudaMalloc(&hs.S[i], scratch_bytes(ctx, chunk, true)));
         }
         hs.cap = chunk;
         hs.ld = ld;
@@ -203,30 +208,34 @@ int dust_ctx_profile(dust_ctx *ctx, int enable) {
     return DUST_OK;
 }
 
-int dust_ctx_profile_read(dust_ctx *ctx, double *ms_absorb, double *ms_solve_emit, int64_t *n_solves) {
+int dust_ctx_profile_read(dust_ctx *ctx, double *ms_absorb, double *ms_solve, double *ms_emit,
+                          int64_t *n_solves) {
     if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard dg(ctx->device);
     if (dg.rc != DUST_OK) return dg.rc;
-    double a = 0.0, b = 0.0;
+    double a = 0.0, b = 0.0, c = 0.0;
     int64_t cnt = 0;
     int rc = DUST_OK;
-    for (size_t i = 0; i + 2 < ctx->prof_marks.size(); i += 3) {
+    for (size_t i = 0; i + 3 < ctx->prof_marks.size(); i += 4) {
         cudaEvent_t *e = &ctx->prof_marks[i];
-        float t01 = 0.f, t12 = 0.f;
-        if (cudaEventSynchronize(e[2]) != cudaSuccess || cudaEventElapsedTime(&t01, e[0], e[1]) != cudaSuccess ||
-            cudaEventElapsedTime(&t12, e[1], e[2]) != cudaSuccess) {
+        float t01 = 0.f, t12 = 0.f, t23 = 0.f;
+        if (cudaEventSynchronize(e[3]) != cudaSuccess || cudaEventElapsedTime(&t01, e[0], e[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t12, e[1], e[2]) != cudaSuccess ||
+            cudaEventElapsedTime(&t23, e[2], e[3]) != cudaSuccess) {
             rc = set_error(DUST_ECUDA, "profiling events could not be read");
             break;
         }
         a += t01;
         b += t12;
+        c += t23;
         ++cnt;
     }
     for (cudaEvent_t e : ctx->prof_marks) ctx->prof_pool.push_back(e);
     ctx->prof_marks.clear();
     if (ms_absorb) *ms_absorb = a;
-    if (ms_solve_emit) *ms_solve_emit = b;
+    if (ms_solve) *ms_solve = b;
+    if (ms_emit) *ms_emit = c;
     if (n_solves) *n_solves = cnt;
     return rc;
 }

@@ -1,32 +1,34 @@
-// Kernel (b): fused equilibrium-temperature solve and emission SED over a
-// work list of requests (one request for dust_solve, many for the server).
+// Kernel (b): equilibrium-temperature solve and emission SED, as two kernels
+// over a work list of requests (one request for dust_solve, many for the
+// server).
 //
-// A persistent CTA walks tiles of TC cells; a tile belongs to one request.
-// Per tile:
-//  load     S (scaled absorbed powers) and n of the tile into shared memory;
-//  phase 0  one warp per cell: exponent m_c of max_g n[c,g] (n enters the
-//           emission as n 2^-m_c);
-//  phase 1  (cell, grain) pairs spread over all threads, NB solves in flight
-//           per thread: the root of Eq. 7 from a guess out of the inverse
-//           table u(t), then Newton on the FP32 Hermite interpolant of
-//           t_g(u) = log2(P_g(2^u) / P_g(T_min)) inside the bracketing table
-//           interval, bisection when a step leaves it.  The paper's kernel 3
-//           iterated Newton with a fresh quadrature per step (Section 4.3);
-//           the device table removes those exponentials;
-//  phase 2  one thread per (cell, 8 consecutive wavelengths), Eq. 10:
-//             L[c,k] = 2^(m_c+q_k) sum_g (n 2^-m_c) Chat[g,k] t/(1-t),
-//             t = 2^(nax_k / T[c,g])  (one MUFU ex2 per term),
-//           the grain sum accumulated as a fraction N/D over groups of 8
-//           grains so that a group costs one reciprocal instead of eight:
-//             N <- N + t (w D - N),  D <- D - t D   (= sum of w t/(1-t)).
-//           Chat sits in shared memory ([k-group][grain][2] float4, odd row
-//           stride), in grain chunks when it does not fit, as the paper staged
-//           sigma per block (Section 4.4);
-//  resid    sum_k w_k L[c,k] / (4 pi sum_g n Pe) - 1.  Both sums are kept in
-//           float-float (error-free FP32 products and two-sums, ~48-bit) up to
-//           one FP64 combination per cell: this GPU's FP64 pipe is far too
-//           slow for per-term FP64.  Every reduction has a fixed order, so
-//           results depend neither on the batch nor on timing.
+// k_solve — one warp per cell, many warps per SM (the solve is a chain of
+// dependent table lookups, so it wants parallelism, not shared memory):
+//   the exponent m_c of max_g n[c,g] (n enters the emission as n 2^-m_c) and,
+//   per grain, the root of Eq. 7 from the scaled absorbed power S
+//   (A / P_g(T_min) = S 2^f_g): a guess from the inverse table u(t), then
+//   Newton on the FP32 Hermite interpolant of
+//   t_g(u) = log2(P_g(2^u) / P_g(T_min)) inside the bracketing table interval
+//   (bisection when a step leaves it).  The paper's kernel 3 iterated Newton
+//   with a fresh quadrature per step (Section 4.3); the device table removes
+//   those exponentials.  Writes T, flags and, when the emission follows, the
+//   pairs (1/T, n 2^-m_c) and a per-cell record (m_c, absorbed power).
+// k_emit — persistent, one thread per (two cells, 8 consecutive wavelengths),
+//   Eq. 10:
+//     L[c,k] = 2^(m_c+q_k) sum_g (n 2^-m_c) Chat[g,k] t/(1-t),
+//     t = 2^(nax_k / T[c,g])  (one MUFU ex2 per term),
+//   the grain sum accumulated as a fraction N/D over groups of 8 grains so
+//   that a group costs one reciprocal instead of eight:
+//     N <- N + t (w D - N),  D <- D - t D   (= sum of w t/(1-t)).
+//   Chat sits in shared memory ([k-group][grain][2] float4, odd row stride),
+//   in grain chunks when it does not fit, as the paper staged sigma per block
+//   (Section 4.4); the next tile's (1/T, n) pairs stream in with cp.async
+//   while the current tile computes.
+// resid = sum_k w_k L[c,k] / (4 pi sum_g n Pe) - 1: both sums are kept in
+//   float-float (error-free FP32 products and two-sums, ~48-bit) up to one
+//   FP64 combination per cell — this GPU's FP64 pipe is far too slow for
+//   per-term FP64.  Every reduction has a fixed order, so results depend
+//   neither on the batch nor on timing.
 #include "dust_internal.cuh"
 
 #include <algorithm>
@@ -34,8 +36,9 @@
 namespace dust {
 namespace {
 
-constexpr int NTH = 256;
-constexpr int NB = 4;   // solves in flight per thread in phase 1
+constexpr int NTH = 256;      // emission threads per CTA
+constexpr int SOLVE_TH = 128; // solve threads per CTA (one warp per cell)
+constexpr int NB_MAX = 4;     // grains per lane per pass in the solve, at most
 constexpr double FOUR_PI = 12.566370614359172954;
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -46,6 +49,11 @@ __device__ __forceinline__ float ex2_approx(float x) {
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 
@@ -64,15 +72,10 @@ __device__ __forceinline__ float hermite(float p0, float d0, float p1, float d1,
     return p0 + x * (d0 + x * (c2 + x * c3));
 }
 
-__device__ __forceinline__ float lg2_approx(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // Equilibrium temperatures of NB grains at once, branch-free: every lane runs
 // the table lookup on y clamped into the table, and the clamp / invalid cases
 // are selected at the end.  s: scaled absorbed power (A / P_g(T_min) = s 2^f_g).
+template <int NB>
 __device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[NB], const float (&s)[NB],
                                             const float4 (&gq)[NB], float (&T)[NB], int (&fl)[NB]) {
     float y[NB], ty[NB];
@@ -147,56 +150,184 @@ __device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[
     }
 }
 
+// NB grains per lane per pass: a launch takes NB = ceil(G8 / 32) of its
+// widest request (at most NB_MAX), so that a cell of up to 32 NB grains is
+// one pass with no idle lanes, and its n row is loaded once: the exponent
+// m_c of max_g n comes from the registers of that pass.
+template <int NB>
+__global__ void __launch_bounds__(SOLVE_TH) k_solve(const __grid_constant__ EmitBatch B) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * SOLVE_TH + threadIdx.x) >> 5;  // global warp
+    const int64_t nw = ((int64_t)gridDim.x * SOLVE_TH) >> 5;
+    int ri = 0;
+    for (int64_t u = gw; u < B.ncells; u += nw) {
+        while (ri + 1 < B.nreq && u >= B.req[ri + 1].cell_begin) ++ri;
+        const EmitReq &q = B.req[ri];
+        const DevTables &tb = q.tb;
+        const int G = tb.G, G8 = tb.G8, Gs = tb.Gs;
+        const int64_t cell = u - q.cell_begin;
+        const bool emit = (q.mode & EMIT_ON) != 0, rs = (q.mode & EMIT_RESID) != 0;
+        const float *Srow = q.S + cell * Gs;
+        const float *nrow = q.n + cell * G;
+        const bool one = G8 <= 32 * NB;
+        int mc = 0;
+        if (!one) {
+            float mx = 0.f;
+            for (int g = lane; g < G; g += 32) mx = fmaxf(mx, __ldg(nrow + g));
+            for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (mx > 0.f && mx < INFINITY) frexpf(mx, &mc);
+        }
+        float ah = 0.f, al = 0.f;  // absorbed power n 2^-m_c Pe 2^-Eg, float-float
+        for (int gb = 0; gb < G8; gb += 32 * NB) {
+            int gi[NB], fl[NB];
+            float s[NB], nv[NB], Tv[NB];
+            float4 gq[NB];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const int g = gb + lane + 32 * i;
+                const bool ok = g < G;
+                gi[i] = ok ? g : 0;
+                s[i] = ok ? __ldg(Srow + g) : 0.f;
+                nv[i] = ok ? __ldg(nrow + g) : 0.f;
+                gq[i] = __ldg(reinterpret_cast<const float4 *>(tb.gp) + gi[i]);
+            }
+            if (one) {
+                float mx = 0.f;
+#pragma unroll
+                for (int i = 0; i < NB; ++i) mx = fmaxf(mx, nv[i]);
+                for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                if (mx > 0.f && mx < INFINITY) frexpf(mx, &mc);
+            }
+            solve_batch<NB>(tb, gi, s, gq, Tv, fl);
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const int g = gb + lane + 32 * i;
+                if (g >= G8) continue;
+                float invT = 1.f / tb.Tmax, nn = 0.f;
+                if (g < G) {
+                    q.T[cell * G + g] = Tv[i];
+                    if (q.flags) q.flags[cell * G + g] = (uint8_t)fl[i];
+                    invT = rcp_approx(Tv[i]);
+                    nn = scale2(nv[i], -mc);
+                    if (rs) {
+                        const float4 gr = __ldg(tb.gres + g);
+                        const float se = fl[i] == DUST_FLAG_OK ? s[i]
+                                       : fl[i] == DUST_FLAG_LOW ? gr.z
+                                       : fl[i] == DUST_FLAG_HIGH ? gr.w : __int_as_float(0x7fc00000);
+                        const float xh = nn * se, xl = fmaf(nn, se, -xh);
+                        const float rh = xh * gr.x;
+                        ff_add(ah, al, rh, fmaf(xh, gr.x, -rh) + fmaf(xh, gr.y, xl * gr.x));
+                    }
+                }
+                if (emit) q.prep[cell * G8 + g] = make_float2(invT, nn);
+            }
+        }
+        if (emit) {
+            if (rs)
+                for (int o = 16; o; o >>= 1) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, ah, o), ol = __shfl_xor_sync(0xffffffffu, al, o);
+                    ff_add(ah, al, oh, ol);
+                }
+            if (lane == 0) {
+                CellInfo ci;
+                ci.mc = mc;
+                ci.pad = 0;
+                ci.absorbed = rs ? ldexp((double)ah + (double)al, mc + tb.Eg) : 0.0;
+                q.cell[cell] = ci;
+            }
+        }
+    }
+}
+
+// One grain's term for two wavelengths of one cell, folded into the group's
+// fraction N/D.  Every FP32 step is a packed (f32x2) operation: the FMA pipe,
+// not the MUFU, is the limit of this loop (an f32x2 FMA costs the FMA pipe
+// as much as two scalar ones, and each ex2 takes dispatch cycles from it),
+// so the step is kept to five packed operations per two terms.
 __device__ __forceinline__ void emit_pair(float2 nax, float2 iT, float2 nn, float2 cw, float2 &N, float2 &D) {
     const float2 a = __fmul2_rn(nax, iT);
     const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
     const float2 w = __fmul2_rn(nn, cw);
-    const float2 e = make_float2(fmaf(w.x, D.x, -N.x), fmaf(w.y, D.y, -N.y));
+    const float2 e = __ffma2_rn(w, D, make_float2(-N.x, -N.y));  // w D - N
     N = __ffma2_rn(t, e, N);
-    D = make_float2(fmaf(-t.x, D.x, D.x), fmaf(-t.y, D.y, D.y));
+    D = __ffma2_rn(make_float2(-t.x, -t.y), D, D);                // D (1 - t)
+}
+// The first grain of a group, from N = 0, D = 1: N = w t, D = 1 - t.
+__device__ __forceinline__ void emit_first(float2 nax, float2 iT, float2 nn, float2 cw, float2 &N, float2 &D) {
+    const float2 a = __fmul2_rn(nax, iT);
+    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+    N = __fmul2_rn(__fmul2_rn(nn, cw), t);
+    D = __ffma2_rn(make_float2(-t.x, -t.y), make_float2(1.f, 1.f), make_float2(1.f, 1.f));
 }
 
-__global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ EmitBatch B) {
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Request and first cell of global emission tile `tile`.
+__device__ __forceinline__ int emit_req_of(const EmitBatch &B, int64_t tile, int ri) {
+    while (ri + 1 < B.nreq && tile >= B.req[ri + 1].tile_begin) ++ri;
+    return ri;
+}
+
+// Issue the cp.async copies of a tile's (1/T, n) pairs into the pair-major
+// shared layout [pair][grain][2 cells] (padding cells of a ragged tile read
+// the dummy values instead).
+__device__ __forceinline__ void prefetch_tile(const EmitReq &q, int64_t local_tile, float *dstTN, int TNP, int tid) {
+    const int G8 = q.tb.G8, TC = q.TC;
+    const int64_t c0 = local_tile * TC;
+    const int nc = (int)((q.C - c0) < (int64_t)TC ? (q.C - c0) : (int64_t)TC);
+    for (int i = tid; i < TC * G8; i += NTH) {
+        const int c = i / G8, g = i - c * G8;
+        float *dst = dstTN + (size_t)(c >> 1) * TNP + 4 * g + 2 * (c & 1);
+        if (c < nc) cp_async8(dst, q.prep + (c0 + c) * G8 + g);
+        else *reinterpret_cast<float2 *>(dst) = make_float2(1.f / q.tb.Tmax, 0.f);
+    }
+    cp_async_commit();
+}
+
+__global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBatch B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
 
     int cur = -1;
-    // per-request shared-memory layout (byte offsets) and thread state.  The
-    // emission item of a thread is one k-group (8 wavelengths) of two
+    // per-request layout: Chat [NKG][CST] float4 | two (1/T, n) tiles [NP+1][TNP] | sEm
+    // The emission item of a thread is one k-group (8 wavelengths) of two
     // neighbouring cells; items run k-group-major over the threads, so the
     // lanes of a warp share few k-groups (Chat loads are near-broadcasts) and
     // one 16-byte load fetches (1/T, n) of both cells of a pair.
-    int oTN = 0, oS = 0, oN = 0, oM = 0, oAbs = 0, oEm = 0;
-    int TNP = 0, CST = 0;
-    int ipair = 0, ikg = 0;
+    int oTN = 0, oEm = 0, TNP = 0, CST = 0, TNB = 0;
+    int ipair = 0, ikg = 0, buf = 0;
+    int64_t pref = -1;  // global tile whose pairs sit (or are landing) in buffer `buf`
 
     for (int64_t tile = blockIdx.x; tile < B.ntiles; tile += gridDim.x) {
-        int ri = cur < 0 ? 0 : cur;
-        while (ri + 1 < B.nreq && tile >= B.req[ri + 1].tile_begin) ++ri;
+        int ri = emit_req_of(B, tile, cur < 0 ? 0 : cur);
         const EmitReq &q = B.req[ri];
         const DevTables &tb = q.tb;
-        const int G = tb.G, G8 = tb.G8, NKG = tb.NKG, K = tb.K, Gs = tb.Gs, TC = q.TC;
-        const bool emit = (q.mode & EMIT_ON) != 0, rs = (q.mode & EMIT_RESID) != 0;
-        const int NP = TC / 2;  // cell pairs per tile
+        const int G8 = tb.G8, NKG = tb.NKG, K = tb.K, TC = q.TC, NP = TC / 2;
+        const bool rs = (q.mode & EMIT_RESID) != 0;
         if (ri != cur) {
+            __syncthreads();  // the previous request is done with shared memory
+            cp_async_wait_all();
+            cur = ri;
             TNP = 4 * G8 + 4;
             CST = 2 * (q.resident ? G8 : q.GC) + 1;
-            __syncthreads();  // the previous request is done with shared memory
-            cur = ri;
-            oTN = emit ? NKG * CST * 16 : 0;
-            oS = oTN + (emit ? (NP + 1) * TNP * 4 : 0);
-            oN = oS + TC * G8 * 4;
-            oM = oN + TC * G8 * 4;
-            oAbs = oM + ((TC + 1) & ~1) * 4;
-            oEm = oAbs + TC * 8;
+            TNB = (NP + 1) * TNP;  // floats per (1/T, n) tile buffer
+            oTN = NKG * CST * 16;
+            oEm = oTN + 2 * TNB * 4;
             const bool okit = tid < NP * NKG;
             ikg = okit ? tid / NP : 0;
             ipair = okit ? tid - ikg * NP : NP;  // idle threads read the dummy pair row NP
-            float *dummy = reinterpret_cast<float *>(smem_raw + oTN) + (size_t)NP * TNP;
-            if (emit)
+            for (int b = 0; b < 2; ++b) {
+                float *dummy = reinterpret_cast<float *>(smem_raw + oTN) + (size_t)b * TNB + (size_t)NP * TNP;
                 for (int g = tid; g < G8; g += NTH)
                     *reinterpret_cast<float4 *>(dummy + 4 * g) = make_float4(1.f / tb.Tmax, 0.f, 1.f / tb.Tmax, 0.f);
-            if (emit && q.resident) {
+            }
+            if (q.resident) {
                 const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
                 float4 *dst = reinterpret_cast<float4 *>(smem_raw);
                 for (int i = tid; i < NKG * 2 * G8; i += NTH) {
@@ -204,102 +335,31 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
                     dst[(size_t)kg * CST + o] = __ldg(src + i);
                 }
             }
+            pref = -1;
         }
         float4 *sC = reinterpret_cast<float4 *>(smem_raw);
-        float *sTN = reinterpret_cast<float *>(smem_raw + oTN);
-        float *sS = reinterpret_cast<float *>(smem_raw + oS);
-        float *sN = reinterpret_cast<float *>(smem_raw + oN);
-        int *sM = reinterpret_cast<int *>(smem_raw + oM);
-        double *sAbs = reinterpret_cast<double *>(smem_raw + oAbs);
+        float *sTN0 = reinterpret_cast<float *>(smem_raw + oTN);
         float2 *sEm = reinterpret_cast<float2 *>(smem_raw + oEm);
-        const int64_t c0 = (tile - q.tile_begin) * TC;
+        const int64_t lt = tile - q.tile_begin;
+        const int64_t c0 = lt * TC;
         const int nc = (int)((q.C - c0) < (int64_t)TC ? (q.C - c0) : (int64_t)TC);
-        const int npair = TC * G8;
         __syncthreads();  // previous tile finished with shared memory
-        // ---- load S and n of the tile (coalesced; padding grains read as 0)
-        for (int i = tid; i < npair; i += NTH) {
-            const int c = i / G8, g = i - c * G8;
-            const bool okv = c < nc && g < G;
-            sS[i] = okv ? __ldg(q.S + (c0 + c) * Gs + g) : 0.f;
-            sN[i] = okv ? __ldg(q.n + (c0 + c) * G + g) : 0.f;
+        if (pref != tile) {  // not prefetched (first tile of a request)
+            buf = 0;
+            prefetch_tile(q, lt, sTN0, TNP, tid);
         }
+        cp_async_wait_all();
         __syncthreads();
-        // ---- phase 0: per-cell exponent of max_g n
-        for (int c = warp; c < TC; c += NTH / 32) {
-            float mx = 0.f;
-            for (int g = lane; g < G8; g += 32) mx = fmaxf(mx, sN[c * G8 + g]);
-            for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            int mc = 0;
-            if (mx > 0.f && mx < INFINITY) frexpf(mx, &mc);
-            if (lane == 0) sM[c] = mc;
+        float *sTN = sTN0 + (size_t)buf * TNB;
+        // prefetch the next tile of this request into the other buffer
+        const int64_t nt = tile + gridDim.x;
+        if (nt < B.ntiles && emit_req_of(B, nt, ri) == ri) {
+            prefetch_tile(q, nt - q.tile_begin, sTN0 + (size_t)(buf ^ 1) * TNB, TNP, tid);
+            pref = nt;
+        } else {
+            pref = -1;
         }
-        __syncthreads();
-        // ---- phase 1: temperatures, NB pairs per thread per round
-        const float invG8 = 1.f / (float)G8;
-        for (int p0 = 0; p0 < npair; p0 += NTH * NB) {
-            int gi[NB], pi[NB], ci[NB];
-            bool ok[NB];
-            float s[NB], nv[NB], Tv[NB];
-            float4 gq[NB];
-            int fl[NB];
-#pragma unroll
-            for (int i = 0; i < NB; ++i) {
-                pi[i] = p0 + tid + NTH * i;
-                const bool in = pi[i] < npair;
-                // p / G8 through a float reciprocal: exact, (p + 1/2) / G8 is >= 1/(2 G8)
-                // away from an integer and p < 2^15
-                ci[i] = in ? (int)(((float)pi[i] + 0.5f) * invG8) : 0;
-                gi[i] = in ? pi[i] - ci[i] * G8 : 0;
-                ok[i] = in && ci[i] < nc && gi[i] < G;
-                s[i] = ok[i] ? sS[pi[i]] : 0.f;
-                nv[i] = in ? sN[pi[i]] : 0.f;
-                if (!ok[i]) gi[i] = 0;
-                gq[i] = __ldg(reinterpret_cast<const float4 *>(tb.gp) + gi[i]);
-            }
-            solve_batch(tb, gi, s, gq, Tv, fl);
-#pragma unroll
-            for (int i = 0; i < NB; ++i) {
-                if (pi[i] >= npair) continue;
-                const int c = ci[i], g = pi[i] - c * G8;
-                float invT = 1.f / tb.Tmax, nn = 0.f, rh = 0.f, rl = 0.f;
-                if (ok[i]) {
-                    const int64_t cell = c0 + c;
-                    q.T[cell * G + g] = Tv[i];
-                    if (q.flags) q.flags[cell * G + g] = (uint8_t)fl[i];
-                    invT = __frcp_rn(Tv[i]);
-                    nn = scale2(nv[i], -sM[c]);
-                    if (rs) {
-                        // n 2^-m_c Pe 2^-Eg in float-float, Pe = s gscale (or the clamp powers)
-                        const float4 gr = __ldg(tb.gres + g);
-                        const float se = fl[i] == DUST_FLAG_OK ? s[i]
-                                       : fl[i] == DUST_FLAG_LOW ? gr.z
-                                       : fl[i] == DUST_FLAG_HIGH ? gr.w : __int_as_float(0x7fc00000);
-                        const float xh = nn * se, xl = fmaf(nn, se, -xh);
-                        rh = xh * gr.x;
-                        rl = fmaf(xh, gr.x, -rh) + fmaf(xh, gr.y, xl * gr.x);
-                    }
-                }
-                if (emit)
-                    *reinterpret_cast<float2 *>(sTN + (size_t)(c >> 1) * TNP + 4 * g + 2 * (c & 1)) =
-                        make_float2(invT, nn);
-                if (rs) { sS[pi[i]] = rh; sN[pi[i]] = rl; }  // this thread's own slots
-            }
-        }
-        __syncthreads();
-        // absorbed power per cell, reduced over grains in a fixed order
-        if (rs) {
-            for (int c = warp; c < TC; c += NTH / 32) {
-                float h = 0.f, l = 0.f;
-                for (int g = lane; g < G8; g += 32) ff_add(h, l, sS[c * G8 + g], sN[c * G8 + g]);
-                for (int o = 16; o; o >>= 1) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
-                    ff_add(h, l, oh, ol);
-                }
-                if (lane == 0) sAbs[c] = ldexp((double)h + (double)l, sM[c] + tb.Eg);
-            }
-        }
-        if (!emit) continue;
-        // ---- phase 2: emission (two cells x 8 wavelengths per thread)
+        // ---- emission (two cells x 8 wavelengths per thread)
         float2 acc[2][4], nax2[4];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
@@ -317,17 +377,13 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
                     const int kg = i / (2 * gn), o = i - kg * 2 * gn;
                     sC[(size_t)kg * CST + o] = __ldg(src + ((size_t)kg * G8 + g0) * 2 + o);
                 }
+                __syncthreads();
             }
-            __syncthreads();
             const int goff = q.resident ? g0 : 0;
             const float4 *tnp = reinterpret_cast<const float4 *>(sTN + (size_t)ipair * TNP) + g0;
             const float4 *cp = sC + (size_t)ikg * CST + 2 * goff;
             for (int gg0 = 0; gg0 < gn; gg0 += RG) {
                 float2 N[2][4], D[2][4];
-#pragma unroll
-                for (int r = 0; r < 2; ++r)
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) { N[r][p] = make_float2(0.f, 0.f); D[r][p] = make_float2(1.f, 1.f); }
 #pragma unroll
                 for (int u = 0; u < RG; ++u) {
                     const float4 tn = tnp[gg0 + u];  // (1/T, n) of both cells
@@ -338,8 +394,13 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
                     const float2 iTb = make_float2(tn.z, tn.z), nb = make_float2(tn.w, tn.w);
 #pragma unroll
                     for (int p = 0; p < 4; ++p) {
-                        emit_pair(nax2[p], iTa, na, cw[p], N[0][p], D[0][p]);
-                        emit_pair(nax2[p], iTb, nb, cw[p], N[1][p], D[1][p]);
+                        if (u == 0) {
+                            emit_first(nax2[p], iTa, na, cw[p], N[0][p], D[0][p]);
+                            emit_first(nax2[p], iTb, nb, cw[p], N[1][p], D[1][p]);
+                        } else {
+                            emit_pair(nax2[p], iTa, na, cw[p], N[0][p], D[0][p]);
+                            emit_pair(nax2[p], iTb, nb, cw[p], N[1][p], D[1][p]);
+                        }
                     }
                 }
 #pragma unroll
@@ -359,7 +420,7 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
             const int c = 2 * ipair + r;
             if (c >= nc) continue;
             const int64_t cell = c0 + c;
-            const int mc = sM[c];
+            const int mc = q.cell[cell].mc;
             float sh = 0.f, sl = 0.f;
             const int kb = ikg * KQ;
 #pragma unroll
@@ -392,86 +453,135 @@ __global__ void __launch_bounds__(NTH, 2) k_solve_emit(const __grid_constant__ E
                     const float2 v = sEm[c * NKG + kg];
                     ff_add(h, l, v.x, v.y);
                 }
-                const double e = ldexp((double)h + (double)l, sM[c] + tb.Ew);
-                q.resid[c0 + c] = e / (FOUR_PI * sAbs[c]) - 1.0;
+                const CellInfo ci = q.cell[c0 + c];
+                const double e = ldexp((double)h + (double)l, ci.mc + tb.Ew);
+                q.resid[c0 + c] = e / (FOUR_PI * ci.absorbed) - 1.0;
             }
         }
+        buf ^= 1;
     }
+    cp_async_wait_all();
 }
 
 }  // namespace
 
-// Work-list geometry of one request: cells per tile, grain chunk, residency
+// Emission geometry of one request: cells per tile, grain chunk, residency
 // of the emission weights and the shared memory they need.
 EmitPlan plan_emit(const dust_ctx *ctx, bool emit) {
     const DevTables &tb = ctx->tb;
     EmitPlan p{};
-    const size_t budget = 113 * 1024;  // two CTAs per SM
-    // temperatures only: S and n of the tile, as many cells as fit (<= 64, even)
-    if (!emit) {
-        int tc = (int)std::min<size_t>(64, (budget - 4096) / ((size_t)8 * tb.G8 + 12)) & ~1;
-        p.TC = std::max(2, tc);
-        p.GC = tb.G8;
-        p.resident = 0;
-        p.smem = (size_t)2 * p.TC * tb.G8 * 4 + (size_t)((p.TC + 1) & ~1) * 4 + (size_t)p.TC * 8 +
-                 (size_t)p.TC * tb.NKG * 8 + 64;
-        return p;
-    }
     const int NP = std::max(1, std::min(32, NTH / tb.NKG));  // cell pairs per tile
     p.TC = 2 * NP;
-    auto fixed = [&](int TC) {  // sTN (+ dummy pair row), sS, sN, sM, sAbs, sEm
-        return (size_t)(TC / 2 + 1) * (4 * tb.G8 + 4) * 4 + (size_t)2 * TC * tb.G8 * 4 +
-               (size_t)((TC + 1) & ~1) * 4 + (size_t)TC * 8 + (size_t)TC * tb.NKG * 8 + 64;
-    };
-    const size_t full = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + fixed(p.TC);
+    if (!emit) { p.GC = tb.G8; p.resident = 0; p.smem = 0; return p; }
+    const size_t budget = 113 * 1024;  // two CTAs per SM
+    const size_t fixed = (size_t)2 * (NP + 1) * (4 * tb.G8 + 4) * 4 + (size_t)p.TC * tb.NKG * 8 + 64;
+    const size_t full = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + fixed;
     if (full <= budget) { p.GC = tb.G8; p.resident = 1; p.smem = full; return p; }
-    const size_t avail = budget > fixed(p.TC) ? budget - fixed(p.TC) : 0;
+    const size_t avail = budget > fixed ? budget - fixed : 0;
     int gc = (int)((avail / ((size_t)tb.NKG * 16) - 1) / 2) / RG * RG;
     gc = std::max(RG, std::min(gc, tb.G8));
     p.GC = gc;
     p.resident = 0;
-    p.smem = (size_t)tb.NKG * (2 * gc + 1) * 16 + fixed(p.TC);
+    p.smem = (size_t)tb.NKG * (2 * gc + 1) * 16 + fixed;
     return p;
 }
 
-int launch_emit_batch(const EmitBatch &B, size_t smem, int num_sms, cudaStream_t st) {
-    if (B.ntiles <= 0) return DUST_OK;
-    DUST_CUDA_TRY(cudaFuncSetAttribute(k_solve_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    DUST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_emit, NTH, smem));
-    per_sm = std::max(per_sm, 1);
-    const int64_t grid = std::min<int64_t>(B.ntiles, (int64_t)num_sms * per_sm);
-    k_solve_emit<<<(unsigned)grid, NTH, smem, st>>>(B);
-    DUST_CUDA_TRY(cudaGetLastError());
-    return DUST_OK;
+// Scratch bytes of a request of C cells: S [C][Gs] FP32, then (emission)
+// the (1/T, n) pairs [C][G8] and one CellInfo per cell, each 16-byte aligned.
+size_t scratch_bytes(const dust_ctx *ctx, int64_t C, bool emit) {
+    size_t b = ((size_t)C * ctx->tb.Gs * 4 + 15) & ~(size_t)15;
+    if (emit) b += (((size_t)C * ctx->tb.G8 * 8 + 15) & ~(size_t)15) + (size_t)C * sizeof(CellInfo);
+    return b;
 }
 
-void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const float *S, const float *n, float *T,
-                   float *L, int64_t ld, double *resid, uint8_t *flags, EmitReq &r) {
+ScratchView scratch_view(const dust_ctx *ctx, int64_t C, void *base) {
+    ScratchView v;
+    char *p = static_cast<char *>(base);
+    v.S = reinterpret_cast<float *>(p);
+    p += ((size_t)C * ctx->tb.Gs * 4 + 15) & ~(size_t)15;
+    v.prep = reinterpret_cast<float2 *>(p);
+    p += ((size_t)C * ctx->tb.G8 * 8 + 15) & ~(size_t)15;
+    v.cell = reinterpret_cast<CellInfo *>(p);
+    return v;
+}
+
+void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const ScratchView &sv, const float *n,
+                   float *T, float *L, int64_t ld, double *resid, uint8_t *flags, EmitReq &r) {
     r.tb = ctx->tb;
     r.C = C;
     r.ld = ld;
-    r.S = S;
+    r.tile_begin = 0;
+    r.cell_begin = 0;
+    r.S = sv.S;
     r.n = n;
     r.T = T;
     r.L = L;
     r.resid = resid;
     r.flags = flags;
+    r.prep = sv.prep;
+    r.cell = sv.cell;
     r.TC = p.TC;
     r.GC = p.GC;
     r.resident = p.resident;
     r.mode = ((L || resid) ? EMIT_ON : 0) | (resid ? EMIT_RESID : 0) | (L ? EMIT_STORE_L : 0);
 }
 
-int launch_solve_emit(const dust_ctx *ctx, int64_t C, const float *S, const float *n, float *T, float *L,
+// Numbers the cells and emission tiles of a filled batch; launches the solve
+// over every request, then the emission over the requests that want it.
+int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, cudaEvent_t between) {
+    int64_t cells = 0, tiles = 0;
+    for (int i = 0; i < B.nreq; ++i) {
+        EmitReq &r = B.req[i];
+        r.cell_begin = cells;
+        cells += r.C;
+    }
+    B.ncells = cells;
+    if (cells <= 0) return DUST_OK;
+    {
+        // one warp per cell, up to 16 CTAs of 4 warps per SM
+        int g8 = 8;
+        for (int i = 0; i < B.nreq; ++i) g8 = std::max(g8, B.req[i].tb.G8);
+        const int nb = std::min(NB_MAX, (g8 + 31) / 32);
+        const int64_t grid = std::min<int64_t>((cells * 32 + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
+        switch (nb) {
+            case 1: k_solve<1><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+            case 2: k_solve<2><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+            case 3: k_solve<3><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+            default: k_solve<4><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+        }
+        DUST_CUDA_TRY(cudaGetLastError());
+    }
+    if (between) DUST_CUDA_TRY(cudaEventRecord(between, st));
+    // emission work list: only the requests that want L or resid, in order
+    EmitBatch E;
+    E.nreq = 0;
+    for (int i = 0; i < B.nreq; ++i) {
+        if (!(B.req[i].mode & EMIT_ON)) continue;
+        EmitReq &r = E.req[E.nreq++];
+        r = B.req[i];
+        r.tile_begin = tiles;
+        tiles += (r.C + r.TC - 1) / r.TC;
+    }
+    E.ntiles = tiles;
+    E.ncells = 0;
+    if (tiles == 0) return DUST_OK;
+    DUST_CUDA_TRY(cudaFuncSetAttribute(k_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    DUST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emit, NTH, smem));
+    per_sm = std::max(per_sm, 1);
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * per_sm);
+    k_emit<<<(unsigned)grid, NTH, smem, st>>>(E);
+    DUST_CUDA_TRY(cudaGetLastError());
+    return DUST_OK;
+}
+
+int launch_solve_emit(const dust_ctx *ctx, int64_t C, const ScratchView &sv, const float *n, float *T, float *L,
                       int64_t ld, double *resid, uint8_t *flags, cudaStream_t st) {
     if (C <= 0) return DUST_OK;
     const EmitPlan p = plan_emit(ctx, L || resid);
     EmitBatch B;
     B.nreq = 1;
-    fill_emit_req(ctx, p, C, S, n, T, L, ld, resid, flags, B.req[0]);
-    B.req[0].tile_begin = 0;
-    B.ntiles = (C + p.TC - 1) / p.TC;
+    fill_emit_req(ctx, p, C, sv, n, T, L, ld, resid, flags, B.req[0]);
     return launch_emit_batch(B, p.smem, ctx->num_sms, st);
 }
 

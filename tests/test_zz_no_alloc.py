@@ -66,8 +66,16 @@ def test_noalloc_rejects_batches_beyond_its_array():
     wl = synth.make_workload(0, cells=np.arange(4))
     with Context.from_workload(wl) as ctx:
         cap = _lib.dust_noalloc_max_cells(ctx.handle)
-        assert cap == (16 << 20) // 16  # G = 16 grains: one 16-column scratch row per cell
-        J = torch.zeros((1, wl.K), device="cuda")
-        with pytest.raises(DustError) as e:
-            _lib.dust_solve_noalloc(ctx.handle, cap + 1, J.data_ptr(), wl.K, J.data_ptr(), J.data_ptr(), 0, 0, 0, 0)
-        assert e.value.code == _lib.DUST_EINVAL and "split the batch" in str(e.value)
+        # G = 16 grains: 64 B of absorbed powers + 128 B of (1/T, n) + 16 B per cell
+        assert cap == (64 << 20) // 208
+        # buffers sized for cap + 1 cells, so that the call would stay in bounds
+        # even if the check let it through; refused with and without outputs
+        out = ctx.alloc_outputs(cap + 1, wl.K)
+        J = torch.zeros((cap + 1, wl.K), device="cuda")
+        n = torch.zeros((cap + 1, wl.G), device="cuda")
+        for L, resid in ((out["L_buf"].data_ptr(), out["resid"].data_ptr()), (0, 0)):
+            with pytest.raises(DustError) as e:
+                _lib.dust_solve_noalloc(ctx.handle, cap + 1, J.data_ptr(), wl.K, n.data_ptr(), out["T"].data_ptr(),
+                                        L, resid, 0, 0)
+            assert e.value.code == _lib.DUST_EINVAL and "split the batch" in str(e.value)
+        torch.cuda.synchronize()
