@@ -419,11 +419,14 @@ def run_large(args, dev, local, ex2_rate):
 def run_serving(args, dev, local):
     """Request stream shaped like the serving workload: Poisson arrivals of
     solves from 64 snapshots, cells log-uniform 1e3-1e6, K in {100, 200, 350,
-    500}, G in {48, 96, 240}.  Request inputs are generated on the device just
-    before submission (same recipe as synth, seeded per request).  Measures the
-    saturated throughput with a closed loop, then a Poisson stream at
-    `serve_load` x that rate through the continuous-batching server (BF16x3),
-    and the same stream through a one-request-at-a-time FP32 loop."""
+    500}, G in {48, 96, 240}.  The inputs of every (K, G) grid are generated
+    once, before any timing, into one resident buffer as large as the grid's
+    largest request (same recipe as synth, seeded per grid); a request solves a
+    seeded slice of its grid's buffer, so the timed loops measure the server,
+    not the input generator.  Measures the saturated throughput with a closed
+    loop, then a Poisson stream at `serve_load` x that rate through the
+    continuous-batching server (BF16x3), and the same stream through a
+    one-request-at-a-time FP32 loop."""
     import numpy as np
     import torch
 
@@ -432,38 +435,41 @@ def run_serving(args, dev, local):
     from synth import workloads as W
 
     reqs = W.serve_requests(n_requests=args.serve_requests, rate_hz=1.0)
+    cmax = {}
+    for r in reqs:
+        cmax[(r["K"], r["G"])] = max(cmax.get((r["K"], r["G"]), 0), r["n_cells"])
     grids = {}
-    for K in W.SERVE_K:
-        for G in W.SERVE_G:
-            cfg = W.serve_snapshot_config(0, K, G, 8)
-            wl = synth.make_workload(cfg, cells=np.arange(1))
-            grids[(K, G)] = dict(
-                cfg=cfg, ld=(K + 3) // 4 * 4,
-                shape=torch.tensor(W.J_ISRF * W.stellar_shape(wl.lam), device=dev, dtype=torch.float64),
-                ext=torch.tensor((wl.lam / (0.55 * W.UM)) ** -1.3, device=dev, dtype=torch.float64),
-                n0=torch.tensor(W.size_weights(wl.sp_of_g, wl.a_of_g), device=dev, dtype=torch.float64),
-                mixed=Context.from_workload(wl, precision="bf16x3", device=local),
-                fp32=Context.from_workload(wl, precision="fp32", device=local))
-
-    def inputs(i):
-        r = reqs[i]
-        g = grids[(r["K"], r["G"])]
-        cfg, C, K = g["cfg"], r["n_cells"], r["K"]
+    for (K, G), C in cmax.items():
+        cfg = W.serve_snapshot_config(0, K, G, 8)
+        wl = synth.make_workload(cfg, cells=np.arange(1))
+        ld = (K + 3) // 4 * 4
         gen = torch.Generator(device=dev)
-        gen.manual_seed(cfg["seed"] * 1000003 + i)
+        gen.manual_seed(cfg["seed"] * 1000003 + K * 1009 + G)
         lo, hi = cfg["log10U"]
         U = 10.0 ** (torch.rand(C, generator=gen, device=dev, dtype=torch.float64) * (hi - lo) + lo)
         rho = torch.exp(torch.randn(C, generator=gen, device=dev, dtype=torch.float64))
         op = torch.rand(C, generator=gen, device=dev, dtype=torch.float64) < cfg["opaque_frac"]
         tau = torch.rand(C, generator=gen, device=dev, dtype=torch.float64) * (cfg["tau_V"][1] - cfg["tau_V"][0]) \
             + cfg["tau_V"][0]
-        Jb = torch.zeros((C, g["ld"]), dtype=torch.float32, device=dev)
-        Jb[:, :K] = U.float()[:, None] * g["shape"].float()[None, :]
-        idx = op.nonzero().squeeze(1)
-        if idx.numel():
-            Jb[idx, :K] *= torch.exp(-(tau[idx].float()[:, None] * g["ext"].float()[None, :]))
-        n = (rho[:, None] * g["n0"][None, :]).float()
-        return g, Jb[:, :K], n
+        shape = torch.tensor(W.J_ISRF * W.stellar_shape(wl.lam), device=dev, dtype=torch.float64)
+        ext = torch.tensor((wl.lam / (0.55 * W.UM)) ** -1.3, device=dev, dtype=torch.float64)
+        n0 = torch.tensor(W.size_weights(wl.sp_of_g, wl.a_of_g), device=dev, dtype=torch.float64)
+        Jb = torch.zeros((C, ld), dtype=torch.float32, device=dev)
+        att = torch.where(op[:, None], torch.exp(-(tau[:, None] * ext[None, :])), torch.ones_like(ext)[None, :])
+        Jb[:, :K] = (U[:, None] * shape[None, :] * att).float()
+        del att
+        grids[(K, G)] = dict(J=Jb[:, :K], n=(rho[:, None] * n0[None, :]).float().contiguous(), C=C,
+                             mixed=Context.from_workload(wl, precision="bf16x3", device=local),
+                             fp32=Context.from_workload(wl, precision="fp32", device=local))
+    torch.cuda.synchronize()
+    offs = np.random.default_rng(4243).random(len(reqs))
+
+    def inputs(i):
+        r = reqs[i]
+        g = grids[(r["K"], r["G"])]
+        C = r["n_cells"]
+        o = int(offs[i] * (g["C"] - C + 1))
+        return g, g["J"][o:o + C], g["n"][o:o + C]
 
     total_cells = sum(r["n_cells"] for r in reqs)
     total_solves = sum(r["n_cells"] * r["G"] for r in reqs)

@@ -208,8 +208,12 @@ int dust_ctx_profile_read(dust_ctx *ctx, double *ms_absorb, double *ms_solve, do
  * dust_server_create: the server allocates `hbm_budget_bytes` (>= 1 MiB) of
  * device memory for scratch up front.  max_inflight in [1, 4096].
  * dust_serve_submit: arguments as dust_solve (device buffers, caller-owned,
- * valid until the request finishes).  Returns a ticket; DUST_EBUSY when the
- * request's footprint exceeds the whole budget (it could never be admitted).
+ * valid until the request finishes).  `stream` is the stream that produced J
+ * and n (NULL = the legacy default stream): the call records an event there,
+ * and the request's first launch waits for it on the device, so inputs still
+ * being written when submit is called are safe and the caller need not
+ * synchronise.  Returns a ticket; DUST_EBUSY when the request's footprint
+ * exceeds the whole budget (it could never be admitted).
  * dust_serve_poll: *state = 0 queued, 1 active, 2 done, 3 cancelled (and
  * *latency_ms = submit-to-completion time, or the time so far).  A poll that
  * reports 2 or 3 releases the ticket (a later call returns DUST_ENOTFOUND);
@@ -231,13 +235,24 @@ typedef struct {
 int dust_server_create(dust_server **out, size_t hbm_budget_bytes, int max_inflight, int device);
 int dust_serve_submit(dust_server *srv, dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld,
                       const float *n, float *T, float *L, double *resid, uint8_t *flags,
-                      uint64_t *ticket);
+                      void *stream, uint64_t *ticket);
 int dust_serve_poll(dust_server *srv, uint64_t ticket, int *state, double *latency_ms);
 int dust_serve_wait(dust_server *srv, uint64_t ticket, double timeout_ms, double *latency_ms);
 int dust_serve_cancel(dust_server *srv, uint64_t ticket);
 int dust_server_stats(dust_server *srv, dust_serve_stats *out);
 int dust_server_reset_stats(dust_server *srv);
 void dust_server_destroy(dust_server *srv);
+
+/* Failure-detection probe (no counterpart in the paper): one thread waits on
+ * an mbarrier phase that nothing completes, through the same bounded wait the
+ * tensor-core absorption kernel uses for every pipeline hand-off, with a
+ * limit of limit_ms (0 < limit_ms <= 2000; kernels use 2000).  The wait gives
+ * up, records DUST_ETIMEOUT in a device status word and returns, so the
+ * context stays usable.  *device_status receives the status word (DUST_ETIMEOUT
+ * when the bound works) and *elapsed_ms the device time the wait took (either
+ * may be NULL).  Synchronises the device.  Returns DUST_EINVAL for a bad
+ * device or limit, DUST_ECUDA if the launch failed. */
+int dust_diag_wait_timeout(int device, double limit_ms, int *device_status, double *elapsed_ms);
 
 /* Diagnostics (no counterpart in the paper): measured issue rates on `device`
  * of the two pipes the emission kernel uses, MUFU ex2.approx and FP32 FMA, in

@@ -39,11 +39,12 @@ _SIGS = {
     "dust_ctx_check": (_i, [_p, _p]),
     "dust_ctx_profile": (_i, [_p, _i]),
     "dust_ctx_profile_read": (_i, [_p, _p, _p, _p, _p]),
+    "dust_diag_wait_timeout": (_i, [_i, _d, _p, _p]),
     "dust_diag_throughput": (_i, [_i, _p, _p]),
     "dust_solve_noalloc": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
     "dust_noalloc_max_cells": (_sz, [_p]),
     "dust_server_create": (_i, [ctypes.POINTER(_p), _sz, _i, _i]),
-    "dust_serve_submit": (_i, [_p, _p, _i64, _p, _i64, _p, _p, _p, _p, _p, ctypes.POINTER(ctypes.c_uint64)]),
+    "dust_serve_submit": (_i, [_p, _p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p, ctypes.POINTER(ctypes.c_uint64)]),
     "dust_serve_poll": (_i, [_p, ctypes.c_uint64, _p, _p]),
     "dust_serve_wait": (_i, [_p, ctypes.c_uint64, _d, _p]),
     "dust_serve_cancel": (_i, [_p, ctypes.c_uint64]),
@@ -177,9 +178,9 @@ def dust_server_create(hbm_budget_bytes, max_inflight, device):
     return out.value
 
 
-def dust_serve_submit(srv, ctx, n_cells, J, ld, n, T, L, resid, flags):
+def dust_serve_submit(srv, ctx, n_cells, J, ld, n, T, L, resid, flags, stream):
     t = ctypes.c_uint64()
-    check(lib().dust_serve_submit(srv, ctx, n_cells, J, ld, n, T, L, resid, flags, ctypes.byref(t)))
+    check(lib().dust_serve_submit(srv, ctx, n_cells, J, ld, n, T, L, resid, flags, stream, ctypes.byref(t)))
     return t.value
 
 
@@ -219,3 +220,10 @@ def dust_last_error():
 
 def dust_version():
     return lib().dust_version().decode()
+
+
+def dust_diag_wait_timeout(device, limit_ms):
+    """(device status word, elapsed ms) of the bounded-wait probe."""
+    st, ms = ctypes.c_int(), ctypes.c_double()
+    check(lib().dust_diag_wait_timeout(device, limit_ms, ctypes.byref(st), ctypes.byref(ms)))
+    return st.value, ms.value

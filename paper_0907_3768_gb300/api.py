@@ -119,15 +119,20 @@ class Context:
                              _ptr(out["L_buf"]), _ptr(out["resid"]), _ptr(out["flags"]), sptr)
         return out
 
-    def submit(self, server, J, n, out=None, want_L=True, want_resid=True, want_flags=True):
+    def submit(self, server, J, n, out=None, want_L=True, want_resid=True, want_flags=True, stream=None):
         """Queue a solve on `server` (continuous batching); returns (ticket, out).
-        J, n and out must stay alive until the request finishes."""
+        J, n and out must stay alive until the request finishes.  `stream`
+        (default: the current torch stream) is where J and n were produced;
+        the server waits for it on the device, so no synchronisation is needed."""
         C, ld = self._check_inputs(J, n)
         if out is None:
             out = self.alloc_outputs(C, ld, want_L, want_resid, want_flags)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         t = _lib.dust_serve_submit(server.handle, self.handle, C, J.data_ptr(), ld, n.data_ptr(),
                                    out["T"].data_ptr(), _ptr(out["L_buf"]), _ptr(out["resid"]),
-                                   _ptr(out["flags"]))
+                                   _ptr(out["flags"]), sptr)
         return t, out
 
     def solve_host(self, J, n, T=None, L=None, resid=None, flags=None):

@@ -199,7 +199,7 @@ __global__ void k_w32(int K, int G, int Gs, int Kw, const double *W, const doubl
 }
 
 // Emission constants: q_k, Chat (split into two float4 halves per group of 8
-// wavelengths) and nax_k; padding wavelengths get Chat = 0 and nax = -1.
+// wavelengths) and nax_k; padding wavelengths get Chat = 0 and nax = -1e30 (t = 0).
 __global__ void k_emis(int K, int G, int G8, int Kp, int NKG, const double *lam, const double *C,
                        float *Chat, int *qexp, float *nax) {
     int k = blockIdx.x;
@@ -220,7 +220,7 @@ __global__ void k_emis(int K, int G, int G8, int Kp, int NKG, const double *lam,
     }
     if (threadIdx.x == 0) {
         qexp[k] = q;
-        nax[k] = (k < K) ? (float)(-LOG2E_D * H_PL * C_LI / (lam[k] * K_BO)) : -1.0f;
+        nax[k] = (k < K) ? (float)(-LOG2E_D * H_PL * C_LI / (lam[k] * K_BO)) : -1e30f;
     }
 }
 

@@ -1,8 +1,10 @@
 // Diagnostics: issue-rate microbenchmarks of the two pipes the emission
-// kernel lives on (MUFU ex2 and FP32 FMA), used as its roofline denominators.
-// Each thread runs 8 independent dependency chains; nothing is read from
-// memory and each thread writes one float.
+// kernel lives on (MUFU ex2 and FP32 FMA), used as its roofline denominators
+// (each thread runs 8 independent dependency chains; nothing is read from
+// memory and each thread writes one float), and a probe of the bounded
+// mbarrier wait that the tensor-core GEMM relies on for failure detection.
 #include "dust_internal.cuh"
+#include "mbar.cuh"
 
 namespace dust {
 namespace {
@@ -39,6 +41,25 @@ __global__ void k_ffma_rate(int iters, float a, float b, float *sink) {
 #pragma unroll
     for (int i = 0; i < CH; ++i) s += x[i];
     sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// One thread waits on phase 0 of an mbarrier that expects one arrival and
+// gets none: the wait must give up after limit_ns, record DUST_ETIMEOUT and
+// return, exactly as a GEMM warp whose producer stalled would.
+__global__ void k_wait_probe(unsigned long long limit_ns, int *status, unsigned long long *elapsed_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long t0 = globaltimer_ns();
+        const bool ok = mbar_wait(&bar, 0, &abort_flag, status, limit_ns);
+        *elapsed_ns = globaltimer_ns() - t0;
+        if (ok) record_status(status, DUST_EINVAL);  // a phase nobody completed completed
+    }
 }
 
 }  // namespace
@@ -85,5 +106,35 @@ extern "C" int dust_diag_throughput(int device, double *ex2_per_s, double *ffma_
     if (err != cudaSuccess) return set_error(DUST_ECUDA, "diag kernels failed: %s", cudaGetErrorString(err));
     if (ex2_per_s) *ex2_per_s = best_ex2;
     if (ffma_per_s) *ffma_per_s = best_fma;
+    return DUST_OK;
+}
+
+extern "C" int dust_diag_wait_timeout(int device, double limit_ms, int *device_status, double *elapsed_ms) {
+    if (!(limit_ms > 0.0 && limit_ms <= 2000.0)) return set_error(DUST_EINVAL, "limit_ms must lie in (0, 2000]");
+    int ndev = 0;
+    DUST_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return set_error(DUST_EINVAL, "device %d of %d", device, ndev);
+    int prev = 0;
+    DUST_CUDA_TRY(cudaGetDevice(&prev));
+    DUST_CUDA_TRY(cudaSetDevice(device));
+    void *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 16);
+    int st = 0;
+    unsigned long long ns = 0;
+    if (e == cudaSuccess) e = cudaMemset(buf, 0, 16);
+    if (e == cudaSuccess) {
+        int *status = static_cast<int *>(buf);
+        unsigned long long *el = reinterpret_cast<unsigned long long *>(static_cast<char *>(buf) + 8);
+        k_wait_probe<<<1, 32>>>((unsigned long long)(limit_ms * 1e6), status, el);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&ns, el, sizeof(ns), cudaMemcpyDeviceToHost);
+    }
+    if (buf) cudaFree(buf);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) return set_error(DUST_ECUDA, "wait probe failed: %s", cudaGetErrorString(e));
+    if (device_status) *device_status = st;
+    if (elapsed_ms) *elapsed_ms = (double)ns * 1e-6;
     return DUST_OK;
 }

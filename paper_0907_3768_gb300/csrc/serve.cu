@@ -51,6 +51,8 @@ struct ServeReq {
     int state = RS_QUEUED;
     int status = DUST_OK;
     double t_submit = 0, t_done = 0;
+    cudaEvent_t ready = nullptr;  // recorded on the producer's stream at submit
+    bool ready_waited = false;    // the server stream waits on it once
 };
 
 // First-fit allocator over one device allocation (offsets in bytes).
@@ -139,6 +141,10 @@ size_t footprint_of(const dust_ctx *ctx, int64_t C, int64_t ld, bool L, bool res
 }
 
 void finish_req(dust_server *s, ServeReq *r, int state, int status) {
+    if (r->ready) {  // the server stream is past its wait (or never reached it)
+        s->ev_pool.push_back(r->ready);
+        r->ready = nullptr;
+    }
     r->state = state;
     r->status = status;
     r->t_done = now_ms();
@@ -213,6 +219,16 @@ ScratchView part_view(const Part &p) {
 }
 
 int launch_round(dust_server *s, const std::vector<Part> &parts) {
+    // a request's first round waits (on the device) for the work its
+    // producer had queued before submitting
+    for (const Part &p : parts) {
+        ServeReq *r = p.r;
+        if (r->ready && !r->ready_waited) {
+            if (cudaStreamWaitEvent(s->st, r->ready, 0) != cudaSuccess)
+                return set_error(DUST_ECUDA, "cudaStreamWaitEvent on a request's input event failed");
+            r->ready_waited = true;
+        }
+    }
     // absorption GEMMs, one launch per precision
     for (int prec = DUST_PREC_FP32; prec <= DUST_PREC_FP16X3; ++prec) {
         if (prec == DUST_PREC_FP32) {
@@ -384,7 +400,7 @@ int dust_server_create(dust_server **out, size_t hbm_budget_bytes, int max_infli
 }
 
 int dust_serve_submit(dust_server *s, dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n,
-                      float *T, float *L, double *resid, uint8_t *flags, uint64_t *ticket) {
+                      float *T, float *L, double *resid, uint8_t *flags, void *stream, uint64_t *ticket) {
     if (!s || !ctx || !ticket) return set_error(DUST_EINVAL, "server, ctx and ticket must be non-NULL");
     if (ctx->device != s->device) return set_error(DUST_EINVAL, "context and server on different devices");
     if (n_cells < 0) return set_error(DUST_EINVAL, "n_cells < 0");
@@ -411,10 +427,38 @@ int dust_serve_submit(dust_server *s, dust_ctx *ctx, int64_t n_cells, const floa
     r->ld = ld;
     r->J = J; r->n = n; r->T = T; r->L = L; r->resid = resid; r->flags = flags;
     r->s_bytes = scratch_bytes(ctx, std::max<int64_t>(n_cells, 1), L || resid);
+    if (n_cells > 0) {
+        // mark the producer's position: J and n are complete once the work
+        // queued on `stream` so far has run
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (!s->ev_pool.empty()) { r->ready = s->ev_pool.back(); s->ev_pool.pop_back(); }
+        }
+        int prev = -1;
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e == cudaSuccess && prev != s->device) e = cudaSetDevice(s->device);
+        if (e == cudaSuccess && !r->ready) e = cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(r->ready, (cudaStream_t)stream);
+        if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (r->ready) {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->ev_pool.push_back(r->ready);
+            }
+            delete r;
+            return set_error(DUST_ECUDA, "recording the input event on the producer stream failed: %s",
+                             cudaGetErrorString(e));
+        }
+    }
     r->t_submit = now_ms();
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (s->stop) { delete r; return set_error(DUST_EINVAL, "server is shutting down"); }
+        if (s->stop) {
+            if (r->ready) s->ev_pool.push_back(r->ready);
+            delete r;
+            return set_error(DUST_EINVAL, "server is shutting down");
+        }
         r->ticket = s->next_ticket++;
         s->by_ticket[r->ticket] = r;
         s->submitted++;
@@ -484,6 +528,10 @@ int dust_serve_cancel(dust_server *s, uint64_t ticket) {
     ServeReq *r = it->second;
     if (r->state == RS_QUEUED) {
         s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+        if (r->ready) {  // never waited on: free to be recorded again
+            s->ev_pool.push_back(r->ready);
+            r->ready = nullptr;
+        }
         r->state = RS_CANCELLED;
         r->t_done = now_ms();
         s->cancelled++;
@@ -556,6 +604,8 @@ void dust_server_destroy(dust_server *s) {
     cudaSetDevice(s->device);
     cudaStreamSynchronize(s->st);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    for (auto &kv : s->by_ticket)
+        if (kv.second->ready) cudaEventDestroy(kv.second->ready);
     cudaStreamDestroy(s->st);
     cudaFree(s->arena_mem);
     cudaSetDevice(prev);

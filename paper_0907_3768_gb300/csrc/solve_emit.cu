@@ -40,6 +40,8 @@ constexpr int NTH = 256;      // emission threads per CTA
 constexpr int SOLVE_TH = 128; // solve threads per CTA (one warp per cell)
 constexpr int NB_MAX = 4;     // grains per lane per pass in the solve, at most
 constexpr double FOUR_PI = 12.566370614359172954;
+// 1/T of padding grains and cells: every t = 2^(nax_k / T) of theirs is 0
+constexpr float PAD_INV_T = 1e30f;
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -203,7 +205,7 @@ __global__ void __launch_bounds__(SOLVE_TH) k_solve(const __grid_constant__ Emit
             for (int i = 0; i < NB; ++i) {
                 const int g = gb + lane + 32 * i;
                 if (g >= G8) continue;
-                float invT = 1.f / tb.Tmax, nn = 0.f;
+                float invT = PAD_INV_T, nn = 0.f;
                 if (g < G) {
                     q.T[cell * G + g] = Tv[i];
                     if (q.flags) q.flags[cell * G + g] = (uint8_t)fl[i];
@@ -281,11 +283,16 @@ __device__ __forceinline__ void prefetch_tile(const EmitReq &q, int64_t local_ti
     const int G8 = q.tb.G8, TC = q.TC;
     const int64_t c0 = local_tile * TC;
     const int nc = (int)((q.C - c0) < (int64_t)TC ? (q.C - c0) : (int64_t)TC);
+    // (c, g) of element i = tid + j NTH, advanced without a division per step
+    const int dc = NTH / G8, dg = NTH - dc * G8;
+    int c = tid / G8, g = tid - c * G8;
     for (int i = tid; i < TC * G8; i += NTH) {
-        const int c = i / G8, g = i - c * G8;
         float *dst = dstTN + (size_t)(c >> 1) * TNP + 4 * g + 2 * (c & 1);
         if (c < nc) cp_async8(dst, q.prep + (c0 + c) * G8 + g);
-        else *reinterpret_cast<float2 *>(dst) = make_float2(1.f / q.tb.Tmax, 0.f);
+        else *reinterpret_cast<float2 *>(dst) = make_float2(PAD_INV_T, 0.f);
+        c += dc;
+        g += dg;
+        if (g >= G8) { g -= G8; ++c; }
     }
     cp_async_commit();
 }
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
             for (int b = 0; b < 2; ++b) {
                 float *dummy = reinterpret_cast<float *>(smem_raw + oTN) + (size_t)b * TNB + (size_t)NP * TNP;
                 for (int g = tid; g < G8; g += NTH)
-                    *reinterpret_cast<float4 *>(dummy + 4 * g) = make_float4(1.f / tb.Tmax, 0.f, 1.f / tb.Tmax, 0.f);
+                    *reinterpret_cast<float4 *>(dummy + 4 * g) = make_float4(PAD_INV_T, 0.f, PAD_INV_T, 0.f);
             }
             if (q.resident) {
                 const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);

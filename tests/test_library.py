@@ -82,7 +82,7 @@ def test_server_null_arguments(L):
     assert L.dust_server_create(ctypes.byref(out), 1000, 4, 0) == _lib.DUST_EINVAL  # budget < 1 MiB
     assert L.dust_server_create(ctypes.byref(out), 1 << 30, 0, 0) == _lib.DUST_EINVAL
     t = ctypes.c_uint64()
-    assert L.dust_serve_submit(None, None, 1, None, 4, None, None, None, None, None, ctypes.byref(t)) == \
+    assert L.dust_serve_submit(None, None, 1, None, 4, None, None, None, None, None, None, ctypes.byref(t)) == \
         _lib.DUST_EINVAL
     assert L.dust_serve_poll(None, 1, None, None) == _lib.DUST_EINVAL
     assert L.dust_serve_wait(None, 1, 1.0, None) == _lib.DUST_EINVAL
@@ -95,3 +95,9 @@ def test_python_wrapper_raises(L):
     with pytest.raises(_lib.DustError) as e:
         _lib.dust_ctx_create(1, 0, 0, 1, 0, 2.0, 3000.0, 0, 0, 0)
     assert e.value.code == _lib.DUST_EINVAL
+
+
+def test_wait_probe_rejects_bad_limits(L):
+    # argument checks come before any CUDA call, so this needs no GPU
+    for bad in (0.0, -1.0, 2000.5, float("nan")):
+        assert L.dust_diag_wait_timeout(0, bad, None, None) == _lib.DUST_EINVAL

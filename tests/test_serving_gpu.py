@@ -134,3 +134,30 @@ def test_zero_cell_request_and_shutdown_with_queue():
     for c in ctxs.values():
         assert c.check() == 0
         c.close()
+
+
+def test_submit_waits_for_the_producer_stream():
+    """Inputs still being written on the producer's stream when submit is
+    called: the server's first launch for the request waits for them on the
+    device, so the result is bitwise that of a solve on finished inputs."""
+    from paper_0907_3768_gb300 import Context, Server
+
+    wl = _request_data(200, 96, 20000, snapshot=3)
+    J_src, n_src = _padded(wl.J), torch.from_numpy(wl.n).cuda()
+    with Context.from_workload(wl, precision="bf16x3") as ctx:
+        ref = ctx.solve(J_src, n_src)
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            J = torch.empty_like(J_src)
+            n = torch.empty_like(n_src)
+            torch.cuda._sleep(100_000_000)  # a bounded device-side delay before the copies
+            J.copy_(J_src)
+            n.copy_(n_src)
+        with Server(1 << 30, max_inflight=4) as srv:
+            t, out = ctx.submit(srv, J, n, stream=side)  # no synchronisation before submit
+            srv.wait(t, 60000.0)
+        torch.cuda.synchronize()
+        for k in ("T", "L", "resid", "flags"):
+            assert torch.equal(out[k], ref[k]), k
