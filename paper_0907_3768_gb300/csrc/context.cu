@@ -388,6 +388,12 @@ int build_context(dust_ctx *ctx, const double *lambda, const double *w, const do
         for (int k = 0; k < K; ++k) wq[k] = (float)std::ldexp(w[k], q[k] - Ew);
         DUST_CUDA_TRY(cudaMemcpy(base + o_wq, wq.data(), sizeof(float) * K, cudaMemcpyHostToDevice));
         tb.Ew = Ew;
+        // the residual's constant 2^(Ew - Eg) / (4 pi) as a float-float mantissa and an exponent
+        int e = 0;
+        const double v = std::frexp(std::ldexp(1.0 / (4.0 * 3.14159265358979323846), Ew - tb.Eg), &e);
+        tb.rc_hi = (float)v;
+        tb.rc_lo = (float)(v - (double)tb.rc_hi);
+        tb.rc_exp = e;
     }
     DUST_CUDA_TRY(cudaDeviceSynchronize());
     return DUST_OK;

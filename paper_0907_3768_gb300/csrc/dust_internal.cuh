@@ -51,12 +51,14 @@ struct DevTables {
     const float4 *gres;       // [G] residual constants: gscale 2^-Eg as float-float (x, y),
                               //     S of a grain clamped low (z = 2^-f) and high (w = Pmax / gscale)
     int Eg;
-    const float *nax;         // [Kp] -log2(e) h c / (lambda_k k_B), 0 in the padding
+    const float *nax;         // [Kp] -log2(e) h c / (lambda_k k_B), -1e30 in the padding
     const float *Chat;        // [NKG][G8][2][4] scaled emission weights (see context.cu)
     const int *qexp;          // [Kp] per-wavelength exponent of Chat
     const double *w;          // [K] quadrature weights
     const float *wq;          // [K] w_k 2^(q_k - Ew) (residual of the scaled emission sums)
     int Ew;
+    float rc_hi, rc_lo;       // 2^(Ew - Eg) / (4 pi) = (rc_hi + rc_lo) 2^rc_exp, rc_hi in [1/2, 1)
+    int rc_exp;
     int *status;              // device status word (dust_status)
 };
 
@@ -66,10 +68,12 @@ constexpr int MAXREQ = 32;
 enum EmitMode { EMIT_ON = 1, EMIT_RESID = 2, EMIT_STORE_L = 4 };
 
 // Per-cell record passed from the solve to the emission: exponent m_c of
-// max_g n[c,g] and the absorbed power sum_g n Pe (residual denominator / 4 pi).
+// max_g n[c,g] and the absorbed power sum_g n Pe = (ah + al) 2^(m_c + Eg)
+// as a float-float pair (the residual's denominator / 4 pi).
 struct CellInfo {
-    int mc, pad;
-    double absorbed;
+    int mc;
+    float ah, al;
+    int pad;
 };
 
 // A request's scratch: S [C][Gs] FP32, then (emission only) the pairs

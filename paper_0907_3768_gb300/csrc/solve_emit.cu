@@ -25,10 +25,11 @@
 //   (Section 4.4); the next tile's (1/T, n) pairs stream in with cp.async
 //   while the current tile computes.
 // resid = sum_k w_k L[c,k] / (4 pi sum_g n Pe) - 1: both sums are kept in
-//   float-float (error-free FP32 products and two-sums, ~48-bit) up to one
-//   FP64 combination per cell — this GPU's FP64 pipe is far too slow for
-//   per-term FP64.  Every reduction has a fixed order, so results depend
-//   neither on the batch nor on timing.
+//   float-float (error-free FP32 products and two-sums, ~48-bit) and their
+//   quotient is taken in float-float too, so the path has no FP64 arithmetic
+//   (this GPU's FP64 pipe issues two operations per clock per SM); only the
+//   stored residual is widened to double.  Every reduction has a fixed order,
+//   so results depend neither on the batch nor on timing.
 #include "dust_internal.cuh"
 
 #include <algorithm>
@@ -39,7 +40,6 @@ namespace {
 constexpr int NTH = 256;      // emission threads per CTA
 constexpr int SOLVE_TH = 128; // solve threads per CTA (one warp per cell)
 constexpr int NB_MAX = 4;     // grains per lane per pass in the solve, at most
-constexpr double FOUR_PI = 12.566370614359172954;
 // 1/T of padding grains and cells: every t = 2^(nax_k / T) of theirs is 0
 constexpr float PAD_INV_T = 1e30f;
 
@@ -64,6 +64,25 @@ __device__ __forceinline__ void ff_add(float &h, float &l, float a, float b) {
     const float t = h + a, bp = t - h;
     l += ((h - (t - bp)) + (a - bp)) + b;
     h = t;
+}
+
+// Energy-balance residual emitted / (4 pi absorbed) - 1 of a cell, with
+// emitted = (h + l) 2^(m_c + Ew) and absorbed = (ah + al) 2^(m_c + Eg), all in
+// FP32: both sums are split into mantissa and exponent, their quotient is
+// taken in float-float (a reciprocal estimate corrected by an exact FMA
+// remainder, ~2^-44 relative), multiplied by 2^(Ew - Eg) / (4 pi), and 1 is
+// subtracted where the quotient is near 1, so that the subtraction is exact.
+__device__ __forceinline__ float residual(float h, float l, float ah, float al, const DevTables &tb) {
+    int he = 0, ae = 0;
+    const float hm = frexpf(h, &he), am = frexpf(ah, &ae);
+    const float lm = ldexpf(l, -he), alm = ldexpf(al, -ae);
+    const float r0 = rcp_approx(am);
+    const float q1 = hm * r0;
+    const float q2 = (fmaf(-q1, am, hm) + lm - q1 * alm) * r0;
+    const float p1 = q1 * tb.rc_hi;
+    const float pe = fmaf(q1, tb.rc_hi, -p1) + fmaf(q1, tb.rc_lo, q2 * tb.rc_hi);
+    const int E = max(-252, min(252, he - ae + tb.rc_exp));
+    return (scale2(p1, E) - 1.f) + scale2(pe, E);
 }
 
 // Cubic Hermite on [0,1] with end values p0, p1 and end slopes d0, d1.
@@ -152,28 +171,58 @@ __device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[
     }
 }
 
+// S and (when the emission follows) n of one pass of a cell: grains
+// gb + lane + 32 i.
+template <int NB>
+__device__ __forceinline__ void load_pass(const EmitReq &q, int64_t cell, int gb, int lane, float (&s)[NB],
+                                          float (&nv)[NB]) {
+    const int G = q.tb.G;
+    const bool with_n = (q.mode & EMIT_ON) != 0;
+    const float *Srow = q.S + cell * q.tb.Gs;
+    const float *nrow = q.n + cell * G;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int g = gb + lane + 32 * i;
+        s[i] = g < G ? __ldg(Srow + g) : 0.f;
+        nv[i] = (with_n && g < G) ? __ldg(nrow + g) : 0.f;
+    }
+}
+
 // NB grains per lane per pass: a launch takes NB = ceil(G8 / 32) of its
 // widest request (at most NB_MAX), so that a cell of up to 32 NB grains is
 // one pass with no idle lanes, and its n row is loaded once: the exponent
-// m_c of max_g n comes from the registers of that pass.
+// m_c of max_g n comes from the registers of that pass.  The loop is
+// software-pipelined: the next cell's first-pass loads are issued before this
+// cell's two dependent table lookups, so their DRAM latency overlaps them.
 template <int NB>
 __global__ void __launch_bounds__(SOLVE_TH) k_solve(const __grid_constant__ EmitBatch B) {
     const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * SOLVE_TH + threadIdx.x) >> 5;  // global warp
     const int64_t nw = ((int64_t)gridDim.x * SOLVE_TH) >> 5;
+    int64_t u = ((int64_t)blockIdx.x * SOLVE_TH + threadIdx.x) >> 5;  // this warp's first cell
+    if (u >= B.ncells) return;
     int ri = 0;
-    for (int64_t u = gw; u < B.ncells; u += nw) {
-        while (ri + 1 < B.nreq && u >= B.req[ri + 1].cell_begin) ++ri;
+    while (ri + 1 < B.nreq && u >= B.req[ri + 1].cell_begin) ++ri;
+    float s0[NB], n0[NB];  // first pass of the current cell
+    load_pass<NB>(B.req[ri], u - B.req[ri].cell_begin, 0, lane, s0, n0);
+    for (;;) {
         const EmitReq &q = B.req[ri];
         const DevTables &tb = q.tb;
-        const int G = tb.G, G8 = tb.G8, Gs = tb.Gs;
+        const int G = tb.G, G8 = tb.G8;
         const int64_t cell = u - q.cell_begin;
         const bool emit = (q.mode & EMIT_ON) != 0, rs = (q.mode & EMIT_RESID) != 0;
-        const float *Srow = q.S + cell * Gs;
-        const float *nrow = q.n + cell * G;
+        // issue the next cell's first pass now
+        const int64_t un = u + nw;
+        const bool more = un < B.ncells;
+        int rn = ri;
+        float s1[NB], n1[NB];
+        if (more) {
+            while (rn + 1 < B.nreq && un >= B.req[rn + 1].cell_begin) ++rn;
+            load_pass<NB>(B.req[rn], un - B.req[rn].cell_begin, 0, lane, s1, n1);
+        }
         const bool one = G8 <= 32 * NB;
         int mc = 0;
-        if (!one) {
+        if (!one && emit) {
+            const float *nrow = q.n + cell * G;
             float mx = 0.f;
             for (int g = lane; g < G; g += 32) mx = fmaxf(mx, __ldg(nrow + g));
             for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -184,16 +233,19 @@ __global__ void __launch_bounds__(SOLVE_TH) k_solve(const __grid_constant__ Emit
             int gi[NB], fl[NB];
             float s[NB], nv[NB], Tv[NB];
             float4 gq[NB];
+            if (gb == 0) {
+#pragma unroll
+                for (int i = 0; i < NB; ++i) { s[i] = s0[i]; nv[i] = n0[i]; }
+            } else {
+                load_pass<NB>(q, cell, gb, lane, s, nv);
+            }
 #pragma unroll
             for (int i = 0; i < NB; ++i) {
                 const int g = gb + lane + 32 * i;
-                const bool ok = g < G;
-                gi[i] = ok ? g : 0;
-                s[i] = ok ? __ldg(Srow + g) : 0.f;
-                nv[i] = ok ? __ldg(nrow + g) : 0.f;
+                gi[i] = g < G ? g : 0;
                 gq[i] = __ldg(reinterpret_cast<const float4 *>(tb.gp) + gi[i]);
             }
-            if (one) {
+            if (one && emit) {
                 float mx = 0.f;
 #pragma unroll
                 for (int i = 0; i < NB; ++i) mx = fmaxf(mx, nv[i]);
@@ -233,11 +285,17 @@ __global__ void __launch_bounds__(SOLVE_TH) k_solve(const __grid_constant__ Emit
             if (lane == 0) {
                 CellInfo ci;
                 ci.mc = mc;
+                ci.ah = rs ? ah : 0.f;
+                ci.al = rs ? al : 0.f;
                 ci.pad = 0;
-                ci.absorbed = rs ? ldexp((double)ah + (double)al, mc + tb.Eg) : 0.0;
                 q.cell[cell] = ci;
             }
         }
+        if (!more) break;
+        u = un;
+        ri = rn;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) { s0[i] = s1[i]; n0[i] = n1[i]; }
     }
 }
 
@@ -461,8 +519,7 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
                     ff_add(h, l, v.x, v.y);
                 }
                 const CellInfo ci = q.cell[c0 + c];
-                const double e = ldexp((double)h + (double)l, ci.mc + tb.Ew);
-                q.resid[c0 + c] = e / (FOUR_PI * ci.absorbed) - 1.0;
+                q.resid[c0 + c] = (double)residual(h, l, ci.ah, ci.al, tb);
             }
         }
         buf ^= 1;
