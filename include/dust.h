@@ -66,7 +66,8 @@ enum dust_flag {
     DUST_FLAG_OK = 0,      /* T solved inside the bracket                          */
     DUST_FLAG_LOW = 1,     /* A < P_g(T_min) (includes A = 0): T = T_min           */
     DUST_FLAG_HIGH = 2,    /* A > P_g(T_max): T = T_max                            */
-    DUST_FLAG_INVALID = 4  /* A negative or not finite (bad J): T = NaN            */
+    DUST_FLAG_INVALID = 4, /* A negative or not finite (bad J): T = NaN            */
+    DUST_FLAG_NOCONV = 8   /* dust_solve_T_newton only: no convergence in 64 steps */
 };
 
 /* Create a context for one wavelength grid and one set of grains on `device`.
@@ -242,6 +243,27 @@ int dust_serve_cancel(dust_server *srv, uint64_t ticket);
 int dust_server_stats(dust_server *srv, dust_serve_stats *out);
 int dust_server_reset_stats(dust_server *srv);
 void dust_server_destroy(dust_server *srv);
+
+/* ------------------------------------------------------- paper's kernel 3
+ * The paper's own temperature method (Section 4.3), kept as an ablation of
+ * the table solve on the same GPU.  Per (cell, grain) it runs Newton-Raphson
+ * in T on Eq. 7, evaluating P_g(T) and dP_g/dT by the full wavelength sum at
+ * every iterate, from the fitted initial guess of Eqs. 11-12 (SI units,
+ * log10; floored at 5 K) until |P_g(T) - A| <= 1e-3 A (the paper's 0.1 %
+ * energy non-conservation).  Costs two MUFU operations per wavelength per
+ * iterate, which is the work the table removes.
+ *
+ * dust_ctx_set_grain_sizes: a_m[G] host FP64 grain radii in metres (> 0), the
+ *   `a` of Eqs. 11-12; required before dust_solve_T_newton.  The guess formula
+ *   assumes SI units for lambda, C_abs and J (it was fitted in them).
+ * dust_solve_T_newton: J as in dust_solve (the absorbed power uses the
+ *   context's precision); T [C,G] FP32 out; iters [C,G] uint8 out (Newton
+ *   steps taken, saturating at 255) or NULL; flags [C,G] uint8 out or NULL,
+ *   as dust_solve plus DUST_FLAG_NOCONV.  Device pointers, async on `stream`.
+ *   Returns DUST_EINVAL when the grain sizes were not set. */
+int dust_ctx_set_grain_sizes(dust_ctx *ctx, const double *a_m);
+int dust_solve_T_newton(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, float *T,
+                        uint8_t *iters, uint8_t *flags, void *stream);
 
 /* Failure-detection probe (no counterpart in the paper): one thread waits on
  * an mbarrier phase that nothing completes, through the same bounded wait the

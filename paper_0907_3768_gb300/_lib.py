@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "DUST_OK", 1: "DUST_EINVAL", 2: "DUST_ENOMEM", 3: "DUST_ECUDA
                 5: "DUST_ETIMEOUT", 6: "DUST_ENOTFOUND"}
 DUST_PREC_FP32, DUST_PREC_BF16X3, DUST_PREC_FP16X3 = 0, 1, 2
 PRECISIONS = {"fp32": DUST_PREC_FP32, "bf16x3": DUST_PREC_BF16X3, "fp16x3": DUST_PREC_FP16X3}
-DUST_FLAG_OK, DUST_FLAG_LOW, DUST_FLAG_HIGH, DUST_FLAG_INVALID = 0, 1, 2, 4
+DUST_FLAG_OK, DUST_FLAG_LOW, DUST_FLAG_HIGH, DUST_FLAG_INVALID, DUST_FLAG_NOCONV = 0, 1, 2, 4, 8
 
 
 class DustError(RuntimeError):
@@ -39,6 +39,8 @@ _SIGS = {
     "dust_ctx_check": (_i, [_p, _p]),
     "dust_ctx_profile": (_i, [_p, _i]),
     "dust_ctx_profile_read": (_i, [_p, _p, _p, _p, _p]),
+    "dust_ctx_set_grain_sizes": (_i, [_p, _p]),
+    "dust_solve_T_newton": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p]),
     "dust_diag_wait_timeout": (_i, [_i, _d, _p, _p]),
     "dust_diag_throughput": (_i, [_i, _p, _p]),
     "dust_solve_noalloc": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
@@ -227,3 +229,11 @@ def dust_diag_wait_timeout(device, limit_ms):
     st, ms = ctypes.c_int(), ctypes.c_double()
     check(lib().dust_diag_wait_timeout(device, limit_ms, ctypes.byref(st), ctypes.byref(ms)))
     return st.value, ms.value
+
+
+def dust_ctx_set_grain_sizes(ctx, a_m):
+    return check(lib().dust_ctx_set_grain_sizes(ctx, a_m))
+
+
+def dust_solve_T_newton(ctx, n_cells, J, ld, T, iters, flags, stream):
+    return check(lib().dust_solve_T_newton(ctx, n_cells, J, ld, T, iters, flags, stream))

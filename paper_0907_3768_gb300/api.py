@@ -135,6 +135,30 @@ class Context:
                                    _ptr(out["flags"]), sptr)
         return t, out
 
+    def set_grain_sizes(self, a_m):
+        """Grain radii [G] in metres, for the paper's Newton kernel (Eqs. 11-12 guess)."""
+        a = np.ascontiguousarray(a_m, dtype=np.float64)
+        if a.shape != (self.G,):
+            raise ValueError(f"a_m must have shape ({self.G},)")
+        _lib.dust_ctx_set_grain_sizes(self.handle, a.ctypes.data)
+
+    def solve_T_newton(self, J, stream=None):
+        """Temperatures by the paper's own kernel-3 method (per-iterate quadrature
+        Newton, 0.1 % stop); returns dict T [C,G], iters [C,G] uint8, flags."""
+        C, K = J.shape
+        if K != self.K or J.dtype != torch.float32 or J.stride(1) != 1 or not J.is_cuda:
+            raise ValueError("J must be a [C, K] float32 CUDA tensor with unit-stride rows")
+        dev = torch.device("cuda", self.device)
+        out = dict(T=torch.empty((C, self.G), dtype=torch.float32, device=dev),
+                   iters=torch.empty((C, self.G), dtype=torch.uint8, device=dev),
+                   flags=torch.empty((C, self.G), dtype=torch.uint8, device=dev))
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _lib.dust_solve_T_newton(self.handle, C, J.data_ptr(), J.stride(0), out["T"].data_ptr(),
+                                 out["iters"].data_ptr(), out["flags"].data_ptr(), sptr)
+        return out
+
     def solve_host(self, J, n, T=None, L=None, resid=None, flags=None):
         """The hot path on host arrays (numpy or CPU tensors, ideally pinned);
         outputs are written into / returned as host arrays."""

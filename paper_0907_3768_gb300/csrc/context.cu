@@ -410,6 +410,7 @@ void free_context(dust_ctx *ctx) {
     cudaFree(ctx->Wimg[0]);
     cudaFree(ctx->Wimg[1]);
     cudaFree(ctx->S);
+    cudaFree(ctx->newton_grain);
     auto &hs = ctx->hs;
     for (int i = 0; i < 2; ++i) {
         cudaFree(hs.J[i]); cudaFree(hs.n[i]); cudaFree(hs.T[i]); cudaFree(hs.L[i]);

@@ -156,6 +156,9 @@ struct dust_ctx {
     size_t Wimg_bytes = 0;
     void *tables_mem = nullptr;  // one block holding every table
     size_t tables_bytes = 0;
+    // per-grain constants of the paper's Newton kernel (float2 [G]; NULL until
+    // dust_ctx_set_grain_sizes)
+    void *newton_grain = nullptr;
     // scratch of scaled absorbed powers S[C][Gs]
     float *S = nullptr;
     size_t S_cap = 0;         // in cells
