@@ -58,6 +58,31 @@ def dist_env():
     return rank, world, local
 
 
+def shard_seed(rank):
+    """Seed of rank `rank`'s batch: every rank solves its own full-size batch
+    of independent cells (weak scaling), so no data crosses ranks."""
+    import synth
+
+    return synth.CONFIGS[CONFIG_ID]["seed"] + 7919 * rank
+
+
+def max_over_ranks(x, world, device):
+    """The slowest rank's value (the whole job's step time); identity at N=1."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while running."""
@@ -135,8 +160,7 @@ def run_ours(args):
         dist.barrier()
         __graft_entry__.build()
 
-    seed = synth.CONFIGS[CONFIG_ID]["seed"] + 7919 * rank
-    wl = synth.make_workload(CONFIG_ID, seed=seed)
+    wl = synth.make_workload(CONFIG_ID, seed=shard_seed(rank))
     C, K, G = wl.n_cells_total, wl.K, wl.G
     ld = (K + 3) // 4 * 4
     Jbuf = torch.zeros((C, ld), dtype=torch.float32, device=dev)
@@ -181,11 +205,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         if world > 1:
             dist.barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = tt.item()
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
         prof = None
         if profile:
             a, b, c, cnt = _lib.dust_ctx_profile_read(ctx.handle)
@@ -234,14 +254,10 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(ke):
             _lib.dust_solve_host(*args_h)
-        te = (time.perf_counter() - t0) / ke
-        if world > 1:
-            tt = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = tt.item()
+        te = max_over_ranks((time.perf_counter() - t0) / ke, world, dev)
         h2d = C * ld * 4 + C * G * 4
         d2h = C * G * 4 + C * ld * 4 + C * 8 + C * G
-        e2e = {"value": C * G * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        e2e = {"value": aggregate_rate(C * G, world, te), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": round(te * 1e3, 4), "api": "dust_solve_host (pinned host buffers)"}
 
     # roofline of the dominant kernel (the emission kernel: one ex2 per term)
@@ -258,7 +274,7 @@ def run_ours(args):
                 "fma_pipe_peak_Gflop_lanes": round(fma_rate / 1e9, 1)}
 
     line = {
-        "metric": METRIC, "value": C * G * world / (ms_main * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": aggregate_rate(C * G, world, ms_main * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_main, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded generators: 2-temperature stellar field x U, toy grain model, MRN sizes)",
@@ -592,8 +608,8 @@ def run_reference(args):
     import synth
 
     oracle.lib()
-    budget = 100.0
-    per_step = max(0.2, budget / max(1, args.steps + args.warmup))
+    # a bounded sample per step: the whole run stays within ~100 s of CPU time
+    per_step = max(0.05, min(args.cpu_seconds, 100.0 / max(1, args.steps + args.warmup)))
     wl = synth.make_workload(CONFIG_ID, cells=np.arange(64))
     t = time.perf_counter()
     oracle.run_workload(wl)
