@@ -282,7 +282,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (J 210 MB, L 210 MB per step)",
                    "parallelism": f"dp{world} (independent cell batches)"},
         "sed_cells_per_s": C * world / (ms_main * 1e-3),
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 4 * args.steps,
         "roofline": roofline,
         "clocks": clk,
         "e2e": e2e,

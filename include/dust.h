@@ -160,11 +160,12 @@ int dust_solve_host(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, 
  * layouts, ownership and errors as dust_solve with the context's current
  * precision; the caller still provides every input and output buffer.  The
  * scratch (absorbed powers, then the solve's per-grain and per-cell results
- * for the emission: about 4 Gs + 8 G8 + 16 bytes per cell, Gs = G rounded up
- * to 16, G8 to 8) lives in one fixed 64 MiB array in the library's device
- * data, which every GPU that loads the library holds until the process
- * exits, so n_cells may not exceed dust_noalloc_max_cells(ctx) (57456 cells
- * for 96 grains): larger batches get DUST_EINVAL and must be split.  The first call on a device looks up the
+ * and the residual's partial sums for the emission: 4 Gs + 8 G8 + 16 + 8 NKG
+ * bytes per cell, Gs = G rounded up to 16, G8 to 8, NKG = K / 8 rounded up)
+ * lives in one fixed 64 MiB array in the library's device data, which every
+ * GPU that loads the library holds until the process exits, so n_cells may
+ * not exceed dust_noalloc_max_cells(ctx) (49056 cells for 96 grains and 200
+ * wavelengths): larger batches get DUST_EINVAL and must be split.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, no allocation); make that
  * first call before any stream capture.  All calls share the array: calls
  * whose work overlaps on the GPU (different streams, or different contexts on

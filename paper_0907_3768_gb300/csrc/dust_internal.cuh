@@ -77,11 +77,13 @@ struct CellInfo {
 };
 
 // A request's scratch: S [C][Gs] FP32, then (emission only) the pairs
-// (1/T, n 2^-m_c) [C][G8] and one CellInfo per cell, each 16-byte aligned.
+// (1/T, n 2^-m_c) [C][G8], one CellInfo per cell and the residual partials
+// [C][NKG] float2, each 16-byte aligned.
 struct ScratchView {
     float *S;
     float2 *prep;
     CellInfo *cell;
+    float2 *part;  // [C][NKG] float-float partial sums of w_k L_k (residual)
 };
 
 // One request of the solve / emission kernels.
@@ -94,6 +96,7 @@ struct EmitReq {
     uint8_t *flags;
     float2 *prep;
     CellInfo *cell;
+    float2 *part;
     int TC, GC, resident, mode;
 };
 

@@ -215,7 +215,8 @@ std::vector<Part> build_round(dust_server *s) {
 // Scratch of one part: rows c0.. of its request's S, (1/T, n) pairs and cell records.
 ScratchView part_view(const Part &p) {
     const ScratchView v = scratch_view(p.r->ctx, p.r->C, p.r->S);
-    return {v.S + p.c0 * p.r->ctx->tb.Gs, v.prep + p.c0 * p.r->ctx->tb.G8, v.cell + p.c0};
+    return {v.S + p.c0 * p.r->ctx->tb.Gs, v.prep + p.c0 * p.r->ctx->tb.G8, v.cell + p.c0,
+            v.part + p.c0 * p.r->ctx->tb.NKG};
 }
 
 int launch_round(dust_server *s, const std::vector<Part> &parts) {
@@ -270,7 +271,7 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
     EmitBatch E;
     E.nreq = 0;
     size_t smem = 0;
-    bool emit = false;
+    bool emit = false, resid = false;
     for (const Part &p : parts) {
         ServeReq *r = p.r;
         dust_ctx *ctx = r->ctx;
@@ -281,10 +282,11 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
                       r->flags ? r->flags + p.c0 * G : nullptr, E.req[E.nreq++]);
         smem = std::max(smem, pl.smem);
         emit = emit || r->L || r->resid;
+        resid = resid || r->resid;
     }
     int rc = launch_emit_batch(E, smem, s->num_sms, s->st);
     if (rc != DUST_OK) return rc;
-    s->launches += emit ? 2 : 1;
+    s->launches += 1 + (emit ? 1 : 0) + (resid ? 1 : 0);
     return DUST_OK;
 }
 

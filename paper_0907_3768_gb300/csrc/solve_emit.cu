@@ -360,12 +360,12 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
     const int tid = threadIdx.x;
 
     int cur = -1;
-    // per-request layout: Chat [NKG][CST] float4 | two (1/T, n) tiles [NP+1][TNP] | sEm
+    // per-request layout: Chat [NKG][CST] float4 | two (1/T, n) tiles [NP+1][TNP]
     // The emission item of a thread is one k-group (8 wavelengths) of two
     // neighbouring cells; items run k-group-major over the threads, so the
     // lanes of a warp share few k-groups (Chat loads are near-broadcasts) and
     // one 16-byte load fetches (1/T, n) of both cells of a pair.
-    int oTN = 0, oEm = 0, TNP = 0, CST = 0, TNB = 0;
+    int oTN = 0, TNP = 0, CST = 0, TNB = 0;
     int ipair = 0, ikg = 0, buf = 0;
     int64_t pref = -1;  // global tile whose pairs sit (or are landing) in buffer `buf`
 
@@ -383,7 +383,6 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
             CST = 2 * (q.resident ? G8 : q.GC) + 1;
             TNB = (NP + 1) * TNP;  // floats per (1/T, n) tile buffer
             oTN = NKG * CST * 16;
-            oEm = oTN + 2 * TNB * 4;
             const bool okit = tid < NP * NKG;
             ikg = okit ? tid / NP : 0;
             ipair = okit ? tid - ikg * NP : NP;  // idle threads read the dummy pair row NP
@@ -404,7 +403,6 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
         }
         float4 *sC = reinterpret_cast<float4 *>(smem_raw);
         float *sTN0 = reinterpret_cast<float *>(smem_raw + oTN);
-        float2 *sEm = reinterpret_cast<float2 *>(smem_raw + oEm);
         const int64_t lt = tile - q.tile_begin;
         const int64_t c0 = lt * TC;
         const int nc = (int)((q.C - c0) < (int64_t)TC ? (q.C - c0) : (int64_t)TC);
@@ -477,9 +475,13 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
                     }
             }
         }
-        // ---- epilogue: scale, store, residual partials.  The 8-term partial
+        // ---- epilogue: scale, store, residual partials.  An item's 8
+        // wavelengths of a cell are one 32-byte sector of L, written as two
+        // 16-byte stores when the rows allow it.  The 8-term partial
         // sum_k w_k L_k of an item is accumulated error-free in float-float
         // (products split by FMA, sums by two-sum).
+        const bool storeL = (q.mode & EMIT_STORE_L) != 0;
+        const bool vecL = storeL && ((reinterpret_cast<uintptr_t>(q.L) & 15) == 0) && (q.ld % 4 == 0);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const int c = 2 * ipair + r;
@@ -488,19 +490,37 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
             const int mc = q.cell[cell].mc;
             float sh = 0.f, sl = 0.f;
             const int kb = ikg * KQ;
+            float Lv[KQ];
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int k = kb + 2 * p + h;
-                    if (k < K) {
-                        const int qk = __ldg(tb.qexp + k);
-                        const float a = h ? acc[r][p].y : acc[r][p].x;
-                        const float Lv = scale2(a, mc + qk);
-                        if (q.mode & EMIT_STORE_L) q.L[cell * q.ld + k] = Lv;
-                        if (rs) {
+                    const int k = min(kb + 2 * p + h, K - 1);
+                    const float a = h ? acc[r][p].y : acc[r][p].x;
+                    Lv[2 * p + h] = scale2(a, mc + __ldg(tb.qexp + k));
+                }
+            }
+            if (storeL) {
+                float *row = q.L + cell * q.ld + kb;
+                if (vecL && kb + KQ <= K) {
+                    reinterpret_cast<float4 *>(row)[0] = make_float4(Lv[0], Lv[1], Lv[2], Lv[3]);
+                    reinterpret_cast<float4 *>(row)[1] = make_float4(Lv[4], Lv[5], Lv[6], Lv[7]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < KQ; ++j)
+                        if (kb + j < K) row[j] = Lv[j];
+                }
+            }
+            if (rs) {
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int k = kb + 2 * p + h;
+                        if (k < K) {
                             // w_k L_k 2^-(m_c + Ew) = wq_k a: the FP32 accumulator before
                             // its power-of-two scaling (equal to the stored L unless L is subnormal)
+                            const float a = h ? acc[r][p].y : acc[r][p].x;
                             const float wk = __ldg(tb.wq + k);
                             const float pr = wk * a;
                             ff_add(sh, sl, pr, fmaf(wk, a, -pr));
@@ -508,23 +528,34 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
                     }
                 }
             }
-            if (rs) sEm[c * NKG + ikg] = make_float2(sh, sl);
-        }
-        if (rs) {
-            __syncthreads();
-            for (int c = tid; c < nc; c += NTH) {
-                float h = 0.f, l = 0.f;
-                for (int kg = 0; kg < NKG; ++kg) {
-                    const float2 v = sEm[c * NKG + kg];
-                    ff_add(h, l, v.x, v.y);
-                }
-                const CellInfo ci = q.cell[c0 + c];
-                q.resid[c0 + c] = (double)residual(h, l, ci.ah, ci.al, tb);
-            }
+            if (rs) q.part[cell * NKG + ikg] = make_float2(sh, sl);
         }
         buf ^= 1;
     }
     cp_async_wait_all();
+}
+
+// Energy-balance residual of every cell of the requests that want it: one
+// thread per cell sums the cell's k-group partials in ascending order, so
+// the order depends only on NKG.
+__global__ void __launch_bounds__(SOLVE_TH) k_resid(const __grid_constant__ EmitBatch E) {
+    const int64_t stride = (int64_t)gridDim.x * SOLVE_TH;
+    int ri = 0;
+    for (int64_t u = (int64_t)blockIdx.x * SOLVE_TH + threadIdx.x; u < E.ncells; u += stride) {
+        while (ri + 1 < E.nreq && u >= E.req[ri + 1].cell_begin) ++ri;
+        const EmitReq &q = E.req[ri];
+        if (!(q.mode & EMIT_RESID)) continue;
+        const int NKG = q.tb.NKG;
+        const int64_t cell = u - q.cell_begin;
+        const float2 *pp = q.part + cell * NKG;
+        float h = 0.f, l = 0.f;
+        for (int kg = 0; kg < NKG; ++kg) {
+            const float2 v = pp[kg];
+            ff_add(h, l, v.x, v.y);
+        }
+        const CellInfo ci = q.cell[cell];
+        q.resid[cell] = (double)residual(h, l, ci.ah, ci.al, q.tb);
+    }
 }
 
 }  // namespace
@@ -538,7 +569,7 @@ EmitPlan plan_emit(const dust_ctx *ctx, bool emit) {
     p.TC = 2 * NP;
     if (!emit) { p.GC = tb.G8; p.resident = 0; p.smem = 0; return p; }
     const size_t budget = 113 * 1024;  // two CTAs per SM
-    const size_t fixed = (size_t)2 * (NP + 1) * (4 * tb.G8 + 4) * 4 + (size_t)p.TC * tb.NKG * 8 + 64;
+    const size_t fixed = (size_t)2 * (NP + 1) * (4 * tb.G8 + 4) * 4 + 64;
     const size_t full = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + fixed;
     if (full <= budget) { p.GC = tb.G8; p.resident = 1; p.smem = full; return p; }
     const size_t avail = budget > fixed ? budget - fixed : 0;
@@ -551,10 +582,13 @@ EmitPlan plan_emit(const dust_ctx *ctx, bool emit) {
 }
 
 // Scratch bytes of a request of C cells: S [C][Gs] FP32, then (emission)
-// the (1/T, n) pairs [C][G8] and one CellInfo per cell, each 16-byte aligned.
+// the (1/T, n) pairs [C][G8], one CellInfo per cell and the residual
+// partials [C][NKG] float2, each 16-byte aligned.
 size_t scratch_bytes(const dust_ctx *ctx, int64_t C, bool emit) {
     size_t b = ((size_t)C * ctx->tb.Gs * 4 + 15) & ~(size_t)15;
-    if (emit) b += (((size_t)C * ctx->tb.G8 * 8 + 15) & ~(size_t)15) + (size_t)C * sizeof(CellInfo);
+    if (emit)
+        b += (((size_t)C * ctx->tb.G8 * 8 + 15) & ~(size_t)15) + (size_t)C * sizeof(CellInfo) +
+             (((size_t)C * ctx->tb.NKG * 8 + 15) & ~(size_t)15);
     return b;
 }
 
@@ -566,6 +600,8 @@ ScratchView scratch_view(const dust_ctx *ctx, int64_t C, void *base) {
     v.prep = reinterpret_cast<float2 *>(p);
     p += ((size_t)C * ctx->tb.G8 * 8 + 15) & ~(size_t)15;
     v.cell = reinterpret_cast<CellInfo *>(p);
+    p += (size_t)C * sizeof(CellInfo);
+    v.part = reinterpret_cast<float2 *>(p);
     return v;
 }
 
@@ -584,6 +620,7 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
     r.flags = flags;
     r.prep = sv.prep;
     r.cell = sv.cell;
+    r.part = sv.part;
     r.TC = p.TC;
     r.GC = p.GC;
     r.resident = p.resident;
@@ -628,6 +665,12 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
     }
     E.ntiles = tiles;
     E.ncells = 0;
+    bool resid = false;
+    for (int i = 0; i < E.nreq; ++i) {  // cells of the emission list, numbered afresh
+        E.req[i].cell_begin = E.ncells;
+        E.ncells += E.req[i].C;
+        resid = resid || (E.req[i].mode & EMIT_RESID);
+    }
     if (tiles == 0) return DUST_OK;
     DUST_CUDA_TRY(cudaFuncSetAttribute(k_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -636,6 +679,11 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
     const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * per_sm);
     k_emit<<<(unsigned)grid, NTH, smem, st>>>(E);
     DUST_CUDA_TRY(cudaGetLastError());
+    if (resid) {
+        const int64_t rgrid = std::min<int64_t>((E.ncells + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
+        k_resid<<<(unsigned)rgrid, SOLVE_TH, 0, st>>>(E);
+        DUST_CUDA_TRY(cudaGetLastError());
+    }
     return DUST_OK;
 }
 

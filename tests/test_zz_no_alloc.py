@@ -41,13 +41,14 @@ def _noalloc(ctx, J, n):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_noalloc_matches_dust_solve_on_two_calls(prec):
-    from paper_0907_3768_gb300 import Context
+    from paper_0907_3768_gb300 import Context, _lib
 
     wl = synth.make_workload(1, cells=np.arange(60000))
     J = torch.from_numpy(wl.J).cuda()
     n = torch.from_numpy(wl.n).cuda()
-    batches = [(J[:50000], n[:50000]), (J[13:21013], n[13:21013])]  # second call: other cells, fewer of them
     with Context.from_workload(wl, precision=prec) as ctx:
+        big = min(50000, _lib.dust_noalloc_max_cells(ctx.handle))  # as large as the array allows
+        batches = [(J[:big], n[:big]), (J[13:21013], n[13:21013])]  # second call: other cells, fewer of them
         for Jb, nb in batches:
             ref = ctx.solve(Jb, nb)
             torch.cuda.synchronize()
@@ -66,8 +67,9 @@ def test_noalloc_rejects_batches_beyond_its_array():
     wl = synth.make_workload(0, cells=np.arange(4))
     with Context.from_workload(wl) as ctx:
         cap = _lib.dust_noalloc_max_cells(ctx.handle)
-        # G = 16 grains: 64 B of absorbed powers + 128 B of (1/T, n) + 16 B per cell
-        assert cap == (64 << 20) // 208
+        # G = 16 grains, K = 64: 64 B of absorbed powers + 128 B of (1/T, n) + 16 B of cell
+        # record + 64 B of residual partials per cell
+        assert cap == (64 << 20) // 272
         # buffers sized for cap + 1 cells, so that the call would stay in bounds
         # even if the check let it through; refused with and without outputs
         out = ctx.alloc_outputs(cap + 1, wl.K)
