@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the 2^20-cell, K=500, G=240 solve")
     ap.add_argument("--no-ablation", action="store_true", help="skip the paper's kernel-3 Newton solve")
+    ap.add_argument("--large-cells", type=int, default=1 << 20,
+                    help="cells of the K=500, G=240 solve (the full case is 2^20; fewer for profiling captures)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-load", type=float, default=0.7, help="arrival rate / saturated throughput")
     return ap.parse_args()
@@ -414,15 +416,18 @@ def run_large(args, dev, local, ex2_rate):
     import synth
     from paper_0907_3768_gb300 import Context, _lib
 
-    wl = synth.make_workload(3)
-    C, K, G = wl.n_cells_total, wl.K, wl.G
+    import numpy as np
+
+    full = synth.CONFIGS[3]["n_cells"]
+    wl = synth.make_workload(3, cells=None if args.large_cells >= full else np.arange(args.large_cells))
+    C, K, G = len(wl.cells), wl.K, wl.G
     ld = (K + 3) // 4 * 4
     Jb = torch.zeros((C, ld), dtype=torch.float32, device=dev)
     Jb[:, :K] = torch.from_numpy(wl.J).to(dev)
     J, n = Jb[:, :K], torch.from_numpy(wl.n).to(dev)
     del wl
     stream = torch.cuda.current_stream(dev)
-    out = {"workload": "2^20 cells x 500 wavelengths (0.05-2000 um) x 240 grains, 10% near-opaque cells"}
+    out = {"workload": f"{C} cells x 500 wavelengths (0.05-2000 um) x 240 grains, 10% near-opaque cells"}
     steps = max(3, min(args.steps, 10))
     for prec in ("bf16x3", "fp32"):
         ctx = Context.from_workload(synth.make_workload(3, cells=[0]), precision=prec, device=local)
