@@ -132,6 +132,25 @@ def test_odd_shapes(prec):
     _compare(out, ref, prec)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("K,sizes,species,lam_um", [(2048, 256, ("silicate", "graphite"), (0.09, 1000.0)),
+                                                     (2, 1, ("graphite",), (5.0, 200.0))])
+def test_size_limits(prec, K, sizes, species, lam_um):
+    """The documented limits.  K = 2048, G = 512: a second tensor-core MMA for
+    grain columns past 256, four solve passes per cell, the emission's
+    cross-section chunks at one cell pair per tile, 256 residual partials.
+    K = 2, G = 1 (two mid-infrared wavelengths, so that the grains solve inside
+    the bracket): one padded wavelength chunk and one padded grain group."""
+    cfg = dict(synth.CONFIGS[0])
+    cfg.update(K=K, n_sizes=sizes, species=species, n_cells=49, seed=91, lam_um=lam_um)
+    wl = synth.make_workload(cfg)
+    assert (wl.K, wl.G) == (K, sizes * len(species))
+    ref = oracle.run_workload(wl)
+    with _ctx(wl, prec) as ctx:
+        out = _run(ctx, wl.J, wl.n, precision=prec)
+    _compare(out, ref, prec)
+
+
 def test_edge_inputs_flags():
     wl = synth.make_workload(0, cells=np.arange(8))
     J = wl.J.copy()
