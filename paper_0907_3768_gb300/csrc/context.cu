@@ -412,12 +412,16 @@ void free_context(dust_ctx *ctx) {
     cudaFree(ctx->S);
     cudaFree(ctx->newton_grain);
     auto &hs = ctx->hs;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < dust_ctx::NHB; ++i) {
         cudaFree(hs.J[i]); cudaFree(hs.n[i]); cudaFree(hs.T[i]); cudaFree(hs.L[i]);
-        cudaFree(hs.r[i]); cudaFree(hs.f[i]); cudaFree(hs.S[i]);
-        if (hs.st[i]) cudaStreamDestroy(hs.st[i]);
-        if (hs.ev[i]) cudaEventDestroy(hs.ev[i]);
+        cudaFree(hs.r[i]); cudaFree(hs.f[i]);
+        if (hs.ev_in[i]) cudaEventDestroy(hs.ev_in[i]);
+        if (hs.ev_c[i]) cudaEventDestroy(hs.ev_c[i]);
+        if (hs.ev_out[i]) cudaEventDestroy(hs.ev_out[i]);
     }
+    cudaFree(hs.S);
+    for (int i = 0; i < 3; ++i)
+        if (hs.st[i]) cudaStreamDestroy(hs.st[i]);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->prof_marks) cudaEventDestroy(e);
     cudaSetDevice(prev);

@@ -166,14 +166,16 @@ struct dust_ctx {
     float *S = nullptr;
     size_t S_cap = 0;         // in cells
     // host-staging for dust_solve_host
+    // a three-stage pipeline (copy in, compute, copy out) over NHB buffer sets
+    static constexpr int NHB = 3;
     struct HostStage {
-        cudaStream_t st[2] = {nullptr, nullptr};
-        cudaEvent_t ev[2] = {nullptr, nullptr};
-        float *J[2] = {nullptr, nullptr}, *n[2] = {nullptr, nullptr};
-        float *T[2] = {nullptr, nullptr}, *L[2] = {nullptr, nullptr};
-        double *r[2] = {nullptr, nullptr};
-        uint8_t *f[2] = {nullptr, nullptr};
-        float *S[2] = {nullptr, nullptr};
+        cudaStream_t st[3] = {nullptr, nullptr, nullptr};  // copy in, compute, copy out
+        cudaEvent_t ev_in[NHB] = {}, ev_c[NHB] = {}, ev_out[NHB] = {};
+        float *J[NHB] = {}, *n[NHB] = {};
+        float *T[NHB] = {}, *L[NHB] = {};
+        double *r[NHB] = {};
+        uint8_t *f[NHB] = {};
+        void *S = nullptr;  // one scratch: the compute stream runs one chunk at a time
         int64_t cap = 0, ld = 0;
     } hs;
     int num_sms = 0;

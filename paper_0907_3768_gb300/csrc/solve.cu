@@ -152,52 +152,72 @@ int dust_solve_host(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, 
     DeviceGuard dg(ctx->device);
     if (dg.rc != DUST_OK) return dg.rc;
     const int G = ctx->G;
-    // chunks of at least 8192 cells, about 8 of them for large batches
-    int64_t chunk = std::max<int64_t>(8192, (n_cells + 7) / 8);
+    constexpr int NB = dust_ctx::NHB;
+    // chunks of at least 8192 cells, about 16 of them for large batches
+    int64_t chunk = std::max<int64_t>(8192, (n_cells + 15) / 16);
     chunk = (chunk + 127) / 128 * 128;
     chunk = std::min<int64_t>(chunk, n_cells);
     auto &hs = ctx->hs;
     if (hs.cap < chunk || hs.ld != ld) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NB; ++i) {
             cudaFree(hs.J[i]); cudaFree(hs.n[i]); cudaFree(hs.T[i]); cudaFree(hs.L[i]);
-            cudaFree(hs.r[i]); cudaFree(hs.f[i]); cudaFree(hs.S[i]);
-            hs.J[i] = hs.n[i] = hs.T[i] = hs.L[i] = hs.S[i] = nullptr;
+            cudaFree(hs.r[i]); cudaFree(hs.f[i]);
+            hs.J[i] = hs.n[i] = hs.T[i] = hs.L[i] = nullptr;
             hs.r[i] = nullptr; hs.f[i] = nullptr;
         }
+        cudaFree(hs.S);
+        hs.S = nullptr;
         hs.cap = 0;
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < 3; ++i)
             if (!hs.st[i]) DUST_CUDA_TRY(cudaStreamCreateWithFlags(&hs.st[i], cudaStreamNonBlocking));
+        for (int i = 0; i < NB; ++i) {
+            if (!hs.ev_in[i]) DUST_CUDA_TRY(cudaEventCreateWithFlags(&hs.ev_in[i], cudaEventDisableTiming));
+            if (!hs.ev_c[i]) DUST_CUDA_TRY(cudaEventCreateWithFlags(&hs.ev_c[i], cudaEventDisableTiming));
+            if (!hs.ev_out[i]) DUST_CUDA_TRY(cudaEventCreateWithFlags(&hs.ev_out[i], cudaEventDisableTiming));
             DUST_CUDA_TRY(cudaMalloc(&hs.J[i], sizeof(float) * chunk * ld));
             DUST_CUDA_TRY(cudaMalloc(&hs.n[i], sizeof(float) * chunk * G));
             DUST_CUDA_TRY(cudaMalloc(&hs.T[i], sizeof(float) * chunk * G));
             DUST_CUDA_TRY(cudaMalloc(&hs.L[i], sizeof(float) * chunk * ld));
             DUST_CUDA_TRY(cudaMalloc(&hs.r[i], sizeof(double) * chunk));
             DUST_CUDA_TRY(cudaMalloc(&hs.f[i], sizeof(uint8_t) * chunk * G));
-            DUST_CUDA_TRY(cudaMalloc(&hs.S[i], scratch_bytes(ctx, chunk, true)));
         }
+        DUST_CUDA_TRY(cudaMalloc(&hs.S, scratch_bytes(ctx, chunk, true)));
         hs.cap = chunk;
         hs.ld = ld;
     }
+    // copy in (stream 0) -> compute (stream 1) -> copy out (stream 2), chunk i in
+    // buffer set i % NB: chunk i's upload, chunk i-1's compute and chunk i-2's
+    // download run at the same time.  A buffer set is reused once the compute
+    // that read its inputs and the download that read its outputs are done.
+    cudaStream_t sin = hs.st[0], scomp = hs.st[1], sout = hs.st[2];
     int64_t i = 0;
     for (int64_t c0 = 0; c0 < n_cells; c0 += chunk, ++i) {
-        const int s = (int)(i & 1);
+        const int b = (int)(i % NB);
         const int64_t cn = std::min<int64_t>(chunk, n_cells - c0);
-        cudaStream_t st = hs.st[s];
-        DUST_CUDA_TRY(cudaMemcpyAsync(hs.J[s], J + c0 * ld, sizeof(float) * cn * ld, cudaMemcpyHostToDevice, st));
-        DUST_CUDA_TRY(cudaMemcpyAsync(hs.n[s], n + c0 * G, sizeof(float) * cn * G, cudaMemcpyHostToDevice, st));
-        rc = solve_device(ctx, precision, cn, hs.J[s], ld, hs.n[s], hs.T[s], L ? hs.L[s] : nullptr,
-                          resid ? hs.r[s] : nullptr, flags ? hs.f[s] : nullptr, hs.S[s], st);
-        if (rc != DUST_OK) { cudaStreamSynchronize(hs.st[0]); cudaStreamSynchronize(hs.st[1]); return rc; }
-        DUST_CUDA_TRY(cudaMemcpyAsync(T + c0 * G, hs.T[s], sizeof(float) * cn * G, cudaMemcpyDeviceToHost, st));
+        if (i >= NB) DUST_CUDA_TRY(cudaStreamWaitEvent(sin, hs.ev_c[b], 0));
+        DUST_CUDA_TRY(cudaMemcpyAsync(hs.J[b], J + c0 * ld, sizeof(float) * cn * ld, cudaMemcpyHostToDevice, sin));
+        DUST_CUDA_TRY(cudaMemcpyAsync(hs.n[b], n + c0 * G, sizeof(float) * cn * G, cudaMemcpyHostToDevice, sin));
+        DUST_CUDA_TRY(cudaEventRecord(hs.ev_in[b], sin));
+        DUST_CUDA_TRY(cudaStreamWaitEvent(scomp, hs.ev_in[b], 0));
+        if (i >= NB) DUST_CUDA_TRY(cudaStreamWaitEvent(scomp, hs.ev_out[b], 0));
+        rc = solve_device(ctx, precision, cn, hs.J[b], ld, hs.n[b], hs.T[b], L ? hs.L[b] : nullptr,
+                          resid ? hs.r[b] : nullptr, flags ? hs.f[b] : nullptr, hs.S, scomp);
+        if (rc != DUST_OK) {
+            for (int k = 0; k < 3; ++k) cudaStreamSynchronize(hs.st[k]);
+            return rc;
+        }
+        DUST_CUDA_TRY(cudaEventRecord(hs.ev_c[b], scomp));
+        DUST_CUDA_TRY(cudaStreamWaitEvent(sout, hs.ev_c[b], 0));
+        DUST_CUDA_TRY(cudaMemcpyAsync(T + c0 * G, hs.T[b], sizeof(float) * cn * G, cudaMemcpyDeviceToHost, sout));
         if (L)
-            DUST_CUDA_TRY(cudaMemcpyAsync(L + c0 * ld, hs.L[s], sizeof(float) * cn * ld, cudaMemcpyDeviceToHost, st));
+            DUST_CUDA_TRY(cudaMemcpyAsync(L + c0 * ld, hs.L[b], sizeof(float) * cn * ld, cudaMemcpyDeviceToHost, sout));
         if (resid)
-            DUST_CUDA_TRY(cudaMemcpyAsync(resid + c0, hs.r[s], sizeof(double) * cn, cudaMemcpyDeviceToHost, st));
+            DUST_CUDA_TRY(cudaMemcpyAsync(resid + c0, hs.r[b], sizeof(double) * cn, cudaMemcpyDeviceToHost, sout));
         if (flags)
-            DUST_CUDA_TRY(cudaMemcpyAsync(flags + c0 * G, hs.f[s], cn * G, cudaMemcpyDeviceToHost, st));
+            DUST_CUDA_TRY(cudaMemcpyAsync(flags + c0 * G, hs.f[b], cn * G, cudaMemcpyDeviceToHost, sout));
+        DUST_CUDA_TRY(cudaEventRecord(hs.ev_out[b], sout));
     }
-    DUST_CUDA_TRY(cudaStreamSynchronize(hs.st[0]));
-    DUST_CUDA_TRY(cudaStreamSynchronize(hs.st[1]));
+    for (int k = 0; k < 3; ++k) DUST_CUDA_TRY(cudaStreamSynchronize(hs.st[k]));
     return DUST_OK;
 }
 

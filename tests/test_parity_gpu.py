@@ -198,15 +198,19 @@ def test_cell_results_independent_of_batch(prec):
         np.testing.assert_array_equal(a[k][1234:2345], b[k])
 
 
-def test_host_entry_point_matches_device():
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_host_entry_point_matches_device(prec):
+    """Host buffers through the copy-in / compute / copy-out pipeline: 5 chunks
+    over 3 buffer sets (a ragged last one), called twice in a row."""
     from paper_0907_3768_gb300 import Context
 
-    wl = synth.make_workload(1, cells=np.arange(40000))
-    with Context.from_workload(wl, precision="fp32") as ctx:
-        dev = _run(ctx, wl.J, wl.n)
-        host = ctx.solve_host(wl.J, wl.n)
-    for k in ("T", "L", "resid", "flags"):
-        np.testing.assert_array_equal(host[k], dev[k])
+    wl = synth.make_workload(1, cells=np.arange(40001))  # K = 200: rows already 16-byte multiples
+    with Context.from_workload(wl, precision=prec) as ctx:
+        dev = _run(ctx, wl.J, wl.n, precision=prec)
+        for _ in range(2):
+            host = ctx.solve_host(wl.J, wl.n)
+            for k in ("T", "L", "resid", "flags"):
+                np.testing.assert_array_equal(host[k], dev[k])
 
 
 def test_invalid_device_arguments():
