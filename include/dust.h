@@ -245,6 +245,30 @@ int dust_server_stats(dust_server *srv, dust_serve_stats *out);
 int dust_server_reset_stats(dust_server *srv);
 void dust_server_destroy(dust_server *srv);
 
+/* ------------------------------------------------------- self-absorption
+ * Dust that is optically thick to its own emission is heated by it as well,
+ * so the paper's radiative-transfer code iterates the radiation field and the
+ * temperatures together (Section 2).  dust_solve_coupled is the local form of
+ * that iteration around the hot path:
+ *   J^(0) = J_ext,  J^(i) = J_ext + E (.) L^(i),  L^(i) = emission of a solve on J^(i-1),
+ * stopping when max_c max_k |L^(i) - L^(i-1)| / max_k L^(i)[c,k] <= tol, or
+ * after max_iters solves (1 <= max_iters <= 10000).
+ *
+ *  J_ext [C,ld], E [C,ld]  FP32 device: the external mean intensity and the
+ *                      coupling E[c,k] >= 0 (the part of the cell's own
+ *                      emission L[c,k], in L's units, that returns to J[c,k]).
+ *                      The iteration converges when the self-absorbed fraction
+ *                      of the emitted power stays below 1.
+ *  n, T, L, resid, flags  as dust_solve; T, L, resid and flags hold the last
+ *                      solve.  L is required.
+ *  *iters_done         solves run; *last_change the last measured change
+ *                      (infinite until two solves have run).  Either may be NULL.
+ * Synchronises `stream` once per iteration (the stop test is read on the
+ * host).  The context keeps a working J and the previous L (8 C ld bytes). */
+int dust_solve_coupled(dust_ctx *ctx, int64_t n_cells, const float *J_ext, int64_t ld, const float *E,
+                       const float *n, int max_iters, double tol, float *T, float *L, double *resid,
+                       uint8_t *flags, int *iters_done, double *last_change, void *stream);
+
 /* ------------------------------------------------------- paper's kernel 3
  * The paper's own temperature method (Section 4.3), kept as an ablation of
  * the table solve on the same GPU.  Per (cell, grain) it runs Newton-Raphson

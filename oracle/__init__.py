@@ -6,6 +6,7 @@ benchmark's CPU-baseline / reference leg may import this package; the CUDA
 library never does, and the two share no code.
 """
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -119,6 +120,28 @@ def run(lam, w, C, J, n, T_min, T_max, want_L=True, want_resid=True, n_threads=0
                                _ptr(L) if want_L else nul, _ptr(fl), _ptr(r) if want_resid else nul,
                                int(n_threads))
     return dict(A=A, T=T, flags=fl, L=L, resid=r, evals=int(ev))
+
+
+def run_coupled(lam, w, C, J_ext, E, n, T_min, T_max, tol=1e-12, max_iters=500):
+    """Self-absorption fixed point (Section 2: dust heated by its own emission
+    needs an iteration of the radiation field and the temperatures), local
+    form: J = J_ext + E * L with L the emission (Eqs. 8-10) at the temperatures
+    solved from J.  Plain fixed-point iteration in FP64, stopped when the
+    largest peak-normalised change of L falls to `tol`.  Returns (result of
+    the last run, iterations, last change)."""
+    J_ext, E = _f64(J_ext), _f64(E)
+    J = J_ext
+    prev, ch = None, math.inf
+    for it in range(1, max_iters + 1):
+        res = run(lam, w, C, J, n, T_min, T_max)
+        L = res["L"]
+        if prev is not None:
+            ch = float((np.abs(L - prev).max(axis=1) / L.max(axis=1)).max())
+            if ch <= tol:
+                return res, it, ch
+        prev = L
+        J = J_ext + E * L
+    return res, max_iters, ch
 
 
 def max_threads():

@@ -41,6 +41,7 @@ _SIGS = {
     "dust_ctx_profile_read": (_i, [_p, _p, _p, _p, _p]),
     "dust_ctx_set_grain_sizes": (_i, [_p, _p]),
     "dust_solve_T_newton": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p]),
+    "dust_solve_coupled": (_i, [_p, _i64, _p, _i64, _p, _p, _i, _d, _p, _p, _p, _p, _p, _p, _p]),
     "dust_diag_wait_timeout": (_i, [_i, _d, _p, _p]),
     "dust_diag_throughput": (_i, [_i, _p, _p]),
     "dust_solve_noalloc": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
@@ -237,3 +238,11 @@ def dust_ctx_set_grain_sizes(ctx, a_m):
 
 def dust_solve_T_newton(ctx, n_cells, J, ld, T, iters, flags, stream):
     return check(lib().dust_solve_T_newton(ctx, n_cells, J, ld, T, iters, flags, stream))
+
+
+def dust_solve_coupled(ctx, n_cells, J_ext, ld, E, n, max_iters, tol, T, L, resid, flags, stream):
+    """Returns (iterations run, last measured change of L)."""
+    it, ch = ctypes.c_int(), ctypes.c_double()
+    check(lib().dust_solve_coupled(ctx, n_cells, J_ext, ld, E, n, max_iters, tol, T, L, resid, flags,
+                                   ctypes.byref(it), ctypes.byref(ch), stream))
+    return it.value, ch.value

@@ -135,6 +135,23 @@ class Context:
                                    _ptr(out["flags"]), sptr)
         return t, out
 
+    def solve_coupled(self, J_ext, E, n, max_iters=50, tol=1e-6, stream=None):
+        """Self-absorbing solve: J = J_ext + E L iterated with the solve until L
+        changes by at most `tol` (peak-normalised).  J_ext and E are [C, K]
+        views with the same row stride.  Returns (outputs, iterations, change)."""
+        C, ld = self._check_inputs(J_ext, n)
+        if E.shape != J_ext.shape or E.stride() != J_ext.stride() or E.dtype != torch.float32:
+            raise ValueError("E must be a float32 tensor shaped and strided like J_ext")
+        out = self.alloc_outputs(C, ld)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        it, ch = _lib.dust_solve_coupled(self.handle, C, J_ext.data_ptr(), ld, E.data_ptr(), n.data_ptr(),
+                                         int(max_iters), float(tol), out["T"].data_ptr(),
+                                         out["L_buf"].data_ptr(), out["resid"].data_ptr(),
+                                         out["flags"].data_ptr(), sptr)
+        return out, it, ch
+
     def set_grain_sizes(self, a_m):
         """Grain radii [G] in metres, for the paper's Newton kernel (Eqs. 11-12 guess)."""
         a = np.ascontiguousarray(a_m, dtype=np.float64)

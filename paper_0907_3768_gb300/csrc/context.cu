@@ -411,6 +411,7 @@ void free_context(dust_ctx *ctx) {
     cudaFree(ctx->Wimg[1]);
     cudaFree(ctx->S);
     cudaFree(ctx->newton_grain);
+    cudaFree(ctx->cpl);
     auto &hs = ctx->hs;
     for (int i = 0; i < dust_ctx::NHB; ++i) {
         cudaFree(hs.J[i]); cudaFree(hs.n[i]); cudaFree(hs.T[i]); cudaFree(hs.L[i]);

@@ -162,6 +162,9 @@ struct dust_ctx {
     // per-grain constants of the paper's Newton kernel (float2 [G]; NULL until
     // dust_ctx_set_grain_sizes)
     void *newton_grain = nullptr;
+    // working J, previous L and a change word of dust_solve_coupled
+    void *cpl = nullptr;
+    size_t cpl_bytes = 0;
     // scratch of scaled absorbed powers S[C][Gs]
     float *S = nullptr;
     size_t S_cap = 0;         // in cells

@@ -216,3 +216,32 @@ def test_mpmath_brute_force_tiny():
                 Lref[i] += mp.mpf(n[ci, g]) * mp.mpf(C[g, i]) * B(mp.mpf(lam[i]), T)
         for i in range(8):
             assert float(4 * mp.pi * Lref[i]) == pytest.approx(r["L"][ci, i], rel=1e-11)
+
+
+def test_coupled_without_coupling_is_the_plain_solve():
+    """E = 0: the self-absorption iteration stops at its second pass with the
+    plain result."""
+    wl = synth.make_workload(0, cells=np.arange(40))
+    plain = oracle.run_workload(wl)
+    res, it, ch = oracle.run_coupled(wl.lam, wl.w, wl.C_abs, wl.J, np.zeros_like(wl.J, dtype=np.float64), wl.n,
+                                     wl.T_min, wl.T_max)
+    assert it == 2 and ch == 0.0
+    for k in ("T", "L", "resid"):
+        np.testing.assert_array_equal(res[k], plain[k])
+
+
+def test_coupled_gray_grain_closed_form(si):
+    """One gray grain (cross section c, number n) in W B(T*) with a constant
+    coupling e: absorbed c (J_bol + e sum w L) with sum w L = 4 pi n c sigma T^4 / pi
+    equals emitted c sigma T^4 / pi, so T = T* (W / (1 - 4 pi e n c))^(1/4)."""
+    lam, w = ext_grid()
+    c = 3.0e-14
+    Ts, W = 300.0, 1e-3
+    J = (W * _bb_field(lam, Ts, si))[None, :]
+    for frac in (0.0, 0.3, 0.7):          # 4 pi e n c
+        n = np.array([[2.0]])
+        e = frac / (4.0 * math.pi * n[0, 0] * c)
+        res, it, ch = oracle.run_coupled(lam, w, np.full((1, len(lam)), c), J, np.full_like(J, e), n, 2.0, 3000.0)
+        expect = Ts * (W / (1.0 - frac)) ** 0.25
+        assert res["T"][0, 0] == pytest.approx(expect, rel=1e-10), (frac, it)
+        assert abs(res["resid"][0]) < 1e-10
