@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-large", action="store_true", help="skip the 2^20-cell, K=500, G=240 solve")
     ap.add_argument("--no-ablation", action="store_true", help="skip the paper's kernel-3 Newton solve")
     ap.add_argument("--no-coupled", action="store_true", help="skip the self-absorbing (coupled) solve")
+    ap.add_argument("--no-mass", action="store_true", help="skip the dust-mass form n[c,g] = n_g m_c")
     ap.add_argument("--large-cells", type=int, default=1 << 20,
                     help="cells of the K=500, G=240 solve (the full case is 2^20; fewer for profiling captures)")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -301,6 +302,8 @@ def run_ours(args):
                     "T_only_ms": round(r["ms_T_only"], 5),
                     "T_only_solves_per_s": C * G * world / (r["ms_T_only"] * 1e-3)}
     line["paths"] = paths
+    if not args.no_mass:
+        line["paths"][main + "_dust_mass_form"] = mass_form(ctxs[main], wl, J, stream, args, world, dev)
     if not args.no_ablation:
         line["ablation_paper_kernel3"] = paper_newton_ablation(ctxs[main], wl, J, stream, res[main]["ms_T_only"])
     if not args.no_coupled:
@@ -350,6 +353,33 @@ def paper_newton_ablation(ctx, wl, J, stream, ms_table_T_only):
             "not_converged": int((out["flags"] == 8).sum()),
             "method": "per (cell, grain) Newton in T with the K-term quadrature at every iterate, "
                       "Eqs. 11-12 guess floored at 5 K, stop at 0.1 % energy non-conservation; same BF16x3 GEMM"}
+
+
+def mass_form(ctx, wl, J, stream, args, world, dev):
+    """The same step through dust_solve_mass: the workload's grain numbers are
+    n[c,g] = rho_c n0_g, so n_g = n[0,:] and m_c = n[c,0] / n[0,0]."""
+    import numpy as np
+    import torch
+
+    n64 = wl.n.astype(np.float64)
+    ctx.set_grain_numbers(n64[0])
+    m = torch.from_numpy((n64[:, 0] / n64[0, 0]).astype(np.float32)).to(dev)
+    C, G = J.shape[0], ctx.G
+    out = ctx.alloc_outputs(C, J.stride(0))
+    for _ in range(max(3, args.warmup)):
+        ctx.solve_mass(J, m, out=out, stream=stream)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 60))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.solve_mass(J, m, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
+    return {"ms_step": round(ms, 5), "solves_per_s": aggregate_rate(C * G, world, ms * 1e-3),
+            "sed_cells_per_s": aggregate_rate(C, world, ms * 1e-3),
+            "api": "dust_solve_mass (n[c,g] = n_g m_c, Eqs. 9-10)"}
 
 
 def coupled_solve(ctx, wl, J, n, stream):

@@ -245,6 +245,24 @@ int dust_server_stats(dust_server *srv, dust_serve_stats *out);
 int dust_server_reset_stats(dust_server *srv);
 void dust_server_destroy(dust_server *srv);
 
+/* ------------------------------------------------------- dust-mass form
+ * The paper writes the grain numbers of a cell as n_s m_d;c (Eqs. 9-10): a
+ * fixed number of grains of each kind per unit dust mass times the cell's
+ * dust mass.  With n[c,g] = n_g m_c the emission weights can carry n_g, so
+ * each Planck term of the emission sum needs one FP32 operation less.
+ *
+ * dust_ctx_set_grain_numbers: n_g[G] host FP64 >= 0 (not all 0), grains per
+ *   unit mass; builds the dust-mass emission tables (synchronous; may be
+ *   called again to replace them).
+ * dust_solve_mass: as dust_solve with n replaced by m[C] FP32 device, the
+ *   cells' dust masses (>= 0); the result is that of dust_solve with
+ *   n[c,g] = n_g m_c up to FP32 rounding.  resid is computed per unit mass
+ *   (it does not depend on m_c; 0 / 0 does not arise for m_c = 0).
+ *   DUST_EINVAL before dust_ctx_set_grain_numbers. */
+int dust_ctx_set_grain_numbers(dust_ctx *ctx, const double *n_g);
+int dust_solve_mass(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *m, float *T,
+                    float *L, double *resid, uint8_t *flags, void *stream);
+
 /* ------------------------------------------------------- self-absorption
  * Dust that is optically thick to its own emission is heated by it as well,
  * so the paper's radiative-transfer code iterates the radiation field and the

@@ -42,6 +42,8 @@ _SIGS = {
     "dust_ctx_set_grain_sizes": (_i, [_p, _p]),
     "dust_solve_T_newton": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p]),
     "dust_solve_coupled": (_i, [_p, _i64, _p, _i64, _p, _p, _i, _d, _p, _p, _p, _p, _p, _p, _p]),
+    "dust_ctx_set_grain_numbers": (_i, [_p, _p]),
+    "dust_solve_mass": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
     "dust_diag_wait_timeout": (_i, [_i, _d, _p, _p]),
     "dust_diag_throughput": (_i, [_i, _p, _p]),
     "dust_solve_noalloc": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
@@ -246,3 +248,11 @@ def dust_solve_coupled(ctx, n_cells, J_ext, ld, E, n, max_iters, tol, T, L, resi
     check(lib().dust_solve_coupled(ctx, n_cells, J_ext, ld, E, n, max_iters, tol, T, L, resid, flags,
                                    ctypes.byref(it), ctypes.byref(ch), stream))
     return it.value, ch.value
+
+
+def dust_ctx_set_grain_numbers(ctx, n_g):
+    return check(lib().dust_ctx_set_grain_numbers(ctx, n_g))
+
+
+def dust_solve_mass(ctx, n_cells, J, ld, m, T, L, resid, flags, stream):
+    return check(lib().dust_solve_mass(ctx, n_cells, J, ld, m, T, L, resid, flags, stream))

@@ -135,6 +135,31 @@ class Context:
                                    _ptr(out["flags"]), sptr)
         return t, out
 
+    def set_grain_numbers(self, n_g):
+        """Grains of each kind per unit dust mass [G] (the paper's n_s), for solve_mass."""
+        a = np.ascontiguousarray(n_g, dtype=np.float64)
+        if a.shape != (self.G,):
+            raise ValueError(f"n_g must have shape ({self.G},)")
+        _lib.dust_ctx_set_grain_numbers(self.handle, a.ctypes.data)
+
+    def solve_mass(self, J, m, out=None, want_L=True, want_resid=True, want_flags=True, stream=None):
+        """The hot path with n[c,g] = n_g m_c (Eqs. 9-10): m [C] float32 CUDA
+        tensor of the cells' dust masses; outputs as solve()."""
+        C = J.shape[0]
+        if m.shape != (C,) or m.dtype != torch.float32 or not m.is_cuda or not m.is_contiguous():
+            raise ValueError("m must be a contiguous float32 CUDA tensor of shape [C]")
+        if J.dim() != 2 or J.shape[1] != self.K or J.stride(1) != 1 or J.dtype != torch.float32 or not J.is_cuda:
+            raise ValueError(f"J must be a [C, {self.K}] float32 CUDA tensor with unit column stride")
+        ld = J.stride(0)
+        if out is None:
+            out = self.alloc_outputs(C, ld, want_L, want_resid, want_flags)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _lib.dust_solve_mass(self.handle, C, J.data_ptr(), ld, m.data_ptr(), out["T"].data_ptr(),
+                             _ptr(out["L_buf"]), _ptr(out["resid"]), _ptr(out["flags"]), sptr)
+        return out
+
     def solve_coupled(self, J_ext, E, n, max_iters=50, tol=1e-6, stream=None):
         """Self-absorbing solve: J = J_ext + E L iterated with the solve until L
         changes by at most `tol` (peak-normalised).  J_ext and E are [C, K]

@@ -411,6 +411,7 @@ void free_context(dust_ctx *ctx) {
     cudaFree(ctx->Wimg[1]);
     cudaFree(ctx->S);
     cudaFree(ctx->newton_grain);
+    cudaFree(ctx->mass_mem);
     cudaFree(ctx->cpl);
     auto &hs = ctx->hs;
     for (int i = 0; i < dust_ctx::NHB; ++i) {
@@ -495,6 +496,11 @@ int dust_ctx_create(dust_ctx **out, int K, const double *lambda, const double *w
                            prop.major, prop.minor);
     }
     if (rc == DUST_OK) rc = build_context(ctx, lambda, w, c_abs);
+    if (rc == DUST_OK) {
+        ctx->lam_h.assign(lambda, lambda + K);
+        ctx->w_h.assign(w, w + K);
+        ctx->C_h.assign(c_abs, c_abs + (size_t)G * K);
+    }
     cudaSetDevice(prev);
     if (rc != DUST_OK) { free_context(ctx); return rc; }
     *out = ctx;
@@ -526,3 +532,82 @@ int dust_ctx_info(const dust_ctx *ctx, int *K, int *G, int *n_table, int *precis
 }
 
 }  // extern "C"
+
+// Dust-mass form (Eqs. 9-10: n[c,g] = n_g m_c): emission weights built from
+// n_g C_abs[g,k] with their own per-wavelength exponents, residual weights and
+// constants, and the normalised n_g for the absorbed side of the residual.
+extern "C" int dust_ctx_set_grain_numbers(dust_ctx *ctx, const double *n_g) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    if (!n_g) return set_error(DUST_EINVAL, "n_g is NULL");
+    const int K = ctx->K, G = ctx->G;
+    double nmax = 0.0;
+    for (int g = 0; g < G; ++g) {
+        if (!(n_g[g] >= 0.0) || !std::isfinite(n_g[g]))
+            return set_error(DUST_EINVAL, "n_g[%d] must be finite and >= 0", g);
+        nmax = std::max(nmax, n_g[g]);
+    }
+    if (!(nmax > 0.0)) return set_error(DUST_EINVAL, "every n_g is 0");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return set_error(DUST_ECUDA, "cudaGetDevice failed");
+    if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess)
+        return set_error(DUST_ECUDA, "cudaSetDevice(%d) failed", ctx->device);
+    const DevTables &tb = ctx->tb;
+    const int G8 = tb.G8, Kp = tb.Kp, NKG = tb.NKG;
+    size_t off = 0;
+    auto take = [&](size_t b) { const size_t o = off; off = align256(off + b); return o; };
+    const size_t o_Ch = take(sizeof(float) * (size_t)G8 * Kp), o_q = take(sizeof(int) * Kp),
+                 o_wq = take(sizeof(float) * K), o_ng = take(sizeof(float) * G8), o_nax = take(sizeof(float) * Kp);
+    int rc = DUST_OK;
+    DevBuf t_lam, t_C;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && !ctx->mass_mem) e = cudaMalloc(&ctx->mass_mem, off);
+    if (e == cudaSuccess) e = cudaMalloc(&t_lam.p, sizeof(double) * K);
+    if (e == cudaSuccess) e = cudaMalloc(&t_C.p, sizeof(double) * G * K);
+    std::vector<double> Cn((size_t)G * K);
+    for (int g = 0; g < G; ++g)
+        for (int k = 0; k < K; ++k) Cn[(size_t)g * K + k] = n_g[g] * ctx->C_h[(size_t)g * K + k];
+    if (e == cudaSuccess) e = cudaMemcpy(t_lam.p, ctx->lam_h.data(), sizeof(double) * K, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(t_C.p, Cn.data(), sizeof(double) * G * K, cudaMemcpyHostToDevice);
+    char *base = static_cast<char *>(ctx->mass_mem);
+    if (e == cudaSuccess) {
+        k_emis<<<Kp, 32>>>(K, G, G8, Kp, NKG, (const double *)t_lam.p, (const double *)t_C.p,
+                           (float *)(base + o_Ch), (int *)(base + o_q), (float *)(base + o_nax));
+        e = cudaGetLastError();
+    }
+    std::vector<int> q(Kp);
+    if (e == cudaSuccess) e = cudaMemcpy(q.data(), base + o_q, sizeof(int) * Kp, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = set_error(DUST_ECUDA, "building the dust-mass tables: %s", cudaGetErrorString(e));
+    DevTables tm = tb;
+    if (rc == DUST_OK) {
+        double mx = 0.0;
+        for (int k = 0; k < K; ++k) mx = std::max(mx, ctx->w_h[k] * std::ldexp(1.0, q[k]));
+        const int Ew = mx > 0.0 ? (int)std::ceil(std::log2(mx)) : 0;
+        std::vector<float> wq(K);
+        for (int k = 0; k < K; ++k) wq[k] = (float)std::ldexp(ctx->w_h[k], q[k] - Ew);
+        const int En = (int)std::ceil(std::log2(nmax));
+        std::vector<float> ng(G8, 0.f);
+        for (int g = 0; g < G; ++g) ng[g] = (float)std::ldexp(n_g[g], -En);
+        e = cudaMemcpy(base + o_wq, wq.data(), sizeof(float) * K, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(base + o_ng, ng.data(), sizeof(float) * G8, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = set_error(DUST_ECUDA, "uploading the dust-mass tables: %s", cudaGetErrorString(e));
+        // residual: emitted per unit mass (h + l) 2^Ew over 4 pi absorbed per unit
+        // mass (ah + al) 2^(Eg + En)
+        int ex = 0;
+        const double v = std::frexp(std::ldexp(1.0 / (4.0 * 3.14159265358979323846), Ew - tb.Eg - En), &ex);
+        tm.Chat = (const float *)(base + o_Ch);
+        tm.qexp = (const int *)(base + o_q);
+        tm.wq = (const float *)(base + o_wq);
+        tm.Ew = Ew;
+        tm.rc_hi = (float)v;
+        tm.rc_lo = (float)(v - (double)tm.rc_hi);
+        tm.rc_exp = ex;
+        tm.ng = (const float *)(base + o_ng);
+    }
+    if (rc == DUST_OK) {
+        ctx->tbm = tm;
+        ctx->mass_ready = true;
+    }
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return rc;
+}

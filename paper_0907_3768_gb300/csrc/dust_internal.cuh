@@ -59,21 +59,26 @@ struct DevTables {
     int Ew;
     float rc_hi, rc_lo;       // 2^(Ew - Eg) / (4 pi) = (rc_hi + rc_lo) 2^rc_exp, rc_hi in [1/2, 1)
     int rc_exp;
+    const float *ng;          // dust-mass form only: [G8] grains per unit mass n_g 2^-En (0 padding)
     int *status;              // device status word (dust_status)
 };
 
 // ---- work lists of the batched kernels (passed by value as kernel parameters)
 constexpr int MAXREQ = 32;
 
-enum EmitMode { EMIT_ON = 1, EMIT_RESID = 2, EMIT_STORE_L = 4 };
+// EMIT_MASS: n[c,g] = m_c n_g (the paper's n_s m_d;c, Eqs. 9-10); req.n holds m [C]
+// and req.tb the dust-mass tables, whose emission weights carry n_g.
+enum EmitMode { EMIT_ON = 1, EMIT_RESID = 2, EMIT_STORE_L = 4, EMIT_MASS = 8 };
 
 // Per-cell record passed from the solve to the emission: exponent m_c of
 // max_g n[c,g] and the absorbed power sum_g n Pe = (ah + al) 2^(m_c + Eg)
-// as a float-float pair (the residual's denominator / 4 pi).
+// as a float-float pair (the residual's denominator / 4 pi).  In the
+// dust-mass form m_c is the exponent of the cell's mass m = ms 2^m_c (ms in
+// [1/2, 1), stored as bits) and the absorbed power is taken per unit mass.
 struct CellInfo {
     int mc;
     float ah, al;
-    int pad;
+    int ms_bits;
 };
 
 // A request's scratch: S [C][Gs] FP32, then (emission only) the pairs
@@ -162,6 +167,12 @@ struct dust_ctx {
     // per-grain constants of the paper's Newton kernel (float2 [G]; NULL until
     // dust_ctx_set_grain_sizes)
     void *newton_grain = nullptr;
+    // dust-mass form (dust_ctx_set_grain_numbers): its tables and one block of
+    // device memory holding its emission weights, exponents and n_g
+    bool mass_ready = false;
+    dust::DevTables tbm{};
+    void *mass_mem = nullptr;
+    std::vector<double> lam_h, w_h, C_h;  // host copies of the context's inputs
     // working J, previous L and a change word of dust_solve_coupled
     void *cpl = nullptr;
     size_t cpl_bytes = 0;
@@ -213,7 +224,7 @@ int launch_gemm_tc(const dust_ctx *ctx, int precision, int64_t C, const float *J
                    float *S, cudaStream_t st);
 int launch_solve_emit(const dust_ctx *ctx, int64_t C, const ScratchView &sv, const float *n, float *T,
                       float *L, int64_t ld, double *resid, uint8_t *flags, cudaStream_t st);
-EmitPlan plan_emit(const dust_ctx *ctx, bool emit);
+EmitPlan plan_emit(const dust_ctx *ctx, bool emit, bool mass);
 // Scratch bytes of a request of C cells and its layout at `base`.
 size_t scratch_bytes(const dust_ctx *ctx, int64_t C, bool emit);
 ScratchView scratch_view(const dust_ctx *ctx, int64_t C, void *base);
@@ -228,7 +239,7 @@ int launch_tc_batch(const TcBatch &B, int precision, size_t smem, int num_sms, c
 void make_simt_req(const dust_ctx *ctx, int64_t C, const float *J, int64_t ld, float *S, SimtReq &r);
 int launch_simt_batch(SimtBatch &B, cudaStream_t st);
 void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const ScratchView &sv, const float *n,
-                   float *T, float *L, int64_t ld, double *resid, uint8_t *flags, EmitReq &r);
+                   float *T, float *L, int64_t ld, double *resid, uint8_t *flags, EmitReq &r, bool mass);
 // Numbers cells and tiles, then launches the solve over every request and the
 // emission over those that want L or resid; `between` (optional) is recorded
 // on `st` between the two kernels.
@@ -241,7 +252,7 @@ int ensure_scratch(dust_ctx *ctx, int64_t cells, cudaStream_t st);
 // bytes at `scratch`.
 int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld,
                  const float *n, float *T, float *L, double *resid, uint8_t *flags, void *scratch,
-                 cudaStream_t st);
+                 cudaStream_t st, bool mass = false);
 
 // Bounded spin budget for device-side waits: a wait that exceeds it records
 // DUST_ETIMEOUT in the status word and gives up.

@@ -276,10 +276,10 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
         ServeReq *r = p.r;
         dust_ctx *ctx = r->ctx;
         const int G = ctx->G;
-        const EmitPlan pl = plan_emit(ctx, r->L || r->resid);
+        const EmitPlan pl = plan_emit(ctx, r->L || r->resid, false);
         fill_emit_req(ctx, pl, p.cn, part_view(p), r->n + p.c0 * G, r->T + p.c0 * G,
                       r->L ? r->L + p.c0 * r->ld : nullptr, r->ld, r->resid ? r->resid + p.c0 : nullptr,
-                      r->flags ? r->flags + p.c0 * G : nullptr, E.req[E.nreq++]);
+                      r->flags ? r->flags + p.c0 * G : nullptr, E.req[E.nreq++], false);
         smem = std::max(smem, pl.smem);
         emit = emit || r->L || r->resid;
         resid = resid || r->resid;

@@ -89,7 +89,7 @@ cudaEvent_t prof_event(dust_ctx *ctx) {
 }  // namespace
 
 int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, const float *n,
-                 float *T, float *L, double *resid, uint8_t *flags, void *scratch, cudaStream_t st) {
+                 float *T, float *L, double *resid, uint8_t *flags, void *scratch, cudaStream_t st, bool mass) {
     if (C == 0) return DUST_OK;
     const ScratchView sv = scratch_view(ctx, C, scratch);
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -101,10 +101,10 @@ int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_
                                          : launch_gemm_tc(ctx, precision, C, J, ld, sv.S, st);
     if (rc == DUST_OK) {
         if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[1], st));
-        const EmitPlan p = plan_emit(ctx, L || resid);
+        const EmitPlan p = plan_emit(ctx, L || resid, mass);
         EmitBatch B;
         B.nreq = 1;
-        fill_emit_req(ctx, p, C, sv, n, T, L, ld, resid, flags, B.req[0]);
+        fill_emit_req(ctx, p, C, sv, n, T, L, ld, resid, flags, B.req[0], mass);
         rc = launch_emit_batch(B, p.smem, ctx->num_sms, st, prof ? ev[2] : nullptr);
         if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[3], st));
     }
@@ -132,6 +132,22 @@ int dust_solve_prec(dust_ctx *ctx, int precision, int64_t n_cells, const float *
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = ensure_scratch(ctx, n_cells, st)) != DUST_OK) return rc;
     return solve_device(ctx, precision, n_cells, J, ld, n, T, L, resid, flags, ctx->S, st);
+}
+
+int dust_solve_mass(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *m, float *T,
+                    float *L, double *resid, uint8_t *flags, void *stream) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    if (!ctx->mass_ready) return set_error(DUST_EINVAL, "grain numbers not set: call dust_ctx_set_grain_numbers");
+    const int precision = ctx->precision;
+    // m [C] takes n's place in the checks (it is read as one float per cell)
+    int rc = validate(ctx, precision, n_cells, J, ld, m, T, L, resid, flags, true);
+    if (rc != DUST_OK || n_cells == 0) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    if (dg.rc != DUST_OK) return dg.rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ensure_scratch(ctx, n_cells, st)) != DUST_OK) return rc;
+    return solve_device(ctx, precision, n_cells, J, ld, m, T, L, resid, flags, ctx->S, st, true);
 }
 
 int dust_solve(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n, float *T,

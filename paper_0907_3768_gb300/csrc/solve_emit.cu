@@ -177,7 +177,7 @@ template <int NB>
 __device__ __forceinline__ void load_pass(const EmitReq &q, int64_t cell, int gb, int lane, float (&s)[NB],
                                           float (&nv)[NB]) {
     const int G = q.tb.G;
-    const bool with_n = (q.mode & EMIT_ON) != 0;
+    const bool with_n = (q.mode & EMIT_ON) != 0 && !(q.mode & EMIT_MASS);
     const float *Srow = q.S + cell * q.tb.Gs;
     const float *nrow = q.n + cell * G;
 #pragma unroll
@@ -195,7 +195,7 @@ __device__ __forceinline__ void load_pass(const EmitReq &q, int64_t cell, int gb
 // software-pipelined: the next cell's first-pass loads are issued before this
 // cell's two dependent table lookups, so their DRAM latency overlaps them.
 template <int NB>
-__global__ void __launch_bounds__(SOLVE_TH) k_solve(const __grid_constant__ EmitBatch B) {
+__global__ void __launch_bounds__(SOLVE_TH, NB >= 4 ? 5 : 6) k_solve(const __grid_constant__ EmitBatch B) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * SOLVE_TH) >> 5;
     int64_t u = ((int64_t)blockIdx.x * SOLVE_TH + threadIdx.x) >> 5;  // this warp's first cell
@@ -220,8 +220,14 @@ __global__ void __launch_bounds__(SOLVE_TH) k_solve(const __grid_constant__ Emit
             load_pass<NB>(B.req[rn], un - B.req[rn].cell_begin, 0, lane, s1, n1);
         }
         const bool one = G8 <= 32 * NB;
+        const bool mass = (q.mode & EMIT_MASS) != 0;
         int mc = 0;
-        if (!one && emit) {
+        float ms = 0.f;  // dust-mass form: m_c = ms 2^mc
+        if (emit && mass) {
+            const float m = __ldg(q.n + cell);
+            ms = (m != 0.f && isfinite(m)) ? frexpf(m, &mc) : m;
+        }
+        if (!one && emit && !mass) {
             const float *nrow = q.n + cell * G;
             float mx = 0.f;
             for (int g = lane; g < G; g += 32) mx = fmaxf(mx, __ldg(nrow + g));
@@ -245,7 +251,7 @@ __global__ void __launch_bounds__(SOLVE_TH) k_solve(const __grid_constant__ Emit
                 gi[i] = g < G ? g : 0;
                 gq[i] = __ldg(reinterpret_cast<const float4 *>(tb.gp) + gi[i]);
             }
-            if (one && emit) {
+            if (one && emit && !mass) {
                 float mx = 0.f;
 #pragma unroll
                 for (int i = 0; i < NB; ++i) mx = fmaxf(mx, nv[i]);
@@ -262,7 +268,7 @@ __global__ void __launch_bounds__(SOLVE_TH) k_solve(const __grid_constant__ Emit
                     q.T[cell * G + g] = Tv[i];
                     if (q.flags) q.flags[cell * G + g] = (uint8_t)fl[i];
                     invT = rcp_approx(Tv[i]);
-                    nn = scale2(nv[i], -mc);
+                    nn = mass ? __ldg(tb.ng + g) : scale2(nv[i], -mc);
                     if (rs) {
                         const float4 gr = __ldg(tb.gres + g);
                         const float se = fl[i] == DUST_FLAG_OK ? s[i]
@@ -273,7 +279,10 @@ __global__ void __launch_bounds__(SOLVE_TH) k_solve(const __grid_constant__ Emit
                         ff_add(ah, al, rh, fmaf(xh, gr.x, -rh) + fmaf(xh, gr.y, xl * gr.x));
                     }
                 }
-                if (emit) q.prep[cell * G8 + g] = make_float2(invT, nn);
+                if (emit) {
+                    if (mass) reinterpret_cast<float *>(q.prep)[cell * G8 + g] = invT;
+                    else q.prep[cell * G8 + g] = make_float2(invT, nn);
+                }
             }
         }
         if (emit) {
@@ -287,7 +296,7 @@ __global__ void __launch_bounds__(SOLVE_TH) k_solve(const __grid_constant__ Emit
                 ci.mc = mc;
                 ci.ah = rs ? ah : 0.f;
                 ci.al = rs ? al : 0.f;
-                ci.pad = 0;
+                ci.ms_bits = __float_as_int(ms);
                 q.cell[cell] = ci;
             }
         }
@@ -312,6 +321,20 @@ __device__ __forceinline__ void emit_pair(float2 nax, float2 iT, float2 nn, floa
     N = __ffma2_rn(t, e, N);
     D = __ffma2_rn(make_float2(-t.x, -t.y), D, D);                // D (1 - t)
 }
+// The dust-mass form: the weight is the table's n_g C entry itself.
+__device__ __forceinline__ void emit_pair_m(float2 nax, float2 iT, float2 cw, float2 &N, float2 &D) {
+    const float2 a = __fmul2_rn(nax, iT);
+    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+    const float2 e = __ffma2_rn(cw, D, make_float2(-N.x, -N.y));
+    N = __ffma2_rn(t, e, N);
+    D = __ffma2_rn(make_float2(-t.x, -t.y), D, D);
+}
+__device__ __forceinline__ void emit_first_m(float2 nax, float2 iT, float2 cw, float2 &N, float2 &D) {
+    const float2 a = __fmul2_rn(nax, iT);
+    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+    N = __fmul2_rn(cw, t);
+    D = __ffma2_rn(make_float2(-t.x, -t.y), make_float2(1.f, 1.f), make_float2(1.f, 1.f));
+}
 // The first grain of a group, from N = 0, D = 1: N = w t, D = 1 - t.
 __device__ __forceinline__ void emit_first(float2 nax, float2 iT, float2 nn, float2 cw, float2 &N, float2 &D) {
     const float2 a = __fmul2_rn(nax, iT);
@@ -322,6 +345,11 @@ __device__ __forceinline__ void emit_first(float2 nax, float2 iT, float2 nn, flo
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
                  "l"(src)
                  : "memory");
 }
@@ -337,6 +365,7 @@ __device__ __forceinline__ int emit_req_of(const EmitBatch &B, int64_t tile, int
 // Issue the cp.async copies of a tile's (1/T, n) pairs into the pair-major
 // shared layout [pair][grain][2 cells] (padding cells of a ragged tile read
 // the dummy values instead).
+template <bool MASS>
 __device__ __forceinline__ void prefetch_tile(const EmitReq &q, int64_t local_tile, float *dstTN, int TNP, int tid) {
     const int G8 = q.tb.G8, TC = q.TC;
     const int64_t c0 = local_tile * TC;
@@ -345,9 +374,15 @@ __device__ __forceinline__ void prefetch_tile(const EmitReq &q, int64_t local_ti
     const int dc = NTH / G8, dg = NTH - dc * G8;
     int c = tid / G8, g = tid - c * G8;
     for (int i = tid; i < TC * G8; i += NTH) {
-        float *dst = dstTN + (size_t)(c >> 1) * TNP + 4 * g + 2 * (c & 1);
-        if (c < nc) cp_async8(dst, q.prep + (c0 + c) * G8 + g);
-        else *reinterpret_cast<float2 *>(dst) = make_float2(PAD_INV_T, 0.f);
+        if (MASS) {  // 1/T only: [pair][grain][2 cells] floats
+            float *dst = dstTN + (size_t)(c >> 1) * TNP + 2 * g + (c & 1);
+            if (c < nc) cp_async4(dst, reinterpret_cast<const float *>(q.prep) + (c0 + c) * G8 + g);
+            else *dst = PAD_INV_T;
+        } else {  // (1/T, n): [pair][grain][2 cells] float2
+            float *dst = dstTN + (size_t)(c >> 1) * TNP + 4 * g + 2 * (c & 1);
+            if (c < nc) cp_async8(dst, q.prep + (c0 + c) * G8 + g);
+            else *reinterpret_cast<float2 *>(dst) = make_float2(PAD_INV_T, 0.f);
+        }
         c += dc;
         g += dg;
         if (g >= G8) { g -= G8; ++c; }
@@ -355,6 +390,7 @@ __device__ __forceinline__ void prefetch_tile(const EmitReq &q, int64_t local_ti
     cp_async_commit();
 }
 
+template <bool MASS>
 __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBatch B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x;
@@ -379,7 +415,7 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
             __syncthreads();  // the previous request is done with shared memory
             cp_async_wait_all();
             cur = ri;
-            TNP = 4 * G8 + 4;
+            TNP = (MASS ? 2 : 4) * G8 + 4;
             CST = 2 * (q.resident ? G8 : q.GC) + 1;
             TNB = (NP + 1) * TNP;  // floats per (1/T, n) tile buffer
             oTN = NKG * CST * 16;
@@ -388,8 +424,10 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
             ipair = okit ? tid - ikg * NP : NP;  // idle threads read the dummy pair row NP
             for (int b = 0; b < 2; ++b) {
                 float *dummy = reinterpret_cast<float *>(smem_raw + oTN) + (size_t)b * TNB + (size_t)NP * TNP;
-                for (int g = tid; g < G8; g += NTH)
-                    *reinterpret_cast<float4 *>(dummy + 4 * g) = make_float4(PAD_INV_T, 0.f, PAD_INV_T, 0.f);
+                for (int g = tid; g < G8; g += NTH) {
+                    if (MASS) *reinterpret_cast<float2 *>(dummy + 2 * g) = make_float2(PAD_INV_T, PAD_INV_T);
+                    else *reinterpret_cast<float4 *>(dummy + 4 * g) = make_float4(PAD_INV_T, 0.f, PAD_INV_T, 0.f);
+                }
             }
             if (q.resident) {
                 const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
@@ -409,7 +447,7 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
         __syncthreads();  // previous tile finished with shared memory
         if (pref != tile) {  // not prefetched (first tile of a request)
             buf = 0;
-            prefetch_tile(q, lt, sTN0, TNP, tid);
+            prefetch_tile<MASS>(q, lt, sTN0, TNP, tid);
         }
         cp_async_wait_all();
         __syncthreads();
@@ -417,7 +455,7 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
         // prefetch the next tile of this request into the other buffer
         const int64_t nt = tile + gridDim.x;
         if (nt < B.ntiles && emit_req_of(B, nt, ri) == ri) {
-            prefetch_tile(q, nt - q.tile_begin, sTN0 + (size_t)(buf ^ 1) * TNB, TNP, tid);
+            prefetch_tile<MASS>(q, nt - q.tile_begin, sTN0 + (size_t)(buf ^ 1) * TNB, TNP, tid);
             pref = nt;
         } else {
             pref = -1;
@@ -444,25 +482,41 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
             }
             const int goff = q.resident ? g0 : 0;
             const float4 *tnp = reinterpret_cast<const float4 *>(sTN + (size_t)ipair * TNP) + g0;
+            const float2 *tnm = reinterpret_cast<const float2 *>(sTN + (size_t)ipair * TNP) + g0;
             const float4 *cp = sC + (size_t)ikg * CST + 2 * goff;
             for (int gg0 = 0; gg0 < gn; gg0 += RG) {
                 float2 N[2][4], D[2][4];
 #pragma unroll
                 for (int u = 0; u < RG; ++u) {
-                    const float4 tn = tnp[gg0 + u];  // (1/T, n) of both cells
                     const float4 ca = cp[2 * (gg0 + u)], cb = cp[2 * (gg0 + u) + 1];
                     const float2 cw[4] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w), make_float2(cb.x, cb.y),
                                           make_float2(cb.z, cb.w)};
-                    const float2 iTa = make_float2(tn.x, tn.x), na = make_float2(tn.y, tn.y);
-                    const float2 iTb = make_float2(tn.z, tn.z), nb = make_float2(tn.w, tn.w);
+                    if (MASS) {
+                        const float2 tm = tnm[gg0 + u];  // 1/T of both cells
+                        const float2 iTa = make_float2(tm.x, tm.x), iTb = make_float2(tm.y, tm.y);
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        if (u == 0) {
-                            emit_first(nax2[p], iTa, na, cw[p], N[0][p], D[0][p]);
-                            emit_first(nax2[p], iTb, nb, cw[p], N[1][p], D[1][p]);
-                        } else {
-                            emit_pair(nax2[p], iTa, na, cw[p], N[0][p], D[0][p]);
-                            emit_pair(nax2[p], iTb, nb, cw[p], N[1][p], D[1][p]);
+                        for (int p = 0; p < 4; ++p) {
+                            if (u == 0) {
+                                emit_first_m(nax2[p], iTa, cw[p], N[0][p], D[0][p]);
+                                emit_first_m(nax2[p], iTb, cw[p], N[1][p], D[1][p]);
+                            } else {
+                                emit_pair_m(nax2[p], iTa, cw[p], N[0][p], D[0][p]);
+                                emit_pair_m(nax2[p], iTb, cw[p], N[1][p], D[1][p]);
+                            }
+                        }
+                    } else {
+                        const float4 tn = tnp[gg0 + u];  // (1/T, n) of both cells
+                        const float2 iTa = make_float2(tn.x, tn.x), na = make_float2(tn.y, tn.y);
+                        const float2 iTb = make_float2(tn.z, tn.z), nb = make_float2(tn.w, tn.w);
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            if (u == 0) {
+                                emit_first(nax2[p], iTa, na, cw[p], N[0][p], D[0][p]);
+                                emit_first(nax2[p], iTb, nb, cw[p], N[1][p], D[1][p]);
+                            } else {
+                                emit_pair(nax2[p], iTa, na, cw[p], N[0][p], D[0][p]);
+                                emit_pair(nax2[p], iTb, nb, cw[p], N[1][p], D[1][p]);
+                            }
                         }
                     }
                 }
@@ -487,7 +541,9 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
             const int c = 2 * ipair + r;
             if (c >= nc) continue;
             const int64_t cell = c0 + c;
-            const int mc = q.cell[cell].mc;
+            const CellInfo ci = q.cell[cell];
+            const int mc = ci.mc;
+            const float ms = MASS ? __int_as_float(ci.ms_bits) : 1.f;  // the cell's mass mantissa
             float sh = 0.f, sl = 0.f;
             const int kb = ikg * KQ;
             float Lv[KQ];
@@ -497,7 +553,7 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
                 for (int h = 0; h < 2; ++h) {
                     const int k = min(kb + 2 * p + h, K - 1);
                     const float a = h ? acc[r][p].y : acc[r][p].x;
-                    Lv[2 * p + h] = scale2(a, mc + __ldg(tb.qexp + k));
+                    Lv[2 * p + h] = scale2(MASS ? a * ms : a, mc + __ldg(tb.qexp + k));
                 }
             }
             if (storeL) {
@@ -562,14 +618,14 @@ __global__ void __launch_bounds__(SOLVE_TH) k_resid(const __grid_constant__ Emit
 
 // Emission geometry of one request: cells per tile, grain chunk, residency
 // of the emission weights and the shared memory they need.
-EmitPlan plan_emit(const dust_ctx *ctx, bool emit) {
+EmitPlan plan_emit(const dust_ctx *ctx, bool emit, bool mass) {
     const DevTables &tb = ctx->tb;
     EmitPlan p{};
     const int NP = std::max(1, std::min(32, NTH / tb.NKG));  // cell pairs per tile
     p.TC = 2 * NP;
     if (!emit) { p.GC = tb.G8; p.resident = 0; p.smem = 0; return p; }
     const size_t budget = 113 * 1024;  // two CTAs per SM
-    const size_t fixed = (size_t)2 * (NP + 1) * (4 * tb.G8 + 4) * 4 + 64;
+    const size_t fixed = (size_t)2 * (NP + 1) * ((mass ? 2 : 4) * tb.G8 + 4) * 4 + 64;
     const size_t full = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + fixed;
     if (full <= budget) { p.GC = tb.G8; p.resident = 1; p.smem = full; return p; }
     const size_t avail = budget > fixed ? budget - fixed : 0;
@@ -606,8 +662,8 @@ ScratchView scratch_view(const dust_ctx *ctx, int64_t C, void *base) {
 }
 
 void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const ScratchView &sv, const float *n,
-                   float *T, float *L, int64_t ld, double *resid, uint8_t *flags, EmitReq &r) {
-    r.tb = ctx->tb;
+                   float *T, float *L, int64_t ld, double *resid, uint8_t *flags, EmitReq &r, bool mass) {
+    r.tb = mass ? ctx->tbm : ctx->tb;
     r.C = C;
     r.ld = ld;
     r.tile_begin = 0;
@@ -624,13 +680,14 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
     r.TC = p.TC;
     r.GC = p.GC;
     r.resident = p.resident;
-    r.mode = ((L || resid) ? EMIT_ON : 0) | (resid ? EMIT_RESID : 0) | (L ? EMIT_STORE_L : 0);
+    r.mode = ((L || resid) ? EMIT_ON : 0) | (resid ? EMIT_RESID : 0) | (L ? EMIT_STORE_L : 0) |
+             ((mass && (L || resid)) ? EMIT_MASS : 0);
 }
 
 // Numbers the cells and emission tiles of a filled batch; launches the solve
 // over every request, then the emission over the requests that want it.
 int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, cudaEvent_t between) {
-    int64_t cells = 0, tiles = 0;
+    int64_t cells = 0;
     for (int i = 0; i < B.nreq; ++i) {
         EmitReq &r = B.req[i];
         r.cell_begin = cells;
@@ -653,36 +710,43 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
         DUST_CUDA_TRY(cudaGetLastError());
     }
     if (between) DUST_CUDA_TRY(cudaEventRecord(between, st));
-    // emission work list: only the requests that want L or resid, in order
-    EmitBatch E;
-    E.nreq = 0;
-    for (int i = 0; i < B.nreq; ++i) {
-        if (!(B.req[i].mode & EMIT_ON)) continue;
-        EmitReq &r = E.req[E.nreq++];
-        r = B.req[i];
-        r.tile_begin = tiles;
-        tiles += (r.C + r.TC - 1) / r.TC;
-    }
-    E.ntiles = tiles;
-    E.ncells = 0;
-    bool resid = false;
-    for (int i = 0; i < E.nreq; ++i) {  // cells of the emission list, numbered afresh
-        E.req[i].cell_begin = E.ncells;
-        E.ncells += E.req[i].C;
-        resid = resid || (E.req[i].mode & EMIT_RESID);
-    }
-    if (tiles == 0) return DUST_OK;
-    DUST_CUDA_TRY(cudaFuncSetAttribute(k_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    DUST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emit, NTH, smem));
-    per_sm = std::max(per_sm, 1);
-    const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * per_sm);
-    k_emit<<<(unsigned)grid, NTH, smem, st>>>(E);
-    DUST_CUDA_TRY(cudaGetLastError());
-    if (resid) {
-        const int64_t rgrid = std::min<int64_t>((E.ncells + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
-        k_resid<<<(unsigned)rgrid, SOLVE_TH, 0, st>>>(E);
+    // emission work lists: the requests that want L or resid, in order, one
+    // list (and launch) per form of the grain numbers
+    for (int form = 0; form < 2; ++form) {
+        EmitBatch E;
+        E.nreq = 0;
+        int64_t tiles = 0;
+        for (int i = 0; i < B.nreq; ++i) {
+            if (!(B.req[i].mode & EMIT_ON) || ((B.req[i].mode & EMIT_MASS) != 0) != (form == 1)) continue;
+            EmitReq &r = E.req[E.nreq++];
+            r = B.req[i];
+            r.tile_begin = tiles;
+            tiles += (r.C + r.TC - 1) / r.TC;
+        }
+        E.ntiles = tiles;
+        E.ncells = 0;
+        bool resid = false;
+        for (int i = 0; i < E.nreq; ++i) {  // cells of the emission list, numbered afresh
+            E.req[i].cell_begin = E.ncells;
+            E.ncells += E.req[i].C;
+            resid = resid || (E.req[i].mode & EMIT_RESID);
+        }
+        if (tiles == 0) continue;
+        const void *kern = form ? reinterpret_cast<const void *>(k_emit<true>)
+                                : reinterpret_cast<const void *>(k_emit<false>);
+        DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        DUST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTH, smem));
+        per_sm = std::max(per_sm, 1);
+        const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * per_sm);
+        if (form) k_emit<true><<<(unsigned)grid, NTH, smem, st>>>(E);
+        else k_emit<false><<<(unsigned)grid, NTH, smem, st>>>(E);
         DUST_CUDA_TRY(cudaGetLastError());
+        if (resid) {
+            const int64_t rgrid = std::min<int64_t>((E.ncells + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
+            k_resid<<<(unsigned)rgrid, SOLVE_TH, 0, st>>>(E);
+            DUST_CUDA_TRY(cudaGetLastError());
+        }
     }
     return DUST_OK;
 }
@@ -690,10 +754,10 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
 int launch_solve_emit(const dust_ctx *ctx, int64_t C, const ScratchView &sv, const float *n, float *T, float *L,
                       int64_t ld, double *resid, uint8_t *flags, cudaStream_t st) {
     if (C <= 0) return DUST_OK;
-    const EmitPlan p = plan_emit(ctx, L || resid);
+    const EmitPlan p = plan_emit(ctx, L || resid, false);
     EmitBatch B;
     B.nreq = 1;
-    fill_emit_req(ctx, p, C, sv, n, T, L, ld, resid, flags, B.req[0]);
+    fill_emit_req(ctx, p, C, sv, n, T, L, ld, resid, flags, B.req[0], false);
     return launch_emit_batch(B, p.smem, ctx->num_sms, st);
 }
 
