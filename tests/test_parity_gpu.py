@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import synth
-from metrics import l_err, t_err
+from metrics import assert_flags_match, l_err, t_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -53,13 +53,13 @@ def _run(ctx, J, n, **kw):
     return {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in out.items()}
 
 
-def _compare(out, ref, prec, rows=None):
+def _compare(out, ref, prec, wl, rows=None):
     tT, tL = TOL[prec]
     T = out["T"] if rows is None else out["T"][rows]
     L = out["L"] if rows is None else out["L"][rows]
     fl = out["flags"] if rows is None else out["flags"][rows]
     r = out["resid"] if rows is None else out["resid"][rows]
-    np.testing.assert_array_equal(fl, ref["flags"])
+    assert_flags_match(fl, ref, wl)
     eT = t_err(T, ref["T"], ref["flags"])
     eL = l_err(L, ref["L"])
     assert eT.max(initial=0.0) <= tT, f"T err {eT.max():.3g}"
@@ -74,7 +74,7 @@ def test_tiny_config_full(prec):
     ref = oracle.run_workload(wl)
     with _ctx(wl, prec) as ctx:
         out = _run(ctx, wl.J, wl.n, precision=prec)
-    _compare(out, ref, prec)
+    _compare(out, ref, prec, wl)
 
 
 @pytest.mark.parametrize("cfg,prec", [(1, "fp32"), (2, "bf16x3"), (2, "fp16x3"), (3, "bf16x3"), (3, "fp32")])
@@ -93,7 +93,7 @@ def test_full_size_sampled(cfg, prec):
         out = _run(ctx, wl.J, wl.n, precision=prec)
     del wl
     assert np.isfinite(out["T"]).all() and np.isfinite(out["L"]).all()
-    _compare(out, ref, prec, rows)
+    _compare(out, ref, prec, sub, rows)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
@@ -117,7 +117,7 @@ def test_ragged_cell_counts(prec, C):
     ref = oracle.run_workload(wl)
     with _ctx(wl, prec) as ctx:
         out = _run(ctx, wl.J, wl.n, precision=prec)
-    _compare(out, ref, prec)
+    _compare(out, ref, prec, wl)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
@@ -129,7 +129,7 @@ def test_odd_shapes(prec):
     ref = oracle.run_workload(wl)
     with _ctx(wl, prec) as ctx:
         out = _run(ctx, wl.J, wl.n, precision=prec)
-    _compare(out, ref, prec)
+    _compare(out, ref, prec, wl)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
@@ -148,7 +148,7 @@ def test_size_limits(prec, K, sizes, species, lam_um):
     ref = oracle.run_workload(wl)
     with _ctx(wl, prec) as ctx:
         out = _run(ctx, wl.J, wl.n, precision=prec)
-    _compare(out, ref, prec)
+    _compare(out, ref, prec, wl)
 
 
 def test_edge_inputs_flags():
