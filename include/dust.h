@@ -104,7 +104,10 @@ void dust_ctx_destroy(dust_ctx *ctx);
 /* Change the default precision of later dust_solve calls. */
 int dust_ctx_set_precision(dust_ctx *ctx, int precision);
 
-/* Shape and capability query: any output pointer may be NULL. */
+/* Shape and capability query: any output pointer may be NULL.  device_bytes
+ * is the device memory the context holds now: its tables and W images, the
+ * grown scratch, the host-buffer staging, and the tables or buffers of the
+ * optional entry points once they have been used. */
 int dust_ctx_info(const dust_ctx *ctx, int *K, int *G, int *n_table, int *precision,
                   int *device, size_t *device_bytes);
 

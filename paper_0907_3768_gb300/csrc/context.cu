@@ -526,8 +526,9 @@ int dust_ctx_info(const dust_ctx *ctx, int *K, int *G, int *n_table, int *precis
     if (precision) *precision = ctx->precision;
     if (device) *device = ctx->device;
     if (device_bytes)
-        *device_bytes = ctx->tables_bytes + sizeof(float) * (size_t)ctx->tb.Gs * ctx->Kw +
-                        2 * ctx->Wimg_bytes + sizeof(float) * ctx->S_cap * ctx->tb.Gs;
+        *device_bytes = ctx->tables_bytes + sizeof(float) * (size_t)ctx->tb.Gs * ctx->Kw + 2 * ctx->Wimg_bytes +
+                        (ctx->S_cap ? scratch_bytes(ctx, (int64_t)ctx->S_cap, true) : 0) + ctx->hs.bytes +
+                        (ctx->newton_grain ? sizeof(float2) * ctx->G : 0) + ctx->mass_bytes + ctx->cpl_bytes;
     return DUST_OK;
 }
 
@@ -561,7 +562,10 @@ extern "C" int dust_ctx_set_grain_numbers(dust_ctx *ctx, const double *n_g) {
     int rc = DUST_OK;
     DevBuf t_lam, t_C;
     cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess && !ctx->mass_mem) e = cudaMalloc(&ctx->mass_mem, off);
+    if (e == cudaSuccess && !ctx->mass_mem) {
+        e = cudaMalloc(&ctx->mass_mem, off);
+        if (e == cudaSuccess) ctx->mass_bytes = off;
+    }
     if (e == cudaSuccess) e = cudaMalloc(&t_lam.p, sizeof(double) * K);
     if (e == cudaSuccess) e = cudaMalloc(&t_C.p, sizeof(double) * G * K);
     std::vector<double> Cn((size_t)G * K);

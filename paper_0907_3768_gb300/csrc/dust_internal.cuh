@@ -172,6 +172,7 @@ struct dust_ctx {
     bool mass_ready = false;
     dust::DevTables tbm{};
     void *mass_mem = nullptr;
+    size_t mass_bytes = 0;
     std::vector<double> lam_h, w_h, C_h;  // host copies of the context's inputs
     // working J, previous L and a change word of dust_solve_coupled
     void *cpl = nullptr;
@@ -191,6 +192,7 @@ struct dust_ctx {
         uint8_t *f[NHB] = {};
         void *S = nullptr;  // one scratch: the compute stream runs one chunk at a time
         int64_t cap = 0, ld = 0;
+        size_t bytes = 0;
     } hs;
     int num_sms = 0;
     size_t smem_optin = 0;

@@ -200,6 +200,8 @@ int dust_solve_host(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, 
         DUST_CUDA_TRY(cudaMalloc(&hs.S, scratch_bytes(ctx, chunk, true)));
         hs.cap = chunk;
         hs.ld = ld;
+        hs.bytes = (size_t)NB * ((size_t)chunk * ld * 4 * 2 + (size_t)chunk * G * (4 * 2 + 1) + (size_t)chunk * 8) +
+                   scratch_bytes(ctx, chunk, true);
     }
     // copy in (stream 0) -> compute (stream 1) -> copy out (stream 2), chunk i in
     // buffer set i % NB: chunk i's upload, chunk i-1's compute and chunk i-2's
