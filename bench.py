@@ -30,6 +30,10 @@ METRIC = "grain-T solves/s & SED cells/s, mixed vs FP32 at stated err, 1 GB300; 
 UNIT = "grain-T solves/s"
 CONFIG_ID = 1
 WORKLOAD = "2^18 cells x 200 wavelengths (0.09-1000 um) x 96 grains (3 species x 32 sizes), P_g(T) table 4096 pts"
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_emit<false> launch on this
+# workload, from one `ncu --set full` capture of that launch; to be retaken
+# whenever the emission kernel changes
+EMIT_TRAFFIC_BYTES = 205.642496e6 + 210.624512e6
 
 
 def parse():
@@ -274,7 +278,10 @@ def run_ours(args):
                 "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "G Planck terms/s",
                 "frac": round(achieved / peak, 4),
                 "peak_source": "measured MUFU ex2.approx issue rate (dust_diag_throughput), 1 ex2 per term",
-                "traffic": None, "ms_per_launch": round(ms_emit, 4),
+                "traffic": EMIT_TRAFFIC_BYTES if (C, K, G) == (1 << 18, 200, 96) and world == 1 else None,
+                "traffic_unit": "bytes per launch (ncu DRAM read + write)",
+                "algorithmic_bytes": C * (8 * ((G + 7) // 8 * 8) + 16 + 4 * K + 8 * ((K + 7) // 8)),
+                "ms_per_launch": round(ms_emit, 4),
                 "fma_pipe_peak_Gflop_lanes": round(fma_rate / 1e9, 1)}
 
     line = {

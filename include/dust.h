@@ -104,6 +104,17 @@ void dust_ctx_destroy(dust_ctx *ctx);
 /* Change the default precision of later dust_solve calls. */
 int dust_ctx_set_precision(dust_ctx *ctx, int precision);
 
+/* Kernel layout of later solves at the tensor-core precisions (Eqs. 6-7):
+ * fused != 0 runs the absorption contraction and the temperature solve as one
+ * kernel whose epilogue solves each cell straight from the tensor-memory
+ * accumulator, so the absorbed powers S[C][G] never go to device memory;
+ * fused == 0 runs them as two kernels with S in the context's scratch.  T,
+ * flags and L are bitwise the same either way; the residual differs by the
+ * summation order of the cell's absorbed power (rounding only).  FP32 solves
+ * ignore the setting.  Takes the context's lock; returns DUST_OK, or
+ * DUST_EINVAL for a NULL context. */
+int dust_ctx_set_fused(dust_ctx *ctx, int fused);
+
 /* Shape and capability query: any output pointer may be NULL.  device_bytes
  * is the device memory the context holds now: its tables and W images, the
  * grown scratch, the host-buffer staging, and the tables or buffers of the

@@ -32,6 +32,7 @@ _SIGS = {
     "dust_ctx_create": (_i, [ctypes.POINTER(_p), _i, _p, _p, _i, _p, _d, _d, _i, _i, _i]),
     "dust_ctx_destroy": (None, [_p]),
     "dust_ctx_set_precision": (_i, [_p, _i]),
+    "dust_ctx_set_fused": (_i, [_p, _i]),
     "dust_ctx_info": (_i, [_p, _p, _p, _p, _p, _p, _p]),
     "dust_solve": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
     "dust_solve_prec": (_i, [_p, _i, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
@@ -109,6 +110,10 @@ def dust_ctx_destroy(ctx):
 
 def dust_ctx_set_precision(ctx, precision):
     return check(lib().dust_ctx_set_precision(ctx, precision))
+
+
+def dust_ctx_set_fused(ctx, fused):
+    return check(lib().dust_ctx_set_fused(ctx, 1 if fused else 0))
 
 
 def dust_ctx_info(ctx):

@@ -79,6 +79,10 @@ class Context:
     def set_precision(self, precision):
         _lib.dust_ctx_set_precision(self.handle, _prec(precision))
 
+    def set_fused(self, fused=True):
+        """Absorption and temperature solve as one kernel (tensor-core precisions)."""
+        _lib.dust_ctx_set_fused(self.handle, fused)
+
     def check(self):
         """Device status word since the last check (0 = DUST_OK)."""
         return _lib.dust_ctx_check(self.handle)

@@ -517,6 +517,13 @@ int dust_ctx_set_precision(dust_ctx *ctx, int precision) {
     return DUST_OK;
 }
 
+int dust_ctx_set_fused(dust_ctx *ctx, int fused) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->fused = fused != 0;
+    return DUST_OK;
+}
+
 int dust_ctx_info(const dust_ctx *ctx, int *K, int *G, int *n_table, int *precision, int *device,
                   size_t *device_bytes) {
     if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");

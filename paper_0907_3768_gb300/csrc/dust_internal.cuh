@@ -111,6 +111,12 @@ struct EmitBatch {
     EmitReq req[MAXREQ];
 };
 
+// Solve requests of a fused absorption + solve launch (index i belongs to
+// TcBatch::req[i]).
+struct SolveList {
+    EmitReq req[MAXREQ];
+};
+
 struct EmitPlan {
     int TC, GC, resident;
     size_t smem;
@@ -154,6 +160,9 @@ struct SimtBatch {
 struct dust_ctx {
     int device = 0;
     int precision = DUST_PREC_FP32;
+    // tensor-core precisions: absorption and temperature solve as one kernel
+    // (dust_ctx_set_fused)
+    bool fused = false;
     int K = 0, G = 0, NT = 0, NI = 0;
     int Kw = 0;               // row length of the FP32 / 16-bit W copies (K rounded to KC)
     double Tmin = 0, Tmax = 0;
@@ -235,8 +244,12 @@ ScratchView scratch_view(const dust_ctx *ctx, int64_t C, void *base);
 // the precision.
 int make_tc_req(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, float *S,
                 TcReq &r, CUtensorMap &tm);
-int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem);
-int launch_tc_batch(const TcBatch &B, int precision, size_t smem, int num_sms, cudaStream_t st);
+// fused: the batch feeds the kernel whose epilogue is the temperature solve
+// (up to four accumulators, each with its own group of solver warps), whose
+// requests `sl` holds.
+int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem, bool fused = false);
+int launch_tc_batch(const TcBatch &B, int precision, size_t smem, int num_sms, cudaStream_t st,
+                    const SolveList *sl = nullptr);
 // FP32 SIMT batches.
 void make_simt_req(const dust_ctx *ctx, int64_t C, const float *J, int64_t ld, float *S, SimtReq &r);
 int launch_simt_batch(SimtBatch &B, cudaStream_t st);
@@ -245,7 +258,10 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
 // Numbers cells and tiles, then launches the solve over every request and the
 // emission over those that want L or resid; `between` (optional) is recorded
 // on `st` between the two kernels.
-int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, cudaEvent_t between = nullptr);
+// With solved = true the temperatures, pairs and cell records are already
+// there (fused absorption + solve) and only the emission runs.
+int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, cudaEvent_t between = nullptr,
+                      bool solved = false);
 
 // Grow the context's scratch to hold `cells` cells (synchronises `st` first).
 int ensure_scratch(dust_ctx *ctx, int64_t cells, cudaStream_t st);

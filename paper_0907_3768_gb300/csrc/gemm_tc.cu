@@ -23,6 +23,7 @@
 // in the status word and winds down.
 #include "dust_internal.cuh"
 #include "mbar.cuh"
+#include "solve_core.cuh"
 
 #include <algorithm>
 #include <cuda.h>
@@ -34,6 +35,8 @@ namespace {
 
 constexpr int BM = 128;                    // cells per tile (UMMA M)
 constexpr int NTHREADS = 352;              // 11 warps
+constexpr int NACC_MAX = 4;                // accumulators (and solver groups of the fused kernel), at most
+constexpr int NTHREADS_F = (7 + 4 * NACC_MAX) * 32;  // fused kernel: 7 + 4 nacc warps
 constexpr int STAGE1_BYTES = BM * KC * 4;  // FP32 staging tile: 16 KB
 constexpr int A_BYTES = BM * KC * 2;       // one 16-bit A part: 8 KB
 
@@ -83,6 +86,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 lanes x 32 bits, 4 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Shared-memory matrix descriptor, K-major, no swizzle: core matrices of
@@ -137,12 +151,122 @@ __device__ __forceinline__ void drain_ring(uint64_t *full, int ns, int64_t n, in
     }
 }
 
+// Fused epilogue, one thread per cell row: the stand-alone solve's work for
+// that cell, with S read from tensor memory (columns of accumulator `tbase`)
+// instead of global memory.  Four grains per step; every result goes through
+// the same solve_batch / grain_out arithmetic as the stand-alone solve, so T,
+// the flags and the emission pairs are bitwise the same; only the order of the
+// cell's absorbed-power sum differs (ascending grains here).  All lanes run
+// the tensor-memory loads; rows past the request (valid = false) store nothing.
+__device__ __forceinline__ void solve_row(const EmitReq &q, int64_t cell, bool valid, int ex, uint32_t tbase) {
+    const DevTables &tb = q.tb;
+    const int G = tb.G, G8 = tb.G8;
+    const bool emit = (q.mode & EMIT_ON) != 0, rs = (q.mode & EMIT_RESID) != 0, mass = (q.mode & EMIT_MASS) != 0;
+    const bool with_n = emit && !mass && valid;
+    const int64_t c = valid ? cell : 0;
+    const float *nrow = q.n + c * G;
+    const bool quad_rows = (G & 3) == 0;  // rows of T, flags and n start on 4-element boundaries
+    const bool nvec = quad_rows && ((uintptr_t)q.n & 15) == 0;
+    const bool tvec = quad_rows && ((uintptr_t)q.T & 15) == 0;
+    const bool fvec = quad_rows && ((uintptr_t)q.flags & 3) == 0;
+    int mc = 0;
+    float ms = 0.f;  // dust-mass form: m_c = ms 2^mc
+    if (emit && valid) {
+        if (mass) {
+            const float m = __ldg(q.n + c);
+            ms = (m != 0.f && isfinite(m)) ? frexpf(m, &mc) : m;
+        } else {
+            float mx = 0.f;
+            if (nvec) {
+                for (int g = 0; g < G; g += 4) {
+                    const float4 v = __ldg(reinterpret_cast<const float4 *>(nrow + g));
+                    mx = fmaxf(mx, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+                }
+            } else {
+                for (int g = 0; g < G; ++g) mx = fmaxf(mx, __ldg(nrow + g));
+            }
+            if (mx > 0.f && mx < INFINITY) frexpf(mx, &mc);
+        }
+    }
+    float *Trow = q.T + c * G;
+    uint8_t *frow = q.flags ? q.flags + c * G : nullptr;
+    float ah = 0.f, al = 0.f;  // absorbed power n 2^-m_c Pe 2^-Eg, float-float
+    for (int g0 = 0; g0 < G8; g0 += 4) {
+        float v[4];
+        __syncwarp();
+        tmem_ld4(tbase + (uint32_t)g0, v);
+        int gi[4], fl[4];
+        float sv[4], nv[4] = {0.f, 0.f, 0.f, 0.f}, Tv[4];
+        float4 gq[4];
+        const bool full = g0 + 4 <= G;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int g = g0 + i;
+            gi[i] = g < G ? g : 0;
+            sv[i] = g < G ? scale2(v[i], ex) : 0.f;
+            gq[i] = __ldg(reinterpret_cast<const float4 *>(tb.gp) + gi[i]);
+        }
+        if (with_n) {
+            if (nvec && full) {
+                const float4 n4 = __ldg(reinterpret_cast<const float4 *>(nrow + g0));
+                nv[0] = n4.x; nv[1] = n4.y; nv[2] = n4.z; nv[3] = n4.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) nv[i] = g0 + i < G ? __ldg(nrow + g0 + i) : 0.f;
+            }
+        }
+        solve_batch<4>(tb, gi, sv, gq, Tv, fl);
+        if (!valid) continue;
+        if (tvec && full) {
+            *reinterpret_cast<float4 *>(Trow + g0) = make_float4(Tv[0], Tv[1], Tv[2], Tv[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) if (g0 + i < G) Trow[g0 + i] = Tv[i];
+        }
+        if (frow) {
+            if (fvec && full) {
+                *reinterpret_cast<uint32_t *>(frow + g0) =
+                    (uint32_t)fl[0] | ((uint32_t)fl[1] << 8) | ((uint32_t)fl[2] << 16) | ((uint32_t)fl[3] << 24);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) if (g0 + i < G) frow[g0 + i] = (uint8_t)fl[i];
+            }
+        }
+        if (emit) {
+            float invT[4], nn[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                invT[i] = PAD_INV_T;
+                nn[i] = 0.f;
+                if (g0 + i < G) grain_out(tb, g0 + i, Tv[i], fl[i], sv[i], nv[i], mc, mass, rs, invT[i], nn[i], ah, al);
+            }
+            // pair rows are G8 (a multiple of 8) long and 16-byte aligned
+            if (mass) {
+                *reinterpret_cast<float4 *>(reinterpret_cast<float *>(q.prep) + c * G8 + g0) =
+                    make_float4(invT[0], invT[1], invT[2], invT[3]);
+            } else {
+                float4 *dst = reinterpret_cast<float4 *>(q.prep + c * G8 + g0);
+                dst[0] = make_float4(invT[0], nn[0], invT[1], nn[1]);
+                dst[1] = make_float4(invT[2], nn[2], invT[3], nn[3]);
+            }
+        }
+    }
+    if (emit && valid) {
+        CellInfo ci;
+        ci.mc = mc;
+        ci.ah = rs ? ah : 0.f;
+        ci.al = rs ? al : 0.f;
+        ci.ms_bits = __float_as_int(ms);
+        q.cell[c] = ci;
+    }
+}
+
 // TcBatch fields: GsMax sets the ring layout, ns1 / ns2 the ring depths,
 // nacc the accumulators (tmem_cols each), j_off scales J to
 // [2^(j_off-1), 2^j_off) per cell, off_exp is the W image scale folded back
 // in the epilogue.
-template <bool BF16, bool TWO_PASS>
-__global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__ TcBatch p) {
+template <bool BF16, bool TWO_PASS, bool FUSED>
+__device__ __forceinline__ void gemm_body(const TcBatch &p, const SolveList *sl) {
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int B_BYTES = p.GsMax * KC * 2 * 2;  // ring slot of a hi + lo W chunk
@@ -152,10 +276,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
     uint64_t *bars = (uint64_t *)(stB + (size_t)p.ns2 * B_BYTES);
     uint64_t *full1 = bars, *empty1 = full1 + p.ns1;
     uint64_t *a_full = empty1 + p.ns1, *b_full = a_full + p.ns2, *ab_empty = b_full + p.ns2;
-    uint64_t *acc_full = ab_empty + p.ns2, *acc_empty = acc_full + 2;
-    uint64_t *e_full = acc_empty + 2, *e_empty = e_full + 2, *drain = e_empty + 2;
-    int *e_smem = (int *)(drain + 1);                 // [2][BM] per-cell exponents
-    uint32_t *tmem_slot = (uint32_t *)(e_smem + 2 * BM);
+    uint64_t *acc_full = ab_empty + p.ns2, *acc_empty = acc_full + NACC_MAX;
+    uint64_t *e_full = acc_empty + NACC_MAX, *e_empty = e_full + NACC_MAX, *drain = e_empty + NACC_MAX;
+    int *e_smem = (int *)(drain + 1);                 // [NACC_MAX][BM] per-cell exponents
+    uint32_t *tmem_slot = (uint32_t *)(e_smem + NACC_MAX * BM);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -165,7 +289,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
     if (threadIdx.x == 0) {
         for (int s = 0; s < p.ns1; ++s) { mbar_init(&full1[s], 1); mbar_init(&empty1[s], 4); }
         for (int s = 0; s < p.ns2; ++s) { mbar_init(&a_full[s], 4); mbar_init(&b_full[s], 1); mbar_init(&ab_empty[s], 1); }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC_MAX; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 4);
             mbar_init(&e_full[b], 4);
@@ -340,6 +464,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
                 if (++sa == p.ns2) { sa = 0; pha ^= 1; }
             }
         }
+    } else if constexpr (FUSED) {
+        // ------------------------------------------------------------ solver groups
+        // group grp owns accumulator grp and the CTA's tiles it = grp, grp + nacc, ...
+        const int grp = (warp - 7) >> 2;
+        const int quad = warp & 3;        // tensor-memory lane quarter of this warp
+        const int r = quad * 32 + lane;   // tile row
+        int ri = 0;
+        int64_t it = grp;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x + (int64_t)grp * gridDim.x; tile < ntiles && ok;
+             tile += (int64_t)nacc * gridDim.x, it += nacc) {
+            ri = tc_req_of(p, tile, ri);
+            const TcReq &tq = p.req[ri];
+            const uint32_t ub = (uint32_t)((it / nacc) & 1);
+            int e = 0;
+            if (TWO_PASS) {
+                if (!(ok = mbar_wait(&e_full[grp], ub, abort_flag, p.status))) break;
+                e = e_smem[grp * BM + r];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&e_empty[grp]);
+            }
+            if (!(ok = mbar_wait(&acc_full[grp], ub, abort_flag, p.status))) break;
+            tc_fence_after();
+            const int64_t cell = (tile - tq.tile_begin) * BM + r;
+            const uint32_t tbase = tmem + (uint32_t)(grp * p.tmem_cols) + ((uint32_t)(quad * 32) << 16);
+            solve_row(sl->req[ri], cell, cell < tq.C, e - p.j_off - p.off_exp, tbase);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[grp]);
+        }
     } else {
         // ------------------------------------------------------------ epilogue
         const int quad = warp & 3;        // tensor-memory lane quarter of this warp
@@ -390,6 +544,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__
     }
 }
 
+template <bool BF16, bool TWO_PASS>
+__global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tc(const __grid_constant__ TcBatch p) {
+    gemm_body<BF16, TWO_PASS, false>(p, nullptr);
+}
+
+// The same contraction with the temperature solve as its epilogue: S never
+// leaves tensor memory.  Solver group g (warps 7 + 4g .. 10 + 4g) takes every
+// nacc-th tile of the CTA from accumulator g, so nacc tiles are solved at
+// once while the MMAs of the next ones run.
+template <bool BF16, bool TWO_PASS>
+// 80 registers: each SM sub-partition holds 16384, and 23 warps put six on some
+__global__ void __launch_bounds__(NTHREADS_F, 1) k_absorb_solve(const __grid_constant__ TcBatch p,
+                                                                const __grid_constant__ SolveList sl) {
+    gemm_body<BF16, TWO_PASS, true>(p, &sl);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -403,11 +573,22 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
+// kernel parameters are limited to 32764 bytes
+static_assert(sizeof(TcBatch) + sizeof(SolveList) <= 32764, "fused launch parameters too large");
+
 template <bool BF16, bool TWO_PASS>
-int launch_t(const TcBatch &B, size_t smem, int grid, cudaStream_t st) {
-    auto kern = k_gemm_tc<BF16, TWO_PASS>;
-    DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, NTHREADS, smem, st>>>(B);
+int launch_t(const TcBatch &B, size_t smem, int grid, cudaStream_t st, const SolveList *sl) {
+    if (sl) {
+        auto kern = k_absorb_solve<BF16, TWO_PASS>;
+        DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int block = (7 + 4 * B.nacc) * 32;
+        if (block > NTHREADS_F) return set_error(DUST_EINVAL, "fused kernel: %d accumulators", B.nacc);
+        kern<<<grid, block, smem, st>>>(B, *sl);
+    } else {
+        auto kern = k_gemm_tc<BF16, TWO_PASS>;
+        DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, NTHREADS, smem, st>>>(B);
+    }
     DUST_CUDA_TRY(cudaGetLastError());
     return DUST_OK;
 }
@@ -439,7 +620,7 @@ int make_tc_req(const dust_ctx *ctx, int precision, int64_t C, const float *J, i
 }
 
 // Tile offsets, ring depths and tensor-memory layout of a filled batch.
-int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem) {
+int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem, bool fused) {
     const bool bf16 = precision == DUST_PREC_BF16X3;
     int64_t t = 0;
     int gmax = 16;
@@ -453,7 +634,9 @@ int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem) 
     int cols = 32;
     while (cols < gmax) cols <<= 1;
     B.tmem_cols = cols;
-    B.nacc = 2 * cols <= 512 ? 2 : 1;  // double-buffer the accumulator when it fits
+    // double-buffer the accumulator when it fits; the fused kernel takes up
+    // to NACC_MAX, one per group of solver warps
+    B.nacc = std::max(1, std::min(fused ? NACC_MAX : 2, 512 / cols));
     // FP16 keeps J in [2^14, 2^15) and W in (2^13, 2^14] (the W image is
     // built with 2^14 folded in); BF16 has FP32's exponent range and needs none.
     B.j_off = bf16 ? 0 : 15;
@@ -462,8 +645,8 @@ int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem) 
     const size_t budget = (smem_optin ? smem_optin : 232448) - 1024;
     int ns2 = 4, ns1 = 6;
     auto need = [&](int a, int b) {
-        return (size_t)a * STAGE1_BYTES + (size_t)b * (2 * A_BYTES + b_bytes) + (size_t)(2 * a + 3 * b + 9) * 8 +
-               2 * BM * 4 + 16;
+        return (size_t)a * STAGE1_BYTES + (size_t)b * (2 * A_BYTES + b_bytes) +
+               (size_t)(2 * a + 3 * b + 4 * NACC_MAX + 1) * 8 + NACC_MAX * BM * 4 + 16;
     };
     while (need(ns1, ns2) > budget && ns1 > 3) --ns1;
     while (need(ns1, ns2) > budget && ns2 > 2) --ns2;
@@ -475,13 +658,14 @@ int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem) 
     return DUST_OK;
 }
 
-int launch_tc_batch(const TcBatch &B, int precision, size_t smem, int num_sms, cudaStream_t st) {
+int launch_tc_batch(const TcBatch &B, int precision, size_t smem, int num_sms, cudaStream_t st,
+                    const SolveList *sl) {
     if (B.ntiles <= 0) return DUST_OK;
     const int grid = (int)std::min<int64_t>(B.ntiles, num_sms);
     // BF16: the per-cell power-of-two scale is exact and leaves every product
     // unchanged, so the exponent pass runs only for FP16.
-    if (precision == DUST_PREC_BF16X3) return launch_t<true, false>(B, smem, grid, st);
-    return launch_t<false, true>(B, smem, grid, st);
+    if (precision == DUST_PREC_BF16X3) return launch_t<true, false>(B, smem, grid, st, sl);
+    return launch_t<false, true>(B, smem, grid, st, sl);
 }
 
 int launch_gemm_tc(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, float *S,

@@ -97,15 +97,30 @@ int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_
         for (int i = 0; i < 4; ++i) ev[i] = prof_event(ctx);
     const bool prof = ev[0] && ev[1] && ev[2] && ev[3];
     if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[0], st));
-    int rc = precision == DUST_PREC_FP32 ? launch_gemm_simt(ctx, C, J, ld, sv.S, st)
+    const EmitPlan p = plan_emit(ctx, L || resid, mass);
+    EmitBatch B;
+    B.nreq = 1;
+    fill_emit_req(ctx, p, C, sv, n, T, L, ld, resid, flags, B.req[0], mass);
+    const bool fused = ctx->fused && precision != DUST_PREC_FP32;
+    int rc = DUST_OK;
+    if (fused) {
+        // one kernel through the temperatures: S stays in tensor memory
+        TcBatch tb;
+        tb.nreq = 1;
+        tb.status = ctx->tb.status;
+        SolveList sl;
+        sl.req[0] = B.req[0];
+        size_t smem = 0;
+        rc = make_tc_req(ctx, precision, C, J, ld, sv.S, tb.req[0], tb.tm[0]);
+        if (rc == DUST_OK) rc = finish_tc_batch(tb, precision, ctx->smem_optin, &smem, true);
+        if (rc == DUST_OK) rc = launch_tc_batch(tb, precision, smem, ctx->num_sms, st, &sl);
+    } else {
+        rc = precision == DUST_PREC_FP32 ? launch_gemm_simt(ctx, C, J, ld, sv.S, st)
                                          : launch_gemm_tc(ctx, precision, C, J, ld, sv.S, st);
+    }
     if (rc == DUST_OK) {
         if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[1], st));
-        const EmitPlan p = plan_emit(ctx, L || resid, mass);
-        EmitBatch B;
-        B.nreq = 1;
-        fill_emit_req(ctx, p, C, sv, n, T, L, ld, resid, flags, B.req[0], mass);
-        rc = launch_emit_batch(B, p.smem, ctx->num_sms, st, prof ? ev[2] : nullptr);
+        rc = launch_emit_batch(B, p.smem, ctx->num_sms, st, prof ? ev[2] : nullptr, fused);
         if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[3], st));
     }
     for (int i = 0; i < 4; ++i) {
