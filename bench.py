@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-ablation", action="store_true", help="skip the paper's kernel-3 Newton solve")
     ap.add_argument("--no-coupled", action="store_true", help="skip the self-absorbing (coupled) solve")
     ap.add_argument("--no-mass", action="store_true", help="skip the dust-mass form n[c,g] = n_g m_c")
+    ap.add_argument("--no-fused", action="store_true", help="skip the fused absorption + solve kernel")
     ap.add_argument("--large-cells", type=int, default=1 << 20,
                     help="cells of the K=500, G=240 solve (the full case is 2^20; fewer for profiling captures)")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -309,6 +310,23 @@ def run_ours(args):
                     "T_only_ms": round(r["ms_T_only"], 5),
                     "T_only_solves_per_s": C * G * world / (r["ms_T_only"] * 1e-3)}
     line["paths"] = paths
+    if main != "fp32" and not args.no_fused:
+        # the same step with absorption and temperature solve as one kernel
+        cm = ctxs[main]
+        cm.set_fused(True)
+        try:
+            ms_f, out_f, prof_f, _ = timed(cm, k2, 3, main, profile=True)
+            ms_ft, _, prof_ft, _ = timed(cm, k2, 3, main, want_L=False, want_resid=False, profile=True)
+            same = all(torch.equal(out_f[k], res[main]["out"][k]) for k in ("T", "flags", "L"))
+            del out_f
+        finally:
+            cm.set_fused(False)
+        line["paths"][main + "_fused_absorb_solve"] = {
+            "ms_step": round(ms_f, 5), "solves_per_s": aggregate_rate(C * G, world, ms_f * 1e-3),
+            "ms_absorb_solve": round(prof_f[0], 5), "ms_emit": round(prof_f[2], 5),
+            "T_only_ms": round(ms_ft, 5), "T_only_solves_per_s": aggregate_rate(C * G, world, ms_ft * 1e-3),
+            "bitwise_equal_T_flags_L": bool(same),
+            "api": "dust_ctx_set_fused(ctx, 1): k_absorb_solve (tcgen05 GEMM whose epilogue solves T), then k_emit"}
     if not args.no_mass:
         line["paths"][main + "_dust_mass_form"] = mass_form(ctxs[main], wl, J, stream, args, world, dev)
     if not args.no_ablation:

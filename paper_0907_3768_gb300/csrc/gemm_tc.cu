@@ -37,6 +37,7 @@ constexpr int BM = 128;                    // cells per tile (UMMA M)
 constexpr int NTHREADS = 352;              // 11 warps
 constexpr int NACC_MAX = 4;                // accumulators (and solver groups of the fused kernel), at most
 constexpr int NTHREADS_F = (7 + 4 * NACC_MAX) * 32;  // fused kernel: 7 + 4 nacc warps
+constexpr int FUSED_NS1 = 2, FUSED_NS2 = 2;          // fused kernel: ring depths, at most
 constexpr int STAGE1_BYTES = BM * KC * 4;  // FP32 staging tile: 16 KB
 constexpr int A_BYTES = BM * KC * 2;       // one 16-bit A part: 8 KB
 
@@ -581,6 +582,9 @@ int launch_t(const TcBatch &B, size_t smem, int grid, cudaStream_t st, const Sol
     if (sl) {
         auto kern = k_absorb_solve<BF16, TWO_PASS>;
         DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // the smallest shared-memory carveout that holds the rings: the rest is L1
+        const int pct = (int)std::min<size_t>(100, (smem + 2048) * 100 / (228 * 1024) + 1);
+        DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
         const int block = (7 + 4 * B.nacc) * 32;
         if (block > NTHREADS_F) return set_error(DUST_EINVAL, "fused kernel: %d accumulators", B.nacc);
         kern<<<grid, block, smem, st>>>(B, *sl);
@@ -643,7 +647,9 @@ int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem, 
     B.off_exp = bf16 ? 0 : 14;
     const size_t b_bytes = (size_t)gmax * KC * 4;
     const size_t budget = (smem_optin ? smem_optin : 232448) - 1024;
-    int ns2 = 4, ns1 = 6;
+    // the fused kernel's solver warps are latency-bound on table lookups that
+    // hit in L1, so its rings stay shallow and leave L1 most of the SM's memory
+    int ns2 = fused ? FUSED_NS2 : 4, ns1 = fused ? FUSED_NS1 : 6;
     auto need = [&](int a, int b) {
         return (size_t)a * STAGE1_BYTES + (size_t)b * (2 * A_BYTES + b_bytes) +
                (size_t)(2 * a + 3 * b + 4 * NACC_MAX + 1) * 8 + NACC_MAX * BM * 4 + 16;
