@@ -137,6 +137,7 @@ struct TcBatch {
     int nreq;
     int64_t ntiles;
     int GsMax, ns1, ns2, tmem_cols, nacc, off_exp, j_off;
+    int orient;  // 0: cells are the MMA's M (128-cell tiles); 1: cells are its N (256-cell tiles, Gs <= 128)
     int *status;
 };
 
@@ -243,7 +244,10 @@ ScratchView scratch_view(const dust_ctx *ctx, int64_t C, void *base);
 // ring geometry of a batch, and the launch.  All requests of one launch share
 // the precision.
 int make_tc_req(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, float *S,
-                TcReq &r, CUtensorMap &tm);
+                TcReq &r, CUtensorMap &tm, int orient = 0);
+// Orientation of the tensor-core GEMM for a context: grain-major (1) when its
+// grains fit one 128-row MMA operand, cell-major (0) otherwise.
+int tc_orient(const dust_ctx *ctx);
 // fused: the batch feeds the kernel whose epilogue is the temperature solve
 // (up to four accumulators, each with its own group of solver warps), whose
 // requests `sl` holds.

@@ -40,6 +40,16 @@ constexpr int NTHREADS_F = (7 + 4 * NACC_MAX) * 32;  // fused kernel: 7 + 4 nacc
 constexpr int FUSED_NS1 = 2, FUSED_NS2 = 2;          // fused kernel: ring depths, at most
 constexpr int STAGE1_BYTES = BM * KC * 4;  // FP32 staging tile: 16 KB
 constexpr int A_BYTES = BM * KC * 2;       // one 16-bit A part: 8 KB
+// grain-major orientation (Gs <= 128): grains are the MMA's M, cells its N
+constexpr int BN_T = 256;                     // cells per tile (UMMA N)
+constexpr int MW = 128;                       // grain rows of the W operand (UMMA M; zero past Gs)
+constexpr int STAGE1T_BYTES = BN_T * KC * 4;  // FP32 staging tile: 32 KB
+constexpr int WA_PART = MW * KC * 2;          // one 16-bit W part: 8 KB
+constexpr int JB_PART = BN_T * KC * 2;        // one 16-bit J part: 16 KB
+constexpr int TN_NS1 = 4, TN_NS2 = 2;         // its ring depths, at most
+constexpr int NCV_T = 8;                      // its converter warps
+constexpr int RPT = BN_T / (32 * NCV_T);      // cell rows per converter thread
+constexpr int NTHREADS_T = (3 + NCV_T + 4) * 32;
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ void fence_proxy_async() {
@@ -98,6 +108,22 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 lanes x 32 bits, 32 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Shared-memory matrix descriptor, K-major, no swizzle: core matrices of
@@ -561,6 +587,279 @@ __global__ void __launch_bounds__(NTHREADS_F, 1) k_absorb_solve(const __grid_con
     gemm_body<BF16, TWO_PASS, true>(p, &sl);
 }
 
+// Grain-major form of the same contraction for Gs <= 128: W (grains x K,
+// zero rows up to 128) is the MMA's A operand and a 256-cell tile of J its B
+// operand, so one MMA covers twice the cells of the cell-major kernel at
+// about the same issue cost; the accumulator is 128 grain lanes x 256 cell
+// columns.  Roles as in k_gemm_tc: warp 0 J producer (TMA, 256-row boxes),
+// warp 1 tensor memory + MMA issuer, warp 2 W producer (two bulk copies per
+// chunk: hi and lo parts into their 128-row slots), then NCV_T converter
+// warps (256 / (32 NCV_T) cell rows per thread) and four epilogue warps
+// (thread = grain, 32 cell columns per tensor-memory load; each store of a
+// warp is 32 consecutive grains of one cell row of S).
+template <bool BF16, bool TWO_PASS>
+__global__ void __launch_bounds__(NTHREADS_T, 1) k_gemm_tc_t(const __grid_constant__ TcBatch p) {
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+    unsigned char *st1 = smem;                                        // [ns1] FP32 J tiles
+    unsigned char *stW = st1 + (size_t)p.ns1 * STAGE1T_BYTES;         // [ns2] W hi | lo
+    unsigned char *stJ = stW + (size_t)p.ns2 * 2 * WA_PART;           // [ns2] J hi | lo
+    uint64_t *bars = (uint64_t *)(stJ + (size_t)p.ns2 * 2 * JB_PART);
+    uint64_t *full1 = bars, *empty1 = full1 + p.ns1;
+    uint64_t *w_full = empty1 + p.ns1, *j_full = w_full + p.ns2, *ab_empty = j_full + p.ns2;
+    uint64_t *acc_full = ab_empty + p.ns2, *acc_empty = acc_full + 2;
+    uint64_t *e_full = acc_empty + 2, *e_empty = e_full + 2, *drain = e_empty + 2;
+    int *e_smem = (int *)(drain + 1);                 // [2][BN_T] per-cell exponents
+    uint32_t *tmem_slot = (uint32_t *)(e_smem + 2 * BN_T);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = p.ntiles;
+
+    // W rows past Gs stay zero: the bulk copies write only the first Gs rows of each part
+    for (int i = threadIdx.x; i < p.ns2 * 2 * WA_PART / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(stW)[i] = make_uint4(0u, 0u, 0u, 0u);
+    fence_proxy_async();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < p.ns1; ++s) { mbar_init(&full1[s], 1); mbar_init(&empty1[s], NCV_T); }
+        for (int s = 0; s < p.ns2; ++s) { mbar_init(&w_full[s], 1); mbar_init(&j_full[s], NCV_T); mbar_init(&ab_empty[s], 1); }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+            mbar_init(&e_full[b], NCV_T);
+            mbar_init(&e_empty[b], 4);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(2 * BN_T) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ J producer
+        if (lane == 0) {
+            int s1 = 0, ri = 0;
+            uint32_t ph1 = 0;
+            int64_t n1 = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                ri = tc_req_of(p, tile, ri);
+                const TcReq &q = p.req[ri];
+                const CUtensorMap *tm = &p.tm[ri];
+                const int row0 = (int)((tile - q.tile_begin) * BN_T);
+                for (int pass = TWO_PASS ? 0 : 1; pass < 2 && ok; ++pass) {
+                    for (int kc = 0; kc < q.nkc && ok; ++kc) {
+                        if (!(ok = mbar_wait(&empty1[s1], ph1 ^ 1, abort_flag, p.status))) break;
+                        mbar_expect_tx(&full1[s1], STAGE1T_BYTES);
+                        tma_load_2d(st1 + (size_t)s1 * STAGE1T_BYTES, tm, kc * KC, row0, &full1[s1]);
+                        ++n1;
+                        if (++s1 == p.ns1) { s1 = 0; ph1 ^= 1; }
+                    }
+                }
+            }
+            if (!ok) drain_ring(full1, p.ns1, n1, p.status);
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------------------ W producer
+        if (lane == 0) {
+            int sa = 0, ri = 0;
+            uint32_t pha = 0;
+            int64_t n2 = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                ri = tc_req_of(p, tile, ri);
+                const TcReq &q = p.req[ri];
+                const uint32_t part = (uint32_t)q.Gs * KC * 2;  // one part of this request's chunk
+                for (int kc = 0; kc < q.nkc && ok; ++kc) {
+                    if (!(ok = mbar_wait(&ab_empty[sa], pha ^ 1, abort_flag, p.status))) break;
+                    mbar_expect_tx(&w_full[sa], 2 * part);
+                    const unsigned char *src = reinterpret_cast<const unsigned char *>(q.Wimg) + (size_t)kc * 2 * part;
+                    unsigned char *dst = stW + (size_t)sa * 2 * WA_PART;
+                    bulk_load(dst, src, part, &w_full[sa]);
+                    bulk_load(dst + WA_PART, src + part, part, &w_full[sa]);
+                    ++n2;
+                    if (++sa == p.ns2) { sa = 0; pha ^= 1; }
+                }
+            }
+            if (!ok) drain_ring(w_full, p.ns2, n2, p.status);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int sa = 0, ri = 0;
+            uint32_t pha = 0;
+            int64_t it = 0;
+            bool ok = true;
+            const uint32_t idesc = instr_desc(BF16, MW, BN_T);
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+                ri = tc_req_of(p, tile, ri);
+                const int nkc = p.req[ri].nkc;
+                const int b = (int)(it & 1);
+                const uint32_t ub = (uint32_t)((it >> 1) & 1);
+                const uint32_t d_tmem = tmem + (uint32_t)(b * BN_T);
+                if (!(ok = mbar_wait(&acc_empty[b], ub ^ 1, abort_flag, p.status))) break;
+                tc_fence_after();
+                for (int kc = 0; kc < nkc && ok; ++kc) {
+                    if (!(ok = mbar_wait(&w_full[sa], pha, abort_flag, p.status))) break;
+                    if (!(ok = mbar_wait(&j_full[sa], pha, abort_flag, p.status))) break;
+                    tc_fence_after();
+                    const uint32_t w_base = smem_u32(stW + (size_t)sa * 2 * WA_PART);
+                    const uint32_t j_base = smem_u32(stJ + (size_t)sa * 2 * JB_PART);
+#pragma unroll
+                    for (int ks = 0; ks < KC / 16; ++ks) {
+#pragma unroll
+                        for (int part = 0; part < 3; ++part) {
+                            // W hi . J hi, W hi . J lo, W lo . J hi
+                            const uint32_t woff = (part == 2 ? WA_PART : 0) + ks * 256;
+                            const uint32_t joff = (part == 1 ? JB_PART : 0) + ks * 256;
+                            const uint32_t acc = (kc | ks | part) ? 1u : 0u;
+                            tc_mma(d_tmem, smem_desc(w_base + woff, 128, 512), smem_desc(j_base + joff, 128, 512),
+                                   idesc, acc);
+                        }
+                    }
+                    tc_commit(&ab_empty[sa]);
+                    if (++sa == p.ns2) { sa = 0; pha ^= 1; }
+                }
+                if (ok) tc_commit(&acc_full[b]);
+            }
+            // drain every MMA still in flight before tensor memory is freed
+            tc_commit(drain);
+            mbar_drain(drain, 0, p.status);
+        }
+    } else if (warp < 3 + NCV_T) {
+        // ------------------------------------------------------------ converters
+        const int r0 = (warp - 3) * 32 + lane;  // cell rows r0 + h NCV_T 32 of the tile, h < RPT
+        int s1 = 0, sa = 0, ri = 0;
+        uint32_t ph1 = 0, pha = 0;
+        int64_t it = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+            ri = tc_req_of(p, tile, ri);
+            const TcReq &q = p.req[ri];
+            int e[RPT] = {};
+            if (TWO_PASS) {
+                float mx[RPT] = {};
+                for (int kc = 0; kc < q.nkc; ++kc) {
+                    if (!(ok = mbar_wait(&full1[s1], ph1, abort_flag, p.status))) break;
+#pragma unroll
+                    for (int h = 0; h < RPT; ++h) {
+                        const int r = r0 + h * NCV_T * 32;
+                        const unsigned char *src = st1 + (size_t)s1 * STAGE1T_BYTES + r * 128;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float4 v = *reinterpret_cast<const float4 *>(src + ((j ^ (r & 7)) << 4));
+                            mx[h] = fmaxf(mx[h], fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty1[s1]);
+                    if (++s1 == p.ns1) { s1 = 0; ph1 ^= 1; }
+                }
+                if (!ok) break;
+#pragma unroll
+                for (int h = 0; h < RPT; ++h) {
+                    if (mx[h] > 0.f && mx[h] < INFINITY) frexpf(mx[h], &e[h]);
+                    e[h] = min(max(e[h], p.j_off - 126), p.j_off + 126);  // keep 2^(j_off - e) a normal float
+                }
+                // hand the exponents to the epilogue
+                const int b = (int)(it & 1);
+                const uint32_t ub = (uint32_t)((it >> 1) & 1);
+                if (!(ok = mbar_wait(&e_empty[b], ub ^ 1, abort_flag, p.status))) break;
+#pragma unroll
+                for (int h = 0; h < RPT; ++h) e_smem[b * BN_T + r0 + h * NCV_T * 32] = e[h];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&e_full[b]);
+            }
+            float scale[RPT];
+#pragma unroll
+            for (int h = 0; h < RPT; ++h) scale[h] = __int_as_float((127 - e[h] + p.j_off) << 23);  // 2^(j_off - e)
+            for (int kc = 0; kc < q.nkc; ++kc) {
+                if (!(ok = mbar_wait(&full1[s1], ph1, abort_flag, p.status))) break;
+                if (!(ok = mbar_wait(&ab_empty[sa], pha ^ 1, abort_flag, p.status))) break;
+#pragma unroll
+                for (int h = 0; h < RPT; ++h) {
+                    const int r = r0 + h * NCV_T * 32;
+                    const unsigned char *src = st1 + (size_t)s1 * STAGE1T_BYTES + r * 128;
+                    unsigned char *dhi = stJ + (size_t)sa * 2 * JB_PART + (r >> 3) * 512 + (r & 7) * 16;
+                    unsigned char *dlo = dhi + JB_PART;
+#pragma unroll
+                    for (int cm = 0; cm < 4; ++cm) {  // 8 wavelengths = one core-matrix row
+                        float4 v0 = *reinterpret_cast<const float4 *>(src + (((2 * cm) ^ (r & 7)) << 4));
+                        float4 v1 = *reinterpret_cast<const float4 *>(src + (((2 * cm + 1) ^ (r & 7)) << 4));
+                        uint4 hv, lv;
+                        hv.x = pack_split(v0.x * scale[h], v0.y * scale[h], BF16, lv.x);
+                        hv.y = pack_split(v0.z * scale[h], v0.w * scale[h], BF16, lv.y);
+                        hv.z = pack_split(v1.x * scale[h], v1.y * scale[h], BF16, lv.z);
+                        hv.w = pack_split(v1.z * scale[h], v1.w * scale[h], BF16, lv.w);
+                        *reinterpret_cast<uint4 *>(dhi + cm * 128) = hv;
+                        *reinterpret_cast<uint4 *>(dlo + cm * 128) = lv;
+                    }
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) { mbar_arrive(&j_full[sa]); mbar_arrive(&empty1[s1]); }
+                if (++s1 == p.ns1) { s1 = 0; ph1 ^= 1; }
+                if (++sa == p.ns2) { sa = 0; pha ^= 1; }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quad = warp & 3;        // tensor-memory lane quarter of this warp
+        const int g = quad * 32 + lane;   // grain row of the accumulator
+        int ri = 0;
+        int64_t it = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+            ri = tc_req_of(p, tile, ri);
+            const TcReq &q = p.req[ri];
+            const int b = (int)(it & 1);
+            const uint32_t ub = (uint32_t)((it >> 1) & 1);
+            if (TWO_PASS && !(ok = mbar_wait(&e_full[b], ub, abort_flag, p.status))) break;
+            if (!(ok = mbar_wait(&acc_full[b], ub, abort_flag, p.status))) break;
+            tc_fence_after();
+            const int Gs = q.Gs;
+            const int64_t cell0 = (tile - q.tile_begin) * BN_T;
+            const int nc = (int)min((int64_t)BN_T, q.C - cell0);  // cells of this tile
+            const uint32_t tbase = tmem + (uint32_t)(b * BN_T) + ((uint32_t)(quad * 32) << 16);
+            if (quad * 32 < Gs) {  // warp-uniform: quarters past the grains hold zeros only
+                float *col = q.S + cell0 * Gs + g;  // S[cell0][g]
+                const bool gok = g < Gs;
+                const int ex0 = -p.j_off - p.off_exp;
+                for (int c0 = 0; c0 < BN_T; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tbase + (uint32_t)c0, v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int ex = (TWO_PASS ? e_smem[b * BN_T + c0 + i] : 0) + ex0;
+                        if (gok && c0 + i < nc) col[(c0 + i) * Gs] = scale2(v[i], ex);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&acc_empty[b]);
+                if (TWO_PASS) mbar_arrive(&e_empty[b]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN_T) : "memory");
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -579,7 +878,11 @@ static_assert(sizeof(TcBatch) + sizeof(SolveList) <= 32764, "fused launch parame
 
 template <bool BF16, bool TWO_PASS>
 int launch_t(const TcBatch &B, size_t smem, int grid, cudaStream_t st, const SolveList *sl) {
-    if (sl) {
+    if (B.orient == 1) {
+        auto kern = k_gemm_tc_t<BF16, TWO_PASS>;
+        DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, NTHREADS_T, smem, st>>>(B);
+    } else if (sl) {
         auto kern = k_absorb_solve<BF16, TWO_PASS>;
         DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         // the smallest shared-memory carveout that holds the rings: the rest is L1
@@ -599,16 +902,19 @@ int launch_t(const TcBatch &B, size_t smem, int grid, cudaStream_t st, const Sol
 
 }  // namespace
 
+int tc_orient(const dust_ctx *ctx) { return ctx->tb.Gs <= MW ? 1 : 0; }
+
 int make_tc_req(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, float *S, TcReq &r,
-                CUtensorMap &tm) {
+                CUtensorMap &tm, int orient) {
     const bool bf16 = precision == DUST_PREC_BF16X3;
     const int K = ctx->K;
-    if (C > 0x7fffffffLL - BM) return set_error(DUST_EINVAL, "too many cells for one tensor-core launch");
+    if (C > 0x7fffffffLL - BN_T) return set_error(DUST_EINVAL, "too many cells for one tensor-core launch");
     auto encode = get_encode();
     if (!encode) return set_error(DUST_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)C};
     cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)BM};
+    if (orient == 1 && ctx->tb.Gs > MW) return set_error(DUST_EINVAL, "grain-major GEMM needs Gs <= %d", MW);
+    cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)(orient == 1 ? BN_T : BM)};
     cuuint32_t estr[2] = {1, 1};
     CUresult cr = encode(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)J, dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -626,15 +932,36 @@ int make_tc_req(const dust_ctx *ctx, int precision, int64_t C, const float *J, i
 // Tile offsets, ring depths and tensor-memory layout of a filled batch.
 int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem, bool fused) {
     const bool bf16 = precision == DUST_PREC_BF16X3;
+    const int bm = B.orient == 1 ? BN_T : BM;
     int64_t t = 0;
     int gmax = 16;
     for (int i = 0; i < B.nreq; ++i) {
         B.req[i].tile_begin = t;
-        t += (B.req[i].C + BM - 1) / BM;
+        t += (B.req[i].C + bm - 1) / bm;
         gmax = std::max(gmax, B.req[i].Gs);
     }
     B.ntiles = t;
     B.GsMax = gmax;
+    const size_t budget = (smem_optin ? smem_optin : 232448) - 1024;
+    if (B.orient == 1) {
+        if (fused || gmax > MW) return set_error(DUST_EINVAL, "grain-major GEMM: Gs <= %d and not fused", MW);
+        B.tmem_cols = BN_T;
+        B.nacc = 2;
+        B.j_off = bf16 ? 0 : 15;
+        B.off_exp = bf16 ? 0 : 14;
+        auto need_t = [&](int a, int b) {
+            return (size_t)a * STAGE1T_BYTES + (size_t)b * 2 * (WA_PART + JB_PART) + (size_t)(2 * a + 3 * b + 9) * 8 +
+                   2 * BN_T * 4 + 16;
+        };
+        int ns1 = TN_NS1, ns2 = TN_NS2;
+        while (need_t(ns1, ns2) > budget && ns1 > 2) --ns1;
+        while (need_t(ns1, ns2) > budget && ns2 > 2) --ns2;
+        if (need_t(ns1, ns2) > budget) return set_error(DUST_EINVAL, "shared memory too small for the grain-major GEMM");
+        B.ns1 = ns1;
+        B.ns2 = ns2;
+        *smem = need_t(ns1, ns2) + 1024;
+        return DUST_OK;
+    }
     int cols = 32;
     while (cols < gmax) cols <<= 1;
     B.tmem_cols = cols;
@@ -646,7 +973,6 @@ int finish_tc_batch(TcBatch &B, int precision, size_t smem_optin, size_t *smem, 
     B.j_off = bf16 ? 0 : 15;
     B.off_exp = bf16 ? 0 : 14;
     const size_t b_bytes = (size_t)gmax * KC * 4;
-    const size_t budget = (smem_optin ? smem_optin : 232448) - 1024;
     // the fused kernel's solver warps are latency-bound on table lookups that
     // hit in L1, so its rings stay shallow and leave L1 most of the SM's memory
     int ns2 = fused ? FUSED_NS2 : 4, ns1 = fused ? FUSED_NS1 : 6;
@@ -680,7 +1006,8 @@ int launch_gemm_tc(const dust_ctx *ctx, int precision, int64_t C, const float *J
     TcBatch B;
     B.nreq = 1;
     B.status = ctx->tb.status;
-    int rc = make_tc_req(ctx, precision, C, J, ld, S, B.req[0], B.tm[0]);
+    B.orient = tc_orient(ctx);
+    int rc = make_tc_req(ctx, precision, C, J, ld, S, B.req[0], B.tm[0], B.orient);
     if (rc != DUST_OK) return rc;
     size_t smem = 0;
     if ((rc = finish_tc_batch(B, precision, ctx->smem_optin, &smem)) != DUST_OK) return rc;

@@ -246,24 +246,29 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
                 s->launches++;
             }
         } else {
-            TcBatch B;
-            B.nreq = 0;
-            B.status = nullptr;
-            for (const Part &p : parts) {
-                if (p.r->precision != prec) continue;
-                ServeReq *r = p.r;
-                if (!B.status) B.status = r->ctx->tb.status;
-                int rc = make_tc_req(r->ctx, prec, p.cn, r->J + p.c0 * r->ld, r->ld, part_view(p).S, B.req[B.nreq],
-                                     B.tm[B.nreq]);
-                if (rc != DUST_OK) return rc;
-                B.nreq++;
-            }
-            if (B.nreq) {
-                size_t smem = 0;
-                int rc = finish_tc_batch(B, prec, s->smem_optin, &smem);
-                if (rc == DUST_OK) rc = launch_tc_batch(B, prec, smem, s->num_sms, s->st);
-                if (rc != DUST_OK) return rc;
-                s->launches++;
+            // one launch per orientation, each request in the one dust_solve uses for
+            // its context, so that results are bitwise those of a solve alone
+            for (int orient = 0; orient < 2; ++orient) {
+                TcBatch B;
+                B.nreq = 0;
+                B.status = nullptr;
+                B.orient = orient;
+                for (const Part &p : parts) {
+                    if (p.r->precision != prec || tc_orient(p.r->ctx) != orient) continue;
+                    ServeReq *r = p.r;
+                    if (!B.status) B.status = r->ctx->tb.status;
+                    int rc = make_tc_req(r->ctx, prec, p.cn, r->J + p.c0 * r->ld, r->ld, part_view(p).S,
+                                         B.req[B.nreq], B.tm[B.nreq], orient);
+                    if (rc != DUST_OK) return rc;
+                    B.nreq++;
+                }
+                if (B.nreq) {
+                    size_t smem = 0;
+                    int rc = finish_tc_batch(B, prec, s->smem_optin, &smem);
+                    if (rc == DUST_OK) rc = launch_tc_batch(B, prec, smem, s->num_sms, s->st);
+                    if (rc != DUST_OK) return rc;
+                    s->launches++;
+                }
             }
         }
     }

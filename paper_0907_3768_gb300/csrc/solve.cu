@@ -108,6 +108,7 @@ int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_
         TcBatch tb;
         tb.nreq = 1;
         tb.status = ctx->tb.status;
+        tb.orient = 0;
         SolveList sl;
         sl.req[0] = B.req[0];
         size_t smem = 0;
