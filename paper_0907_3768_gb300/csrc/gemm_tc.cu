@@ -21,6 +21,13 @@
 //               overlapped with the next tile's MMAs in the other accumulator.
 // Every mbarrier wait is bounded; on expiry the kernel records DUST_ETIMEOUT
 // in the status word and winds down.
+//
+// k_gemm_tc_t is the grain-major form used when Gs <= 128: W is the MMA's A
+// operand (M = 128 grain rows) and 256 cells of J its B operand (N = 256), so
+// each MMA covers twice the cells; the issue cost of an MMA, not its
+// tensor-pipe time, is what limits the cell-major form at small G.
+// k_absorb_solve is the cell-major kernel with the temperature solve as its
+// epilogue (S stays in tensor memory).
 #include "dust_internal.cuh"
 #include "mbar.cuh"
 #include "solve_core.cuh"
