@@ -151,6 +151,22 @@ def test_size_limits(prec, K, sizes, species, lam_um):
     _compare(out, ref, prec, wl)
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("sizes,C", [(64, 255), (64, 513), (65, 257)])
+def test_gemm_orientation_boundary(prec, sizes, C):
+    """Two species x 64 sizes = 128 grains: the grain-major GEMM with every one of
+    its 128 MMA rows a real grain; x 65 = 130 grains: the cell-major GEMM.  Cell
+    counts just off the 256-cell tile of the former."""
+    cfg = dict(synth.CONFIGS[0])
+    cfg.update(K=100, n_sizes=sizes, species=("silicate", "graphite"), n_cells=C, seed=123)
+    wl = synth.make_workload(cfg)
+    assert wl.G == 2 * sizes
+    ref = oracle.run_workload(wl)
+    with _ctx(wl, prec) as ctx:
+        out = _run(ctx, wl.J, wl.n, precision=prec)
+    _compare(out, ref, prec, wl)
+
+
 def test_edge_inputs_flags():
     wl = synth.make_workload(0, cells=np.arange(8))
     J = wl.J.copy()

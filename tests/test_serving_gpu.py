@@ -32,10 +32,12 @@ def _padded(J):
 
 
 def _mix():
-    """Requests over three grids / grain sets and all three precisions."""
+    """Requests over four grids / three grain sets and all three precisions."""
     from paper_0907_3768_gb300 import Context
 
-    shapes = [(100, 48, "bf16x3"), (350, 96, "fp32"), (500, 240, "fp16x3"), (200, 96, "bf16x3")]
+    # both GEMM orientations within each tensor-core precision: G <= 128 grain-major, G = 240 cell-major
+    shapes = [(100, 48, "bf16x3"), (350, 96, "fp32"), (500, 240, "fp16x3"), (200, 96, "bf16x3"),
+              (100, 240, "bf16x3"), (200, 48, "fp16x3")]
     ctxs, reqs = {}, []
     rng = np.random.default_rng(11)
     for i in range(10):
