@@ -30,10 +30,10 @@ METRIC = "grain-T solves/s & SED cells/s, mixed vs FP32 at stated err, 1 GB300; 
 UNIT = "grain-T solves/s"
 CONFIG_ID = 1
 WORKLOAD = "2^18 cells x 200 wavelengths (0.09-1000 um) x 96 grains (3 species x 32 sizes), P_g(T) table 4096 pts"
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_emit<false> launch on this
-# workload, from one `ncu --set full` capture of that launch; to be retaken
-# whenever the emission kernel changes
-EMIT_TRAFFIC_BYTES = 205.649408e6 + 210.221312e6
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the step's dominant
+# kernel on this workload, from one `ncu --set full` capture of that launch
+# (None until captured); to be retaken whenever that kernel changes
+DOMINANT_TRAFFIC_BYTES = None
 
 
 def parse():
@@ -195,6 +195,7 @@ def run_ours(args):
         for _ in range(warmup):
             ctx.solve(J, n, precision=prec, out=out, stream=stream)
         torch.cuda.synchronize()
+        nl0 = _lib.dust_ctx_launch_count(ctx.handle)
         _lib.dust_ctx_profile_read(ctx.handle)
         if profile:
             _lib.dust_ctx_profile(ctx.handle, True)
@@ -215,6 +216,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
         ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
+        launches[id(ctx), want_L, want_resid] = (_lib.dust_ctx_launch_count(ctx.handle) - nl0) / steps
         prof = None
         if profile:
             a, b, c, cnt = _lib.dust_ctx_profile_read(ctx.handle)
@@ -224,7 +226,9 @@ def run_ours(args):
         return ms, out, prof, clk
 
     res = {}
+    launches = {}
     ms_main, out_main, prof_main, clk = timed(ctxs[main], args.steps, args.warmup, main, profile=True, clocks=True)
+    launches_main = launches[id(ctxs[main]), True, True]
     res[main] = dict(ms_step=ms_main, out=out_main, prof=prof_main)
     others = [p for p in ctxs if p != main]
     k2 = max(3, min(args.steps, 60))
@@ -269,21 +273,41 @@ def run_ours(args):
         e2e = {"value": aggregate_rate(C * G, world, te), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": round(te * 1e3, 4), "api": "dust_solve_host (pinned host buffers)"}
 
-    # roofline of the dominant kernel (the emission kernel: one ex2 per term)
+    # roofline of the dominant kernel: the warp-specialized solve + emission where
+    # it applies (its solve is timed with the emission), else the emission kernel;
+    # either way one MUFU ex2 per Planck term
     ex2_rate, fma_rate = _lib.dust_diag_throughput(local)
     ms_emit = res[main]["prof"][2]
+    solve_in_emit = res[main]["prof"][1] < 0.02 * ms_emit
     terms = C * G * K
     achieved = terms / (ms_emit * 1e-3) / 1e9
     peak = ex2_rate / 1e9
-    roofline = {"bound": "alu", "kernel": "k_emit (emission + energy-balance residual, MUFU ex2)",
+    roofline = {"bound": "alu",
+                "kernel": ("k_solve_emit (temperature solve + emission, warp-specialized) + k_resid" if solve_in_emit
+                           else "k_emit (emission) + k_resid"),
                 "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "G Planck terms/s",
                 "frac": round(achieved / peak, 4),
                 "peak_source": "measured MUFU ex2.approx issue rate (dust_diag_throughput), 1 ex2 per term",
-                "traffic": EMIT_TRAFFIC_BYTES if (C, K, G) == (1 << 18, 200, 96) and world == 1 else None,
+                "traffic": DOMINANT_TRAFFIC_BYTES if (C, K, G) == (1 << 18, 200, 96) and world == 1 else None,
                 "traffic_unit": "bytes per launch (ncu DRAM read + write)",
-                "algorithmic_bytes": C * (8 * ((G + 7) // 8 * 8) + 16 + 4 * K + 8 * ((K + 7) // 8)),
+                "algorithmic_bytes": C * (4 * ((G + 15) // 16 * 16) + 4 * G + 4 * G + G + 16 + 4 * K + 8 * ((K + 7) // 8))
+                if solve_in_emit else C * (8 * ((G + 7) // 8 * 8) + 16 + 4 * K + 8 * ((K + 7) // 8)),
                 "ms_per_launch": round(ms_emit, 4),
                 "fma_pipe_peak_Gflop_lanes": round(fma_rate / 1e9, 1)}
+    if solve_in_emit:
+        # the same step with the solve and the emission as two kernels
+        cm = ctxs[main]
+        cm.set_fused_emit(False)
+        try:
+            ms_2, out_2, prof_2, _ = timed(cm, k2, 3, main, profile=True)
+            same2 = all(torch.equal(out_2[k], res[main]["out"][k]) for k in ("T", "flags", "L", "resid"))
+            del out_2
+        finally:
+            cm.set_fused_emit(True)
+        roofline["emission_kernel_alone"] = {
+            "kernel": "k_emit + k_resid (solve in its own kernel)", "ms_per_launch": round(prof_2[2], 4),
+            "achieved": round(terms / (prof_2[2] * 1e-3) / 1e9, 2), "frac": round(terms / (prof_2[2] * 1e-3) / ex2_rate, 4),
+            "step_ms": round(ms_2, 5), "ms_solve": round(prof_2[1], 5), "bitwise_equal": bool(same2)}
 
     line = {
         "metric": METRIC, "value": aggregate_rate(C * G, world, ms_main * 1e-3), "unit": UNIT, "n_gpus": world,
@@ -294,7 +318,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (J 210 MB, L 210 MB per step)",
                    "parallelism": f"dp{world} (independent cell batches)"},
         "sed_cells_per_s": C * world / (ms_main * 1e-3),
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": int(round(launches_main * args.steps)),
         "roofline": roofline,
         "clocks": clk,
         "e2e": e2e,
@@ -307,6 +331,7 @@ def run_ours(args):
                     "sed_cells_per_s": C * world / (r["ms_step"] * 1e-3),
                     "ms_absorb": round(r["prof"][0], 5), "ms_solve": round(r["prof"][1], 5),
                     "ms_emit": round(r["prof"][2], 5),
+                    "solve_inside_emission_kernel": bool(r["prof"][1] < 0.02 * r["prof"][2]),
                     "T_only_ms": round(r["ms_T_only"], 5),
                     "T_only_solves_per_s": C * G * world / (r["ms_T_only"] * 1e-3)}
     line["paths"] = paths

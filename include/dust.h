@@ -115,6 +115,23 @@ int dust_ctx_set_precision(dust_ctx *ctx, int precision);
  * DUST_EINVAL for a NULL context. */
 int dust_ctx_set_fused(dust_ctx *ctx, int fused);
 
+/* Kernel layout of the temperature solve and the emission (Eqs. 7-10) in
+ * later dust_solve calls: fused != 0 runs them as one warp-specialized kernel
+ * where it applies (L or resid wanted, the general form n[c,g], and the
+ * emission weights fitting in shared memory beside two tiles of (1/T, n)
+ * pairs; other calls keep the two kernels).  Its solver warps solve the next
+ * tile of cells into shared memory while its emission warps emit the current
+ * one.  T, flags, L and resid are bitwise the same either way.  On by
+ * default; ignored when dust_ctx_set_fused is on.  Takes the context's lock; returns DUST_OK, or
+ * DUST_EINVAL for a NULL context. */
+int dust_ctx_set_fused_emit(dust_ctx *ctx, int fused);
+
+/* Number of kernels that this context's solves (dust_solve and the entry
+ * points built on it) have launched since it was created; the server's own
+ * launches are counted by dust_server_stats.  Takes the context's lock;
+ * DUST_EINVAL for a NULL argument. */
+int dust_ctx_launch_count(dust_ctx *ctx, uint64_t *count);
+
 /* Shape and capability query: any output pointer may be NULL.  device_bytes
  * is the device memory the context holds now: its tables and W images, the
  * grown scratch, the host-buffer staging, and the tables or buffers of the

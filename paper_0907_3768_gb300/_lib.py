@@ -33,6 +33,8 @@ _SIGS = {
     "dust_ctx_destroy": (None, [_p]),
     "dust_ctx_set_precision": (_i, [_p, _i]),
     "dust_ctx_set_fused": (_i, [_p, _i]),
+    "dust_ctx_set_fused_emit": (_i, [_p, _i]),
+    "dust_ctx_launch_count": (_i, [_p, ctypes.POINTER(ctypes.c_uint64)]),
     "dust_ctx_info": (_i, [_p, _p, _p, _p, _p, _p, _p]),
     "dust_solve": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
     "dust_solve_prec": (_i, [_p, _i, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
@@ -114,6 +116,16 @@ def dust_ctx_set_precision(ctx, precision):
 
 def dust_ctx_set_fused(ctx, fused):
     return check(lib().dust_ctx_set_fused(ctx, 1 if fused else 0))
+
+
+def dust_ctx_set_fused_emit(ctx, fused):
+    return check(lib().dust_ctx_set_fused_emit(ctx, 1 if fused else 0))
+
+
+def dust_ctx_launch_count(ctx):
+    n = ctypes.c_uint64()
+    check(lib().dust_ctx_launch_count(ctx, ctypes.byref(n)))
+    return n.value
 
 
 def dust_ctx_info(ctx):

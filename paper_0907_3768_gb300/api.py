@@ -83,6 +83,10 @@ class Context:
         """Absorption and temperature solve as one kernel (tensor-core precisions)."""
         _lib.dust_ctx_set_fused(self.handle, fused)
 
+    def set_fused_emit(self, fused=True):
+        """Temperature solve and emission as one warp-specialized kernel, where it applies."""
+        _lib.dust_ctx_set_fused_emit(self.handle, fused)
+
     def check(self):
         """Device status word since the last check (0 = DUST_OK)."""
         return _lib.dust_ctx_check(self.handle)

@@ -524,6 +524,20 @@ int dust_ctx_set_fused(dust_ctx *ctx, int fused) {
     return DUST_OK;
 }
 
+int dust_ctx_set_fused_emit(dust_ctx *ctx, int fused) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->fused_emit = fused != 0;
+    return DUST_OK;
+}
+
+int dust_ctx_launch_count(dust_ctx *ctx, uint64_t *count) {
+    if (!ctx || !count) return set_error(DUST_EINVAL, "ctx and count must be non-NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *count = ctx->launches;
+    return DUST_OK;
+}
+
 int dust_ctx_info(const dust_ctx *ctx, int *K, int *G, int *n_table, int *precision, int *device,
                   size_t *device_bytes) {
     if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");

@@ -164,6 +164,11 @@ struct dust_ctx {
     // tensor-core precisions: absorption and temperature solve as one kernel
     // (dust_ctx_set_fused)
     bool fused = false;
+    // solve and emission as one warp-specialized kernel where it applies
+    // (dust_ctx_set_fused_emit)
+    bool fused_emit = true;
+    // kernels launched by this context's solves (dust_ctx_launch_count)
+    uint64_t launches = 0;
     int K = 0, G = 0, NT = 0, NI = 0;
     int Kw = 0;               // row length of the FP32 / 16-bit W copies (K rounded to KC)
     double Tmin = 0, Tmax = 0;
@@ -265,7 +270,14 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
 // With solved = true the temperatures, pairs and cell records are already
 // there (fused absorption + solve) and only the emission runs.
 int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, cudaEvent_t between = nullptr,
-                      bool solved = false);
+                      bool solved = false, int *nlaunch = nullptr);
+
+// Warp-specialized solve + emission over one request: the plan (its tile of
+// TC cells and shared memory, 0 where it does not apply) and the launch (the
+// kernel, then the residual fold when the request wants it).
+size_t plan_solve_emit(const dust_ctx *ctx, bool emit, bool mass, int *TC);
+int launch_solve_emit_fused(const EmitReq &req, int TC, size_t smem, int num_sms, cudaStream_t st,
+                            int *nlaunch = nullptr);
 
 // Grow the context's scratch to hold `cells` cells (synchronises `st` first).
 int ensure_scratch(dust_ctx *ctx, int64_t cells, cudaStream_t st);

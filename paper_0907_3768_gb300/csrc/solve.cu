@@ -119,9 +119,20 @@ int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_
         rc = precision == DUST_PREC_FP32 ? launch_gemm_simt(ctx, C, J, ld, sv.S, st)
                                          : launch_gemm_tc(ctx, precision, C, J, ld, sv.S, st);
     }
+    if (rc == DUST_OK) ctx->launches += 1;
+    int ftc = 0;
+    const size_t fsmem = !fused && ctx->fused_emit ? plan_solve_emit(ctx, L || resid, mass, &ftc) : 0;
     if (rc == DUST_OK) {
         if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[1], st));
-        rc = launch_emit_batch(B, p.smem, ctx->num_sms, st, prof ? ev[2] : nullptr, fused);
+        int nl = 0;
+        if (fsmem) {
+            // the solve runs inside the emission kernel: its time is reported with the emission's
+            if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[2], st));
+            rc = launch_solve_emit_fused(B.req[0], ftc, fsmem, ctx->num_sms, st, &nl);
+        } else {
+            rc = launch_emit_batch(B, p.smem, ctx->num_sms, st, prof ? ev[2] : nullptr, fused, &nl);
+        }
+        ctx->launches += (uint64_t)nl;
         if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[3], st));
     }
     for (int i = 0; i < 4; ++i) {

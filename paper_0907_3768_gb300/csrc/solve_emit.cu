@@ -32,6 +32,7 @@
 //   so results depend neither on the batch nor on timing.
 #include "dust_internal.cuh"
 #include "solve_core.cuh"
+#include "mbar.cuh"
 
 #include <algorithm>
 
@@ -78,6 +79,94 @@ __device__ __forceinline__ void load_pass(const EmitReq &q, int64_t cell, int gb
     }
 }
 
+// The solve of one cell by one warp: the exponent m_c of max_g n (general
+// form) or of the cell's mass (dust-mass form), then per pass of 32 NB grains
+// the roots, T and flags to global memory, and (emission) the pairs
+// (1/T, n 2^-m_c) and the cell record: to the request's scratch (q.prep
+// [C][G8], float2 or, in the dust-mass form, 1/T only; q.cell), or with SMEM
+// to `spairs` (float2 [G8], general form only) and `srec` in shared memory as
+// well as the record to q.cell.  s0 / n0: this cell's first pass, loaded.
+template <int NB, bool SMEM>
+__device__ __forceinline__ void solve_cell(const EmitReq &q, int64_t cell, int lane, const float (&s0)[NB],
+                                           const float (&n0)[NB], float2 *spairs, CellInfo *srec) {
+    const DevTables &tb = q.tb;
+    const int G = tb.G, G8 = tb.G8;
+    const bool emit = (q.mode & EMIT_ON) != 0, rs = (q.mode & EMIT_RESID) != 0;
+    const bool one = G8 <= 32 * NB;
+    const bool mass = (q.mode & EMIT_MASS) != 0;
+    int mc = 0;
+    float ms = 0.f;  // dust-mass form: m_c = ms 2^mc
+    if (emit && mass) {
+        const float m = __ldg(q.n + cell);
+        ms = (m != 0.f && isfinite(m)) ? frexpf(m, &mc) : m;
+    }
+    if (!one && emit && !mass) {
+        const float *nrow = q.n + cell * G;
+        float mx = 0.f;
+        for (int g = lane; g < G; g += 32) mx = fmaxf(mx, __ldg(nrow + g));
+        for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (mx > 0.f && mx < INFINITY) frexpf(mx, &mc);
+    }
+    float ah = 0.f, al = 0.f;  // absorbed power n 2^-m_c Pe 2^-Eg, float-float
+    for (int gb = 0; gb < G8; gb += 32 * NB) {
+        int gi[NB], fl[NB];
+        float s[NB], nv[NB], Tv[NB];
+        float4 gq[NB];
+        if (gb == 0) {
+#pragma unroll
+            for (int i = 0; i < NB; ++i) { s[i] = s0[i]; nv[i] = n0[i]; }
+        } else {
+            load_pass<NB>(q, cell, gb, lane, s, nv);
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int g = gb + lane + 32 * i;
+            gi[i] = g < G ? g : 0;
+            gq[i] = __ldg(reinterpret_cast<const float4 *>(tb.gp) + gi[i]);
+        }
+        if (one && emit && !mass) {
+            float mx = 0.f;
+#pragma unroll
+            for (int i = 0; i < NB; ++i) mx = fmaxf(mx, nv[i]);
+            for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (mx > 0.f && mx < INFINITY) frexpf(mx, &mc);
+        }
+        solve_batch<NB>(tb, gi, s, gq, Tv, fl);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int g = gb + lane + 32 * i;
+            if (g >= G8) continue;
+            float invT = PAD_INV_T, nn = 0.f;
+            if (g < G) {
+                q.T[cell * G + g] = Tv[i];
+                if (q.flags) q.flags[cell * G + g] = (uint8_t)fl[i];
+                grain_out(tb, g, Tv[i], fl[i], s[i], nv[i], mc, mass, rs, invT, nn, ah, al);
+            }
+            if (emit) {
+                if (SMEM) spairs[g] = make_float2(invT, nn);
+                else if (mass) reinterpret_cast<float *>(q.prep)[cell * G8 + g] = invT;
+                else q.prep[cell * G8 + g] = make_float2(invT, nn);
+            }
+        }
+    }
+    if (emit) {
+        if (rs)
+            for (int o = 16; o; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, ah, o), ol = __shfl_xor_sync(0xffffffffu, al, o);
+                ff_add(ah, al, oh, ol);
+            }
+        if (lane == 0) {
+            CellInfo ci;
+            ci.mc = mc;
+            ci.ah = rs ? ah : 0.f;
+            ci.al = rs ? al : 0.f;
+            ci.ms_bits = __float_as_int(ms);
+            q.cell[cell] = ci;
+            if (SMEM) *srec = ci;
+        }
+    }
+}
+
 // NB grains per lane per pass: a launch takes NB = ceil(G8 / 32) of its
 // widest request (at most NB_MAX), so that a cell of up to 32 NB grains is
 // one pass with no idle lanes, and its n row is loaded once: the exponent
@@ -96,10 +185,7 @@ __global__ void __launch_bounds__(SOLVE_TH, NB >= 4 ? 5 : 6) k_solve(const __gri
     load_pass<NB>(B.req[ri], u - B.req[ri].cell_begin, 0, lane, s0, n0);
     for (;;) {
         const EmitReq &q = B.req[ri];
-        const DevTables &tb = q.tb;
-        const int G = tb.G, G8 = tb.G8;
         const int64_t cell = u - q.cell_begin;
-        const bool emit = (q.mode & EMIT_ON) != 0, rs = (q.mode & EMIT_RESID) != 0;
         // issue the next cell's first pass now
         const int64_t un = u + nw;
         const bool more = un < B.ncells;
@@ -109,77 +195,7 @@ __global__ void __launch_bounds__(SOLVE_TH, NB >= 4 ? 5 : 6) k_solve(const __gri
             while (rn + 1 < B.nreq && un >= B.req[rn + 1].cell_begin) ++rn;
             load_pass<NB>(B.req[rn], un - B.req[rn].cell_begin, 0, lane, s1, n1);
         }
-        const bool one = G8 <= 32 * NB;
-        const bool mass = (q.mode & EMIT_MASS) != 0;
-        int mc = 0;
-        float ms = 0.f;  // dust-mass form: m_c = ms 2^mc
-        if (emit && mass) {
-            const float m = __ldg(q.n + cell);
-            ms = (m != 0.f && isfinite(m)) ? frexpf(m, &mc) : m;
-        }
-        if (!one && emit && !mass) {
-            const float *nrow = q.n + cell * G;
-            float mx = 0.f;
-            for (int g = lane; g < G; g += 32) mx = fmaxf(mx, __ldg(nrow + g));
-            for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if (mx > 0.f && mx < INFINITY) frexpf(mx, &mc);
-        }
-        float ah = 0.f, al = 0.f;  // absorbed power n 2^-m_c Pe 2^-Eg, float-float
-        for (int gb = 0; gb < G8; gb += 32 * NB) {
-            int gi[NB], fl[NB];
-            float s[NB], nv[NB], Tv[NB];
-            float4 gq[NB];
-            if (gb == 0) {
-#pragma unroll
-                for (int i = 0; i < NB; ++i) { s[i] = s0[i]; nv[i] = n0[i]; }
-            } else {
-                load_pass<NB>(q, cell, gb, lane, s, nv);
-            }
-#pragma unroll
-            for (int i = 0; i < NB; ++i) {
-                const int g = gb + lane + 32 * i;
-                gi[i] = g < G ? g : 0;
-                gq[i] = __ldg(reinterpret_cast<const float4 *>(tb.gp) + gi[i]);
-            }
-            if (one && emit && !mass) {
-                float mx = 0.f;
-#pragma unroll
-                for (int i = 0; i < NB; ++i) mx = fmaxf(mx, nv[i]);
-                for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                if (mx > 0.f && mx < INFINITY) frexpf(mx, &mc);
-            }
-            solve_batch<NB>(tb, gi, s, gq, Tv, fl);
-#pragma unroll
-            for (int i = 0; i < NB; ++i) {
-                const int g = gb + lane + 32 * i;
-                if (g >= G8) continue;
-                float invT = PAD_INV_T, nn = 0.f;
-                if (g < G) {
-                    q.T[cell * G + g] = Tv[i];
-                    if (q.flags) q.flags[cell * G + g] = (uint8_t)fl[i];
-                    grain_out(tb, g, Tv[i], fl[i], s[i], nv[i], mc, mass, rs, invT, nn, ah, al);
-                }
-                if (emit) {
-                    if (mass) reinterpret_cast<float *>(q.prep)[cell * G8 + g] = invT;
-                    else q.prep[cell * G8 + g] = make_float2(invT, nn);
-                }
-            }
-        }
-        if (emit) {
-            if (rs)
-                for (int o = 16; o; o >>= 1) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, ah, o), ol = __shfl_xor_sync(0xffffffffu, al, o);
-                    ff_add(ah, al, oh, ol);
-                }
-            if (lane == 0) {
-                CellInfo ci;
-                ci.mc = mc;
-                ci.ah = rs ? ah : 0.f;
-                ci.al = rs ? al : 0.f;
-                ci.ms_bits = __float_as_int(ms);
-                q.cell[cell] = ci;
-            }
-        }
+        solve_cell<NB, false>(q, cell, lane, s0, n0, nullptr, nullptr);
         if (!more) break;
         u = un;
         ri = rn;
@@ -474,6 +490,180 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
 // Energy-balance residual of every cell of the requests that want it: one
 // thread per cell sums the cell's k-group partials in ascending order, so
 // the order depends only on NKG.
+// Solve and emission of one request in one warp-specialized kernel, for
+// the general form with the emission weights resident in shared memory.
+// One CTA per SM walks tiles of TC = q.TC cells.  Its FS_W solver warps run
+// k_solve's per-cell solve (solve_cell) on the tile after the one being
+// emitted, writing T and the flags to global memory and the pairs (1/T, n
+// 2^-m_c) and cell records into one of FSE_NBUF shared-memory tile buffers; its
+// FE_W emission warps take one cell x 8 wavelengths per thread from an
+// earlier buffer, with k_emit's arithmetic in k_emit's order.  The solve is a
+// latency-bound chain of table lookups and the emission is bound by the FMA
+// pipe, so the two overlap on the same SM.  Two mbarriers per buffer hand it
+// over (full: the solvers' writes are done; empty: the emission has read
+// it); every wait is bounded, and on expiry the kernel records
+// DUST_ETIMEOUT and both roles wind down.
+constexpr int FE_W = 16;  // emission warps
+constexpr int FS_W = 8;   // solver warps
+constexpr int FSE_TH = (FE_W + FS_W) * 32;
+constexpr int FSE_NBUF = 3;  // pair-tile buffers: the solvers run up to FSE_NBUF tiles ahead
+
+template <int NB>
+__global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant__ EmitReq q) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const DevTables &tb = q.tb;
+    const int G8 = tb.G8, NKG = tb.NKG, K = tb.K, TC = q.TC;
+    const int CST = 2 * G8 + 1;
+    const int PS = G8 + 1;  // odd row stride (in float2) of a pair tile: the lanes' cells fall in distinct banks
+    float4 *sC = reinterpret_cast<float4 *>(smem_raw);                          // [NKG][CST]
+    float2 *sP = reinterpret_cast<float2 *>(sC + (size_t)NKG * CST);           // [FSE_NBUF][TC][PS]
+    CellInfo *sI = reinterpret_cast<CellInfo *>(sP + (size_t)FSE_NBUF * TC * PS);  // [FSE_NBUF][TC]
+    uint64_t *full = reinterpret_cast<uint64_t *>(sI + FSE_NBUF * TC);         // [FSE_NBUF]
+    uint64_t *empty = full + FSE_NBUF;                                         // [FSE_NBUF]
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + FSE_NBUF);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t ntiles = (q.C + TC - 1) / TC;
+
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
+        for (int i = tid; i < NKG * 2 * G8; i += FSE_TH) {
+            const int kg = i / (2 * G8), o = i - kg * 2 * G8;
+            sC[(size_t)kg * CST + o] = __ldg(src + i);
+        }
+    }
+    if (tid == 0) {
+        for (int b = 0; b < FSE_NBUF; ++b) { mbar_init(&full[b], FS_W); mbar_init(&empty[b], FE_W); }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp >= FE_W) {
+        // ------------------------------------------------------------ solvers
+        const int sw = warp - FE_W;
+        int64_t tile = blockIdx.x;
+        int cl = sw;  // this warp's cells of a tile: sw, sw + FS_W, ...
+        int it = 0;
+        // first cell of this warp (tiles whose share for it is empty are skipped by the loop)
+        auto cell_of = [&](int64_t t, int c) { return t * TC + c; };
+        float s0[NB], n0[NB];
+        bool have = tile < ntiles && cl < TC && cell_of(tile, cl) < q.C;
+        if (have) load_pass<NB>(q, cell_of(tile, cl), 0, lane, s0, n0);
+        bool ok = true;
+        for (; tile < ntiles && ok; tile += gridDim.x, ++it) {
+            const int b = it % FSE_NBUF;
+            const uint32_t ph = (uint32_t)((it / FSE_NBUF) & 1);
+            if (!(ok = mbar_wait(&empty[b], ph ^ 1, abort_flag, tb.status))) break;
+            const int nc = (int)min((int64_t)TC, q.C - tile * TC);
+            for (cl = sw; cl < nc; cl += FS_W) {
+                const int64_t cell = cell_of(tile, cl);
+                // next cell of this warp: in this tile, else its first in the next tile
+                int64_t tn = tile;
+                int cn = cl + FS_W;
+                if (cn >= nc) { tn = tile + gridDim.x; cn = sw; }
+                const int64_t un = cell_of(tn, cn);
+                const bool more = tn < ntiles && cn < TC && un < q.C;
+                float s1[NB], n1[NB];
+                if (more) load_pass<NB>(q, un, 0, lane, s1, n1);
+                solve_cell<NB, true>(q, cell, lane, s0, n0, sP + ((size_t)b * TC + cl) * PS, sI + b * TC + cl);
+#pragma unroll
+                for (int i = 0; i < NB; ++i) { s0[i] = s1[i]; n0[i] = n1[i]; }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[b]);
+        }
+    } else {
+        // ------------------------------------------------------------ emission
+        const int icell = tid % TC, ikg = tid / TC;
+        const bool active = ikg < NKG;
+        const int kgi = active ? ikg : 0;
+        float2 nax2[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) nax2[p] = __ldg(reinterpret_cast<const float2 *>(tb.nax + kgi * KQ) + p);
+        const float4 *cp = sC + (size_t)kgi * CST;
+        const bool rs = (q.mode & EMIT_RESID) != 0, storeL = (q.mode & EMIT_STORE_L) != 0;
+        const bool vecL = storeL && ((reinterpret_cast<uintptr_t>(q.L) & 15) == 0) && (q.ld % 4 == 0);
+        int it = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+            const int b = it % FSE_NBUF;
+            const uint32_t ph = (uint32_t)((it / FSE_NBUF) & 1);
+            if (!(ok = mbar_wait(&full[b], ph, abort_flag, tb.status))) break;
+            const int nc = (int)min((int64_t)TC, q.C - tile * TC);
+            if (active && icell < nc) {
+                const float2 *tnp = sP + ((size_t)b * TC + icell) * PS;
+                float2 acc[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc[p] = make_float2(0.f, 0.f);
+                for (int gg0 = 0; gg0 < G8; gg0 += RG) {
+                    float2 N[4], D[4];
+#pragma unroll
+                    for (int u = 0; u < RG; ++u) {
+                        const float4 ca = cp[2 * (gg0 + u)], cb = cp[2 * (gg0 + u) + 1];
+                        const float2 cw[4] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w), make_float2(cb.x, cb.y),
+                                              make_float2(cb.z, cb.w)};
+                        const float2 tn = tnp[gg0 + u];  // (1/T, n) of this cell
+                        const float2 iT = make_float2(tn.x, tn.x), nn = make_float2(tn.y, tn.y);
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            if (u == 0) emit_first(nax2[p], iT, nn, cw[p], N[p], D[p]);
+                            else emit_pair(nax2[p], iT, nn, cw[p], N[p], D[p]);
+                        }
+                    }
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        acc[p].x = fmaf(N[p].x, rcp_approx(D[p].x), acc[p].x);
+                        acc[p].y = fmaf(N[p].y, rcp_approx(D[p].y), acc[p].y);
+                    }
+                }
+                // epilogue, as k_emit's: scale, store, residual partial
+                const int64_t cell = tile * TC + icell;
+                const int mc = sI[b * TC + icell].mc;
+                const int kb = ikg * KQ;
+                if (storeL) {
+                    float Lv[KQ];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int k = min(kb + 2 * p + h, K - 1);
+                            Lv[2 * p + h] = scale2(h ? acc[p].y : acc[p].x, mc + __ldg(tb.qexp + k));
+                        }
+                    }
+                    float *row = q.L + cell * q.ld + kb;
+                    if (vecL && kb + KQ <= K) {
+                        reinterpret_cast<float4 *>(row)[0] = make_float4(Lv[0], Lv[1], Lv[2], Lv[3]);
+                        reinterpret_cast<float4 *>(row)[1] = make_float4(Lv[4], Lv[5], Lv[6], Lv[7]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < KQ; ++j)
+                            if (kb + j < K) row[j] = Lv[j];
+                    }
+                }
+                if (rs) {
+                    float sh = 0.f, sl = 0.f;
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int k = kb + 2 * p + h;
+                            if (k < K) {
+                                const float a = h ? acc[p].y : acc[p].x;
+                                const float wk = __ldg(tb.wq + k);
+                                const float pr = wk * a;
+                                ff_add(sh, sl, pr, fmaf(wk, a, -pr));
+                            }
+                        }
+                    }
+                    q.part[cell * NKG + ikg] = make_float2(sh, sl);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[b]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(SOLVE_TH) k_resid(const __grid_constant__ EmitBatch E) {
     const int64_t stride = (int64_t)gridDim.x * SOLVE_TH;
     int ri = 0;
@@ -567,7 +757,8 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
 // Numbers the cells and emission tiles of a filled batch; launches the solve
 // over every request, then the emission over the requests that want it.
 int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, cudaEvent_t between,
-                      bool solved) {
+                      bool solved, int *nlaunch) {
+    int nl = 0;
     int64_t cells = 0;
     for (int i = 0; i < B.nreq; ++i) {
         EmitReq &r = B.req[i];
@@ -575,6 +766,7 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
         cells += r.C;
     }
     B.ncells = cells;
+    if (nlaunch) *nlaunch = 0;
     if (cells <= 0) return DUST_OK;
     if (!solved) {
         // one warp per cell, up to 16 CTAs of 4 warps per SM
@@ -589,6 +781,7 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
             default: k_solve<4><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
         }
         DUST_CUDA_TRY(cudaGetLastError());
+        ++nl;
     }
     if (between) DUST_CUDA_TRY(cudaEventRecord(between, st));
     // emission work lists: the requests that want L or resid, in order, one
@@ -623,11 +816,68 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
         if (form) k_emit<true><<<(unsigned)grid, NTH, smem, st>>>(E);
         else k_emit<false><<<(unsigned)grid, NTH, smem, st>>>(E);
         DUST_CUDA_TRY(cudaGetLastError());
+        ++nl;
         if (resid) {
             const int64_t rgrid = std::min<int64_t>((E.ncells + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
             k_resid<<<(unsigned)rgrid, SOLVE_TH, 0, st>>>(E);
             DUST_CUDA_TRY(cudaGetLastError());
+            ++nl;
         }
+    }
+    if (nlaunch) *nlaunch = nl;
+    return DUST_OK;
+}
+
+// Tile and shared memory of the warp-specialized solve + emission kernel for
+// the context, or 0 where it does not apply: no emission, the dust-mass form,
+// or emission weights that do not fit beside two pair tiles with room left
+// for L1 (the solve's table lookups live there).
+size_t plan_solve_emit(const dust_ctx *ctx, bool emit, bool mass, int *TC) {
+    if (!emit || mass) return 0;
+    const DevTables &tb = ctx->tb;
+    const int tc = std::min(64, (FE_W * 32) / tb.NKG);
+    if (tc < 1) return 0;
+    const size_t smem = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + (size_t)FSE_NBUF * tc * (tb.G8 + 1) * 8 +
+                        (size_t)FSE_NBUF * tc * sizeof(CellInfo) + 2 * FSE_NBUF * sizeof(uint64_t) + 16;
+    if (smem > 160 * 1024) return 0;
+    *TC = tc;
+    return smem;
+}
+
+// The fused kernel over one request (general form), then the residual fold.
+int launch_solve_emit_fused(const EmitReq &req, int TC, size_t smem, int num_sms, cudaStream_t st,
+                            int *nlaunch) {
+    if (nlaunch) *nlaunch = 0;
+    if (req.C <= 0) return DUST_OK;
+    EmitBatch E;
+    E.nreq = 1;
+    E.req[0] = req;
+    EmitReq &r = E.req[0];
+    r.TC = TC;
+    r.cell_begin = 0;
+    r.tile_begin = 0;
+    E.ncells = r.C;
+    E.ntiles = (r.C + TC - 1) / TC;
+    const int nb = std::min(NB_MAX, (r.tb.G8 + 31) / 32);
+    const void *kern = nb == 1 ? reinterpret_cast<const void *>(k_solve_emit<1>)
+                     : nb == 2 ? reinterpret_cast<const void *>(k_solve_emit<2>)
+                     : nb == 3 ? reinterpret_cast<const void *>(k_solve_emit<3>)
+                               : reinterpret_cast<const void *>(k_solve_emit<4>);
+    DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned grid = (unsigned)std::min<int64_t>(E.ntiles, num_sms);
+    switch (nb) {
+        case 1: k_solve_emit<1><<<grid, FSE_TH, smem, st>>>(r); break;
+        case 2: k_solve_emit<2><<<grid, FSE_TH, smem, st>>>(r); break;
+        case 3: k_solve_emit<3><<<grid, FSE_TH, smem, st>>>(r); break;
+        default: k_solve_emit<4><<<grid, FSE_TH, smem, st>>>(r); break;
+    }
+    DUST_CUDA_TRY(cudaGetLastError());
+    if (nlaunch) *nlaunch = 1;
+    if (r.mode & EMIT_RESID) {
+        const int64_t rgrid = std::min<int64_t>((r.C + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
+        k_resid<<<(unsigned)rgrid, SOLVE_TH, 0, st>>>(E);
+        DUST_CUDA_TRY(cudaGetLastError());
+        if (nlaunch) *nlaunch = 2;
     }
     return DUST_OK;
 }
