@@ -84,8 +84,9 @@ __device__ __forceinline__ void load_pass(const EmitReq &q, int64_t cell, int gb
 // the roots, T and flags to global memory, and (emission) the pairs
 // (1/T, n 2^-m_c) and the cell record: to the request's scratch (q.prep
 // [C][G8], float2 or, in the dust-mass form, 1/T only; q.cell), or with SMEM
-// to `spairs` (float2 [G8], general form only) and `srec` in shared memory as
-// well as the record to q.cell.  s0 / n0: this cell's first pass, loaded.
+// to `spairs` (G8 float2, or G8 floats in the dust-mass form) and `srec` in
+// shared memory as well as the record to q.cell.  s0 / n0: this cell's first
+// pass, loaded.
 template <int NB, bool SMEM>
 __device__ __forceinline__ void solve_cell(const EmitReq &q, int64_t cell, int lane, const float (&s0)[NB],
                                            const float (&n0)[NB], float2 *spairs, CellInfo *srec) {
@@ -143,9 +144,14 @@ __device__ __forceinline__ void solve_cell(const EmitReq &q, int64_t cell, int l
                 grain_out(tb, g, Tv[i], fl[i], s[i], nv[i], mc, mass, rs, invT, nn, ah, al);
             }
             if (emit) {
-                if (SMEM) spairs[g] = make_float2(invT, nn);
-                else if (mass) reinterpret_cast<float *>(q.prep)[cell * G8 + g] = invT;
-                else q.prep[cell * G8 + g] = make_float2(invT, nn);
+                if (SMEM) {
+                    if (mass) reinterpret_cast<float *>(spairs)[g] = invT;
+                    else spairs[g] = make_float2(invT, nn);
+                } else if (mass) {
+                    reinterpret_cast<float *>(q.prep)[cell * G8 + g] = invT;
+                } else {
+                    q.prep[cell * G8 + g] = make_float2(invT, nn);
+                }
             }
         }
     }
@@ -491,7 +497,8 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
 // thread per cell sums the cell's k-group partials in ascending order, so
 // the order depends only on NKG.
 // Solve and emission of one request in one warp-specialized kernel, for
-// the general form with the emission weights resident in shared memory.
+// either form of n (general, or the dust-mass form n_g m_c with 1/T-only
+// pairs), with the emission weights resident in shared memory.
 // One CTA per SM walks tiles of TC = q.TC cells.  Its FS_W solver warps run
 // k_solve's per-cell solve (solve_cell) on the tile after the one being
 // emitted, writing T and the flags to global memory and the pairs (1/T, n
@@ -508,16 +515,18 @@ constexpr int FS_W = 8;   // solver warps
 constexpr int FSE_TH = (FE_W + FS_W) * 32;
 constexpr int FSE_NBUF = 3;  // pair-tile buffers: the solvers run up to FSE_NBUF tiles ahead
 
-template <int NB>
+template <int NB, bool MASS>
 __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant__ EmitReq q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevTables &tb = q.tb;
     const int G8 = tb.G8, NKG = tb.NKG, K = tb.K, TC = q.TC;
     const int CST = 2 * G8 + 1;
-    const int PS = G8 + 1;  // odd row stride (in float2) of a pair tile: the lanes' cells fall in distinct banks
+    // odd row stride of a pair tile (in float2, or floats for 1/T alone): a warp's cells fall in distinct banks
+    const int PS = G8 + 1;
+    constexpr int PW = MASS ? 1 : 2;  // floats per pair
     float4 *sC = reinterpret_cast<float4 *>(smem_raw);                          // [NKG][CST]
-    float2 *sP = reinterpret_cast<float2 *>(sC + (size_t)NKG * CST);           // [FSE_NBUF][TC][PS]
-    CellInfo *sI = reinterpret_cast<CellInfo *>(sP + (size_t)FSE_NBUF * TC * PS);  // [FSE_NBUF][TC]
+    float *sP = reinterpret_cast<float *>(sC + (size_t)NKG * CST);             // [FSE_NBUF][TC][PS][PW]
+    CellInfo *sI = reinterpret_cast<CellInfo *>(sP + (((size_t)FSE_NBUF * TC * PS * PW + 3) & ~(size_t)3));  // [FSE_NBUF][TC]
     uint64_t *full = reinterpret_cast<uint64_t *>(sI + FSE_NBUF * TC);         // [FSE_NBUF]
     uint64_t *empty = full + FSE_NBUF;                                         // [FSE_NBUF]
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + FSE_NBUF);
@@ -565,7 +574,8 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
                 const bool more = tn < ntiles && cn < TC && un < q.C;
                 float s1[NB], n1[NB];
                 if (more) load_pass<NB>(q, un, 0, lane, s1, n1);
-                solve_cell<NB, true>(q, cell, lane, s0, n0, sP + ((size_t)b * TC + cl) * PS, sI + b * TC + cl);
+                solve_cell<NB, true>(q, cell, lane, s0, n0, reinterpret_cast<float2 *>(sP + ((size_t)b * TC + cl) * PS * PW),
+                                     sI + b * TC + cl);
 #pragma unroll
                 for (int i = 0; i < NB; ++i) { s0[i] = s1[i]; n0[i] = n1[i]; }
             }
@@ -591,7 +601,7 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
             if (!(ok = mbar_wait(&full[b], ph, abort_flag, tb.status))) break;
             const int nc = (int)min((int64_t)TC, q.C - tile * TC);
             if (active && icell < nc) {
-                const float2 *tnp = sP + ((size_t)b * TC + icell) * PS;
+                const float *tnp = sP + ((size_t)b * TC + icell) * PS * PW;
                 float2 acc[4];
 #pragma unroll
                 for (int p = 0; p < 4; ++p) acc[p] = make_float2(0.f, 0.f);
@@ -602,12 +612,22 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
                         const float4 ca = cp[2 * (gg0 + u)], cb = cp[2 * (gg0 + u) + 1];
                         const float2 cw[4] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w), make_float2(cb.x, cb.y),
                                               make_float2(cb.z, cb.w)};
-                        const float2 tn = tnp[gg0 + u];  // (1/T, n) of this cell
-                        const float2 iT = make_float2(tn.x, tn.x), nn = make_float2(tn.y, tn.y);
+                        if (MASS) {  // 1/T of this cell; the weights carry n_g
+                            const float t = tnp[gg0 + u];
+                            const float2 iT = make_float2(t, t);
 #pragma unroll
-                        for (int p = 0; p < 4; ++p) {
-                            if (u == 0) emit_first(nax2[p], iT, nn, cw[p], N[p], D[p]);
-                            else emit_pair(nax2[p], iT, nn, cw[p], N[p], D[p]);
+                            for (int p = 0; p < 4; ++p) {
+                                if (u == 0) emit_first_m(nax2[p], iT, cw[p], N[p], D[p]);
+                                else emit_pair_m(nax2[p], iT, cw[p], N[p], D[p]);
+                            }
+                        } else {  // (1/T, n) of this cell
+                            const float2 tn = reinterpret_cast<const float2 *>(tnp)[gg0 + u];
+                            const float2 iT = make_float2(tn.x, tn.x), nn = make_float2(tn.y, tn.y);
+#pragma unroll
+                            for (int p = 0; p < 4; ++p) {
+                                if (u == 0) emit_first(nax2[p], iT, nn, cw[p], N[p], D[p]);
+                                else emit_pair(nax2[p], iT, nn, cw[p], N[p], D[p]);
+                            }
                         }
                     }
 #pragma unroll
@@ -618,7 +638,9 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
                 }
                 // epilogue, as k_emit's: scale, store, residual partial
                 const int64_t cell = tile * TC + icell;
-                const int mc = sI[b * TC + icell].mc;
+                const CellInfo ci = sI[b * TC + icell];
+                const int mc = ci.mc;
+                const float ms = MASS ? __int_as_float(ci.ms_bits) : 1.f;  // the cell's mass mantissa
                 const int kb = ikg * KQ;
                 if (storeL) {
                     float Lv[KQ];
@@ -627,7 +649,8 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int k = min(kb + 2 * p + h, K - 1);
-                            Lv[2 * p + h] = scale2(h ? acc[p].y : acc[p].x, mc + __ldg(tb.qexp + k));
+                            const float a = h ? acc[p].y : acc[p].x;
+                            Lv[2 * p + h] = scale2(MASS ? a * ms : a, mc + __ldg(tb.qexp + k));
                         }
                     }
                     float *row = q.L + cell * q.ld + kb;
@@ -829,15 +852,15 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
 }
 
 // Tile and shared memory of the warp-specialized solve + emission kernel for
-// the context, or 0 where it does not apply: no emission, the dust-mass form,
-// or emission weights that do not fit beside two pair tiles with room left
-// for L1 (the solve's table lookups live there).
+// the context, or 0 where it does not apply: no emission, or emission
+// weights that do not fit beside the pair tiles with room left for L1 (the
+// solve's table lookups live there).
 size_t plan_solve_emit(const dust_ctx *ctx, bool emit, bool mass, int *TC) {
-    if (!emit || mass) return 0;
-    const DevTables &tb = ctx->tb;
+    if (!emit || (mass && !ctx->mass_ready)) return 0;
+    const DevTables &tb = mass ? ctx->tbm : ctx->tb;
     const int tc = std::min(64, (FE_W * 32) / tb.NKG);
     if (tc < 1) return 0;
-    const size_t smem = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + (size_t)FSE_NBUF * tc * (tb.G8 + 1) * 8 +
+    const size_t smem = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + (((size_t)FSE_NBUF * tc * (tb.G8 + 1) * (mass ? 4 : 8) + 15) & ~(size_t)15) +
                         (size_t)FSE_NBUF * tc * sizeof(CellInfo) + 2 * FSE_NBUF * sizeof(uint64_t) + 16;
     if (smem > 160 * 1024) return 0;
     *TC = tc;
@@ -845,6 +868,23 @@ size_t plan_solve_emit(const dust_ctx *ctx, bool emit, bool mass, int *TC) {
 }
 
 // The fused kernel over one request (general form), then the residual fold.
+template <bool MASS>
+int launch_fse(const EmitReq &r, int nb, unsigned grid, size_t smem, cudaStream_t st) {
+    const void *kern = nb == 1 ? reinterpret_cast<const void *>(k_solve_emit<1, MASS>)
+                     : nb == 2 ? reinterpret_cast<const void *>(k_solve_emit<2, MASS>)
+                     : nb == 3 ? reinterpret_cast<const void *>(k_solve_emit<3, MASS>)
+                               : reinterpret_cast<const void *>(k_solve_emit<4, MASS>);
+    DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    switch (nb) {
+        case 1: k_solve_emit<1, MASS><<<grid, FSE_TH, smem, st>>>(r); break;
+        case 2: k_solve_emit<2, MASS><<<grid, FSE_TH, smem, st>>>(r); break;
+        case 3: k_solve_emit<3, MASS><<<grid, FSE_TH, smem, st>>>(r); break;
+        default: k_solve_emit<4, MASS><<<grid, FSE_TH, smem, st>>>(r); break;
+    }
+    DUST_CUDA_TRY(cudaGetLastError());
+    return DUST_OK;
+}
+
 int launch_solve_emit_fused(const EmitReq &req, int TC, size_t smem, int num_sms, cudaStream_t st,
                             int *nlaunch) {
     if (nlaunch) *nlaunch = 0;
@@ -859,19 +899,10 @@ int launch_solve_emit_fused(const EmitReq &req, int TC, size_t smem, int num_sms
     E.ncells = r.C;
     E.ntiles = (r.C + TC - 1) / TC;
     const int nb = std::min(NB_MAX, (r.tb.G8 + 31) / 32);
-    const void *kern = nb == 1 ? reinterpret_cast<const void *>(k_solve_emit<1>)
-                     : nb == 2 ? reinterpret_cast<const void *>(k_solve_emit<2>)
-                     : nb == 3 ? reinterpret_cast<const void *>(k_solve_emit<3>)
-                               : reinterpret_cast<const void *>(k_solve_emit<4>);
-    DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const bool mass = (r.mode & EMIT_MASS) != 0;
     const unsigned grid = (unsigned)std::min<int64_t>(E.ntiles, num_sms);
-    switch (nb) {
-        case 1: k_solve_emit<1><<<grid, FSE_TH, smem, st>>>(r); break;
-        case 2: k_solve_emit<2><<<grid, FSE_TH, smem, st>>>(r); break;
-        case 3: k_solve_emit<3><<<grid, FSE_TH, smem, st>>>(r); break;
-        default: k_solve_emit<4><<<grid, FSE_TH, smem, st>>>(r); break;
-    }
-    DUST_CUDA_TRY(cudaGetLastError());
+    int rc = mass ? launch_fse<true>(r, nb, grid, smem, st) : launch_fse<false>(r, nb, grid, smem, st);
+    if (rc != DUST_OK) return rc;
     if (nlaunch) *nlaunch = 1;
     if (r.mode & EMIT_RESID) {
         const int64_t rgrid = std::min<int64_t>((r.C + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);

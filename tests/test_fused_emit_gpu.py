@@ -120,3 +120,32 @@ def test_fused_emit_cell_results_independent_of_batch():
         b = {k: v.cpu().numpy() for k, v in ctx.solve(J[1234:2345], n[1234:2345]).items()}
     for k in ("T", "L", "resid", "flags"):
         np.testing.assert_array_equal(a[k][1234:2345], b[k])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_fused_emit_mass_form(prec):
+    """The dust-mass form n[c,g] = n_g m_c (Eqs. 9-10): 1/T-only pairs, the
+    weights carrying n_g, L scaled by the cell's mass; dust-free cells too."""
+    from paper_0907_3768_gb300 import Context, padded_rows
+
+    wl = synth.make_workload(1, cells=np.arange(2500))
+    rng = np.random.default_rng(3)
+    n_g = wl.n[0].astype(np.float64) * np.exp(rng.normal(0.0, 1.0, wl.G))
+    m = np.exp(rng.normal(0.0, 2.0, 2500)).astype(np.float32)
+    m[::41] = 0.0
+    out = {}
+    with Context.from_workload(wl, precision=prec) as ctx:
+        ctx.set_grain_numbers(n_g)
+        J = padded_rows(torch.from_numpy(wl.J).cuda())
+        for fused in (False, True):
+            ctx.set_fused_emit(fused)
+            o = ctx.solve_mass(J, torch.from_numpy(m).cuda())
+            torch.cuda.synchronize()
+            assert ctx.check() == 0
+            out[fused] = {k: v.cpu().numpy() for k, v in o.items() if v is not None}
+    _same(out[False], out[True])
+    n_full = m.astype(np.float64)[:, None] * n_g[None, :]
+    ref = oracle.run(wl.lam, wl.w, wl.C_abs, wl.J, n_full, wl.T_min, wl.T_max)
+    dusty = m > 0
+    assert l_err(out[True]["L"][dusty], ref["L"][dusty]).max() <= TOL[prec][1]
+
