@@ -196,8 +196,10 @@ int dust_solve_host(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, 
     if (dg.rc != DUST_OK) return dg.rc;
     const int G = ctx->G;
     constexpr int NB = dust_ctx::NHB;
-    // chunks of at least 8192 cells, about 16 of them for large batches
-    int64_t chunk = std::max<int64_t>(8192, (n_cells + 15) / 16);
+    // about 8 chunks of at least 8192 cells: every chunk costs six copies, and
+    // each copy has a fixed cost of ~10 us that, with both directions busy,
+    // outweighs the shorter pipeline fill and drain of more, smaller chunks
+    int64_t chunk = std::max<int64_t>(8192, (n_cells + 7) / 8);
     chunk = (chunk + 127) / 128 * 128;
     chunk = std::min<int64_t>(chunk, n_cells);
     auto &hs = ctx->hs;
