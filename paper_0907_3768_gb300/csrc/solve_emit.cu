@@ -258,6 +258,62 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Epilogue of one emission item (one cell, the 8 wavelengths of k-group
+// ikg) in the warp-specialized kernel, the same arithmetic in the same order
+// as k_emit's inline epilogue (kept inline there: as a call it cost k_emit
+// 1-3 %): the accumulators scaled by
+// 2^(m_c + q_k) (times the cell's mass mantissa ms in the dust-mass form) are
+// stored as L, as two 16-byte stores (one 32-byte sector) when the row allows
+// it, and the item's residual partial sum_k w_k L_k is accumulated
+// error-free in float-float (products split by FMA, sums by two-sum).
+template <bool MASS>
+__device__ __forceinline__ void emit_item_out(const EmitReq &q, int64_t cell, int ikg, const float2 (&acc)[4], int mc,
+                                              float ms, bool storeL, bool vecL, bool rs) {
+    const DevTables &tb = q.tb;
+    const int K = tb.K;
+    float sh = 0.f, sl = 0.f;
+    const int kb = ikg * KQ;
+    float Lv[KQ];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = min(kb + 2 * p + h, K - 1);
+            const float a = h ? acc[p].y : acc[p].x;
+            Lv[2 * p + h] = scale2(MASS ? a * ms : a, mc + __ldg(tb.qexp + k));
+        }
+    }
+    if (storeL) {
+        float *row = q.L + cell * q.ld + kb;
+        if (vecL && kb + KQ <= K) {
+            reinterpret_cast<float4 *>(row)[0] = make_float4(Lv[0], Lv[1], Lv[2], Lv[3]);
+            reinterpret_cast<float4 *>(row)[1] = make_float4(Lv[4], Lv[5], Lv[6], Lv[7]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < KQ; ++j)
+                if (kb + j < K) row[j] = Lv[j];
+        }
+    }
+    if (rs) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = kb + 2 * p + h;
+                if (k < K) {
+                    // w_k L_k 2^-(m_c + Ew) = wq_k a: the FP32 accumulator before
+                    // its power-of-two scaling (equal to the stored L unless L is subnormal)
+                    const float a = h ? acc[p].y : acc[p].x;
+                    const float wk = __ldg(tb.wq + k);
+                    const float pr = wk * a;
+                    ff_add(sh, sl, pr, fmaf(wk, a, -pr));
+                }
+            }
+        }
+    }
+    if (rs) q.part[cell * tb.NKG + ikg] = make_float2(sh, sl);
+}
+
 // Request and first cell of global emission tile `tile`.
 __device__ __forceinline__ int emit_req_of(const EmitBatch &B, int64_t tile, int ri) {
     while (ri + 1 < B.nreq && tile >= B.req[ri + 1].tile_begin) ++ri;
@@ -519,7 +575,7 @@ template <int NB, bool MASS>
 __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant__ EmitReq q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevTables &tb = q.tb;
-    const int G8 = tb.G8, NKG = tb.NKG, K = tb.K, TC = q.TC;
+    const int G8 = tb.G8, NKG = tb.NKG, TC = q.TC;
     const int CST = 2 * G8 + 1;
     // odd row stride of a pair tile (in float2, or floats for 1/T alone): a warp's cells fall in distinct banks
     const int PS = G8 + 1;
@@ -636,50 +692,10 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
                         acc[p].y = fmaf(N[p].y, rcp_approx(D[p].y), acc[p].y);
                     }
                 }
-                // epilogue, as k_emit's: scale, store, residual partial
+                // epilogue, the emission kernel's
                 const int64_t cell = tile * TC + icell;
                 const CellInfo ci = sI[b * TC + icell];
-                const int mc = ci.mc;
-                const float ms = MASS ? __int_as_float(ci.ms_bits) : 1.f;  // the cell's mass mantissa
-                const int kb = ikg * KQ;
-                if (storeL) {
-                    float Lv[KQ];
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int k = min(kb + 2 * p + h, K - 1);
-                            const float a = h ? acc[p].y : acc[p].x;
-                            Lv[2 * p + h] = scale2(MASS ? a * ms : a, mc + __ldg(tb.qexp + k));
-                        }
-                    }
-                    float *row = q.L + cell * q.ld + kb;
-                    if (vecL && kb + KQ <= K) {
-                        reinterpret_cast<float4 *>(row)[0] = make_float4(Lv[0], Lv[1], Lv[2], Lv[3]);
-                        reinterpret_cast<float4 *>(row)[1] = make_float4(Lv[4], Lv[5], Lv[6], Lv[7]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < KQ; ++j)
-                            if (kb + j < K) row[j] = Lv[j];
-                    }
-                }
-                if (rs) {
-                    float sh = 0.f, sl = 0.f;
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int k = kb + 2 * p + h;
-                            if (k < K) {
-                                const float a = h ? acc[p].y : acc[p].x;
-                                const float wk = __ldg(tb.wq + k);
-                                const float pr = wk * a;
-                                ff_add(sh, sl, pr, fmaf(wk, a, -pr));
-                            }
-                        }
-                    }
-                    q.part[cell * NKG + ikg] = make_float2(sh, sl);
-                }
+                emit_item_out<MASS>(q, cell, ikg, acc, ci.mc, MASS ? __int_as_float(ci.ms_bits) : 1.f, storeL, vecL, rs);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[b]);
