@@ -103,6 +103,8 @@ struct EmitReq {
     CellInfo *cell;
     float2 *part;
     int TC, GC, resident, mode;
+    int nth;        // emission threads per CTA (256: two CTAs per SM; 512: one, for streamed weights)
+    uint32_t smem;  // its emission kernel's shared memory
 };
 
 struct EmitBatch {
@@ -118,7 +120,7 @@ struct SolveList {
 };
 
 struct EmitPlan {
-    int TC, GC, resident;
+    int TC, GC, resident, nth;
     size_t smem;
 };
 
@@ -227,11 +229,13 @@ const char *cuda_err_name(cudaError_t e);
 #define DUST_CUDA_TRY(expr)                                                          \
     do {                                                                             \
         cudaError_t _e = (expr);                                                     \
-        if (_e != cudaSuccess)                                                       \
+        if (_e != cudaSuccess) {                                                     \
+            cudaGetLastError(); /* clear it, so that it is not reported again */      \
             return ::dust::set_error(_e == cudaErrorMemoryAllocation ? DUST_ENOMEM     \
                                                                     : DUST_ECUDA,    \
                                      "%s failed: %s (%s:%d)", #expr,                 \
                                      cudaGetErrorString(_e), __FILE__, __LINE__);    \
+        }                                                                            \
     } while (0)
 
 // Kernels' entry points (host launchers), each returning a dust_status.

@@ -39,7 +39,8 @@
 namespace dust {
 namespace {
 
-constexpr int NTH = 256;      // emission threads per CTA
+constexpr int NTH = 256;      // emission threads per CTA (resident weights; 512 when streamed)
+constexpr int EMIT_STREAM_NTH = 512;  // threads of the streamed-weights emission CTA
 constexpr int SOLVE_TH = 128; // solve threads per CTA (one warp per cell)
 constexpr int NB_MAX = 4;     // grains per lane per pass in the solve, at most
 
@@ -323,15 +324,15 @@ __device__ __forceinline__ int emit_req_of(const EmitBatch &B, int64_t tile, int
 // Issue the cp.async copies of a tile's (1/T, n) pairs into the pair-major
 // shared layout [pair][grain][2 cells] (padding cells of a ragged tile read
 // the dummy values instead).
-template <bool MASS>
+template <bool MASS, int NT>
 __device__ __forceinline__ void prefetch_tile(const EmitReq &q, int64_t local_tile, float *dstTN, int TNP, int tid) {
     const int G8 = q.tb.G8, TC = q.TC;
     const int64_t c0 = local_tile * TC;
     const int nc = (int)((q.C - c0) < (int64_t)TC ? (q.C - c0) : (int64_t)TC);
-    // (c, g) of element i = tid + j NTH, advanced without a division per step
-    const int dc = NTH / G8, dg = NTH - dc * G8;
+    // (c, g) of element i = tid + j NT, advanced without a division per step
+    const int dc = NT / G8, dg = NT - dc * G8;
     int c = tid / G8, g = tid - c * G8;
-    for (int i = tid; i < TC * G8; i += NTH) {
+    for (int i = tid; i < TC * G8; i += NT) {
         if (MASS) {  // 1/T only: [pair][grain][2 cells] floats
             float *dst = dstTN + (size_t)(c >> 1) * TNP + 2 * g + (c & 1);
             if (c < nc) cp_async4(dst, reinterpret_cast<const float *>(q.prep) + (c0 + c) * G8 + g);
@@ -348,8 +349,8 @@ __device__ __forceinline__ void prefetch_tile(const EmitReq &q, int64_t local_ti
     cp_async_commit();
 }
 
-template <bool MASS>
-__global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBatch B) {
+template <bool MASS, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) k_emit(const __grid_constant__ EmitBatch B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x;
 
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
             ipair = okit ? tid - ikg * NP : NP;  // idle threads read the dummy pair row NP
             for (int b = 0; b < 2; ++b) {
                 float *dummy = reinterpret_cast<float *>(smem_raw + oTN) + (size_t)b * TNB + (size_t)NP * TNP;
-                for (int g = tid; g < G8; g += NTH) {
+                for (int g = tid; g < G8; g += NT) {
                     if (MASS) *reinterpret_cast<float2 *>(dummy + 2 * g) = make_float2(PAD_INV_T, PAD_INV_T);
                     else *reinterpret_cast<float4 *>(dummy + 4 * g) = make_float4(PAD_INV_T, 0.f, PAD_INV_T, 0.f);
                 }
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
             if (q.resident) {
                 const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
                 float4 *dst = reinterpret_cast<float4 *>(smem_raw);
-                for (int i = tid; i < NKG * 2 * G8; i += NTH) {
+                for (int i = tid; i < NKG * 2 * G8; i += NT) {
                     const int kg = i / (2 * G8), o = i - kg * 2 * G8;
                     dst[(size_t)kg * CST + o] = __ldg(src + i);
                 }
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
         __syncthreads();  // previous tile finished with shared memory
         if (pref != tile) {  // not prefetched (first tile of a request)
             buf = 0;
-            prefetch_tile<MASS>(q, lt, sTN0, TNP, tid);
+            prefetch_tile<MASS, NT>(q, lt, sTN0, TNP, tid);
         }
         cp_async_wait_all();
         __syncthreads();
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
         // prefetch the next tile of this request into the other buffer
         const int64_t nt = tile + gridDim.x;
         if (nt < B.ntiles && emit_req_of(B, nt, ri) == ri) {
-            prefetch_tile<MASS>(q, nt - q.tile_begin, sTN0 + (size_t)(buf ^ 1) * TNB, TNP, tid);
+            prefetch_tile<MASS, NT>(q, nt - q.tile_begin, sTN0 + (size_t)(buf ^ 1) * TNB, TNP, tid);
             pref = nt;
         } else {
             pref = -1;
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(NTH, 2) k_emit(const __grid_constant__ EmitBat
             if (!q.resident) {
                 __syncthreads();
                 const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
-                for (int i = tid; i < NKG * 2 * gn; i += NTH) {
+                for (int i = tid; i < NKG * 2 * gn; i += NT) {
                     const int kg = i / (2 * gn), o = i - kg * 2 * gn;
                     sC[(size_t)kg * CST + o] = __ldg(src + ((size_t)kg * G8 + g0) * 2 + o);
                 }
@@ -730,14 +731,24 @@ __global__ void __launch_bounds__(SOLVE_TH) k_resid(const __grid_constant__ Emit
 EmitPlan plan_emit(const dust_ctx *ctx, bool emit, bool mass) {
     const DevTables &tb = ctx->tb;
     EmitPlan p{};
-    const int NP = std::max(1, std::min(32, NTH / tb.NKG));  // cell pairs per tile
+    auto fixed_of = [&](int np) { return (size_t)2 * (np + 1) * ((mass ? 2 : 4) * tb.G8 + 4) * 4 + 64; };
+    int NP = std::max(1, std::min(32, NTH / tb.NKG));  // cell pairs per tile
     p.TC = 2 * NP;
+    p.nth = NTH;
     if (!emit) { p.GC = tb.G8; p.resident = 0; p.smem = 0; return p; }
     const size_t budget = 113 * 1024;  // two CTAs per SM
-    const size_t fixed = (size_t)2 * (NP + 1) * ((mass ? 2 : 4) * tb.G8 + 4) * 4 + 64;
-    const size_t full = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + fixed;
+    const size_t full = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + fixed_of(NP);
     if (full <= budget) { p.GC = tb.G8; p.resident = 1; p.smem = full; return p; }
-    const size_t avail = budget > fixed ? budget - fixed : 0;
+    // streamed weights: one CTA of 2 NTH threads per SM, twice the cells per
+    // tile and the whole shared memory for the grain chunks, so that each
+    // staged chunk serves more cells and fewer barriers are paid per cell
+    p.nth = EMIT_STREAM_NTH;
+    const size_t budget2 = ctx->smem_optin ? ctx->smem_optin - 1024 : budget;
+    NP = std::max(1, std::min(32, p.nth / tb.NKG));
+    while (NP > 1 && fixed_of(NP) + (size_t)tb.NKG * (2 * RG + 1) * 16 > budget2) --NP;  // room for a chunk
+    p.TC = 2 * NP;
+    const size_t fixed = fixed_of(NP);
+    const size_t avail = budget2 > fixed ? budget2 - fixed : 0;
     int gc = (int)((avail / ((size_t)tb.NKG * 16) - 1) / 2) / RG * RG;
     gc = std::max(RG, std::min(gc, tb.G8));
     p.GC = gc;
@@ -789,6 +800,8 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
     r.TC = p.TC;
     r.GC = p.GC;
     r.resident = p.resident;
+    r.nth = p.nth;
+    r.smem = (uint32_t)p.smem;
     r.mode = ((L || resid) ? EMIT_ON : 0) | (resid ? EMIT_RESID : 0) | (L ? EMIT_STORE_L : 0) |
              ((mass && (L || resid)) ? EMIT_MASS : 0);
 }
@@ -824,43 +837,56 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
     }
     if (between) DUST_CUDA_TRY(cudaEventRecord(between, st));
     // emission work lists: the requests that want L or resid, in order, one
-    // list (and launch) per form of the grain numbers
+    // list (and launch) per form of the grain numbers and CTA size
     for (int form = 0; form < 2; ++form) {
-        EmitBatch E;
-        E.nreq = 0;
-        int64_t tiles = 0;
-        for (int i = 0; i < B.nreq; ++i) {
-            if (!(B.req[i].mode & EMIT_ON) || ((B.req[i].mode & EMIT_MASS) != 0) != (form == 1)) continue;
-            EmitReq &r = E.req[E.nreq++];
-            r = B.req[i];
-            r.tile_begin = tiles;
-            tiles += (r.C + r.TC - 1) / r.TC;
-        }
-        E.ntiles = tiles;
-        E.ncells = 0;
-        bool resid = false;
-        for (int i = 0; i < E.nreq; ++i) {  // cells of the emission list, numbered afresh
-            E.req[i].cell_begin = E.ncells;
-            E.ncells += E.req[i].C;
-            resid = resid || (E.req[i].mode & EMIT_RESID);
-        }
-        if (tiles == 0) continue;
-        const void *kern = form ? reinterpret_cast<const void *>(k_emit<true>)
-                                : reinterpret_cast<const void *>(k_emit<false>);
-        DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0;
-        DUST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTH, smem));
-        per_sm = std::max(per_sm, 1);
-        const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * per_sm);
-        if (form) k_emit<true><<<(unsigned)grid, NTH, smem, st>>>(E);
-        else k_emit<false><<<(unsigned)grid, NTH, smem, st>>>(E);
-        DUST_CUDA_TRY(cudaGetLastError());
-        ++nl;
-        if (resid) {
-            const int64_t rgrid = std::min<int64_t>((E.ncells + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
-            k_resid<<<(unsigned)rgrid, SOLVE_TH, 0, st>>>(E);
+        for (int nt : {NTH, EMIT_STREAM_NTH}) {
+            EmitBatch E;
+            E.nreq = 0;
+            int64_t tiles = 0;
+            size_t lsmem = 0;
+            for (int i = 0; i < B.nreq; ++i) {
+                if (!(B.req[i].mode & EMIT_ON) || ((B.req[i].mode & EMIT_MASS) != 0) != (form == 1) ||
+                    B.req[i].nth != nt)
+                    continue;
+                EmitReq &r = E.req[E.nreq++];
+                r = B.req[i];
+                r.tile_begin = tiles;
+                tiles += (r.C + r.TC - 1) / r.TC;
+                lsmem = std::max(lsmem, (size_t)r.smem);
+            }
+            E.ntiles = tiles;
+            E.ncells = 0;
+            bool resid = false;
+            for (int i = 0; i < E.nreq; ++i) {  // cells of the emission list, numbered afresh
+                E.req[i].cell_begin = E.ncells;
+                E.ncells += E.req[i].C;
+                resid = resid || (E.req[i].mode & EMIT_RESID);
+            }
+            if (tiles == 0) continue;
+            const void *kern = form ? (nt == NTH ? reinterpret_cast<const void *>(k_emit<true, NTH>)
+                                                 : reinterpret_cast<const void *>(k_emit<true, EMIT_STREAM_NTH>))
+                                    : (nt == NTH ? reinterpret_cast<const void *>(k_emit<false, NTH>)
+                                                 : reinterpret_cast<const void *>(k_emit<false, EMIT_STREAM_NTH>));
+            DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
+            int per_sm = 0;
+            DUST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, lsmem));
+            per_sm = std::max(per_sm, 1);
+            const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)num_sms * per_sm);
+            if (form) {
+                if (nt == NTH) k_emit<true, NTH><<<grid, NTH, lsmem, st>>>(E);
+                else k_emit<true, EMIT_STREAM_NTH><<<grid, EMIT_STREAM_NTH, lsmem, st>>>(E);
+            } else {
+                if (nt == NTH) k_emit<false, NTH><<<grid, NTH, lsmem, st>>>(E);
+                else k_emit<false, EMIT_STREAM_NTH><<<grid, EMIT_STREAM_NTH, lsmem, st>>>(E);
+            }
             DUST_CUDA_TRY(cudaGetLastError());
             ++nl;
+            if (resid) {
+                const int64_t rgrid = std::min<int64_t>((E.ncells + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
+                k_resid<<<(unsigned)rgrid, SOLVE_TH, 0, st>>>(E);
+                DUST_CUDA_TRY(cudaGetLastError());
+                ++nl;
+            }
         }
     }
     if (nlaunch) *nlaunch = nl;
