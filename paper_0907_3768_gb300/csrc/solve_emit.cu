@@ -1,6 +1,8 @@
-// Kernel (b): equilibrium-temperature solve and emission SED, as two kernels
-// over a work list of requests (one request for dust_solve, many for the
-// server).
+// Kernel (b): equilibrium-temperature solve and emission SED.  For one
+// request whose emission weights fit in shared memory (dust_solve's usual
+// case) they run as one warp-specialized kernel, k_solve_emit; otherwise, and
+// for the server's work lists of many requests, as two kernels, k_solve and
+// k_emit.  All three give the same bits.
 //
 // k_solve — one warp per cell, many warps per SM (the solve is a chain of
 // dependent table lookups, so it wants parallelism, not shared memory):
@@ -23,7 +25,13 @@
 //   Chat sits in shared memory ([k-group][grain][2] float4, odd row stride),
 //   in grain chunks when it does not fit, as the paper staged sigma per block
 //   (Section 4.4); the next tile's (1/T, n) pairs stream in with cp.async
-//   while the current tile computes.
+//   while the current tile computes.  Resident weights: two CTAs of 256
+//   threads per SM; streamed weights: one CTA of 512 threads, twice the cells
+//   per tile and nearly all of shared memory for the chunks.
+// k_solve_emit — one CTA per SM: solver warps run k_solve's per-cell code on
+//   the tile after the one being emitted and leave its pairs in shared
+//   memory; emission warps take one cell x 8 wavelengths per thread with
+//   k_emit's arithmetic.  The latency-bound solve hides behind the emission.
 // resid = sum_k w_k L[c,k] / (4 pi sum_g n Pe) - 1: both sums are kept in
 //   float-float (error-free FP32 products and two-sums, ~48-bit) and their
 //   quotient is taken in float-float too, so the path has no FP64 arithmetic
