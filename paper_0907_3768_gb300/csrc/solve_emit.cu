@@ -51,6 +51,9 @@ constexpr int NTH = 256;      // emission threads per CTA (resident weights; 512
 constexpr int EMIT_STREAM_NTH = 512;  // threads of the streamed-weights emission CTA
 constexpr int SOLVE_TH = 128; // solve threads per CTA (one warp per cell)
 constexpr int NB_MAX = 4;     // grains per lane per pass in the solve, at most
+// temperature-only solve: CTAs of SOLVE_TH per SM (measured best: 8 at up to 3 grains per
+// lane, 6 at 4)
+constexpr int solve_tonly_ctas(int nb) { return nb >= 4 ? 6 : 8; }
 
 // Energy-balance residual emitted / (4 pi absorbed) - 1 of a cell, with
 // emitted = (h + l) 2^(m_c + Ew) and absorbed = (ah + al) 2^(m_c + Eg), all in
@@ -73,11 +76,11 @@ __device__ __forceinline__ float residual(float h, float l, float ah, float al, 
 
 // S and (when the emission follows) n of one pass of a cell: grains
 // gb + lane + 32 i.
-template <int NB>
+template <int NB, bool TONLY = false>
 __device__ __forceinline__ void load_pass(const EmitReq &q, int64_t cell, int gb, int lane, float (&s)[NB],
                                           float (&nv)[NB]) {
     const int G = q.tb.G;
-    const bool with_n = (q.mode & EMIT_ON) != 0 && !(q.mode & EMIT_MASS);
+    const bool with_n = !TONLY && (q.mode & EMIT_ON) != 0 && !(q.mode & EMIT_MASS);
     const float *Srow = q.S + cell * q.tb.Gs;
     const float *nrow = q.n + cell * G;
 #pragma unroll
@@ -96,12 +99,12 @@ __device__ __forceinline__ void load_pass(const EmitReq &q, int64_t cell, int gb
 // to `spairs` (G8 float2, or G8 floats in the dust-mass form) and `srec` in
 // shared memory as well as the record to q.cell.  s0 / n0: this cell's first
 // pass, loaded.
-template <int NB, bool SMEM>
+template <int NB, bool SMEM, bool TONLY = false>
 __device__ __forceinline__ void solve_cell(const EmitReq &q, int64_t cell, int lane, const float (&s0)[NB],
                                            const float (&n0)[NB], float2 *spairs, CellInfo *srec) {
     const DevTables &tb = q.tb;
     const int G = tb.G, G8 = tb.G8;
-    const bool emit = (q.mode & EMIT_ON) != 0, rs = (q.mode & EMIT_RESID) != 0;
+    const bool emit = !TONLY && (q.mode & EMIT_ON) != 0, rs = (q.mode & EMIT_RESID) != 0;
     const bool one = G8 <= 32 * NB;
     const bool mass = (q.mode & EMIT_MASS) != 0;
     int mc = 0;
@@ -126,7 +129,7 @@ __device__ __forceinline__ void solve_cell(const EmitReq &q, int64_t cell, int l
 #pragma unroll
             for (int i = 0; i < NB; ++i) { s[i] = s0[i]; nv[i] = n0[i]; }
         } else {
-            load_pass<NB>(q, cell, gb, lane, s, nv);
+            load_pass<NB, TONLY>(q, cell, gb, lane, s, nv);
         }
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
@@ -150,7 +153,7 @@ __device__ __forceinline__ void solve_cell(const EmitReq &q, int64_t cell, int l
             if (g < G) {
                 q.T[cell * G + g] = Tv[i];
                 if (q.flags) q.flags[cell * G + g] = (uint8_t)fl[i];
-                grain_out(tb, g, Tv[i], fl[i], s[i], nv[i], mc, mass, rs, invT, nn, ah, al);
+                if (!TONLY) grain_out(tb, g, Tv[i], fl[i], s[i], nv[i], mc, mass, rs, invT, nn, ah, al);
             }
             if (emit) {
                 if (SMEM) {
@@ -188,8 +191,11 @@ __device__ __forceinline__ void solve_cell(const EmitReq &q, int64_t cell, int l
 // m_c of max_g n comes from the registers of that pass.  The loop is
 // software-pipelined: the next cell's first-pass loads are issued before this
 // cell's two dependent table lookups, so their DRAM latency overlaps them.
-template <int NB>
-__global__ void __launch_bounds__(SOLVE_TH, NB >= 4 ? 5 : 6) k_solve(const __grid_constant__ EmitBatch B) {
+// TONLY: a launch whose requests all stop at T (no n, pairs or records), with
+// the emission's code compiled out and more CTAs per SM.
+template <int NB, bool TONLY>
+__global__ void __launch_bounds__(SOLVE_TH, TONLY ? solve_tonly_ctas(NB) : (NB >= 4 ? 5 : 6))
+    k_solve(const __grid_constant__ EmitBatch B) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * SOLVE_TH) >> 5;
     int64_t u = ((int64_t)blockIdx.x * SOLVE_TH + threadIdx.x) >> 5;  // this warp's first cell
@@ -197,7 +203,7 @@ __global__ void __launch_bounds__(SOLVE_TH, NB >= 4 ? 5 : 6) k_solve(const __gri
     int ri = 0;
     while (ri + 1 < B.nreq && u >= B.req[ri + 1].cell_begin) ++ri;
     float s0[NB], n0[NB];  // first pass of the current cell
-    load_pass<NB>(B.req[ri], u - B.req[ri].cell_begin, 0, lane, s0, n0);
+    load_pass<NB, TONLY>(B.req[ri], u - B.req[ri].cell_begin, 0, lane, s0, n0);
     for (;;) {
         const EmitReq &q = B.req[ri];
         const int64_t cell = u - q.cell_begin;
@@ -208,9 +214,9 @@ __global__ void __launch_bounds__(SOLVE_TH, NB >= 4 ? 5 : 6) k_solve(const __gri
         float s1[NB], n1[NB];
         if (more) {
             while (rn + 1 < B.nreq && un >= B.req[rn + 1].cell_begin) ++rn;
-            load_pass<NB>(B.req[rn], un - B.req[rn].cell_begin, 0, lane, s1, n1);
+            load_pass<NB, TONLY>(B.req[rn], un - B.req[rn].cell_begin, 0, lane, s1, n1);
         }
-        solve_cell<NB, false>(q, cell, lane, s0, n0, nullptr, nullptr);
+        solve_cell<NB, false, TONLY>(q, cell, lane, s0, n0, nullptr, nullptr);
         if (!more) break;
         u = un;
         ri = rn;
@@ -834,11 +840,22 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
         for (int i = 0; i < B.nreq; ++i) g8 = std::max(g8, B.req[i].tb.G8);
         const int nb = std::min(NB_MAX, (g8 + 31) / 32);
         const int64_t grid = std::min<int64_t>((cells * 32 + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
-        switch (nb) {
-            case 1: k_solve<1><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
-            case 2: k_solve<2><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
-            case 3: k_solve<3><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
-            default: k_solve<4><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+        bool tonly = true;
+        for (int i = 0; i < B.nreq; ++i) tonly = tonly && !(B.req[i].mode & EMIT_ON);
+        if (tonly) {
+            switch (nb) {
+                case 1: k_solve<1, true><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+                case 2: k_solve<2, true><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+                case 3: k_solve<3, true><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+                default: k_solve<4, true><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+            }
+        } else {
+            switch (nb) {
+                case 1: k_solve<1, false><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+                case 2: k_solve<2, false><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+                case 3: k_solve<3, false><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+                default: k_solve<4, false><<<(unsigned)grid, SOLVE_TH, 0, st>>>(B); break;
+            }
         }
         DUST_CUDA_TRY(cudaGetLastError());
         ++nl;
