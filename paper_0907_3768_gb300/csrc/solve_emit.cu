@@ -100,14 +100,16 @@ __device__ __forceinline__ void load_pass(const EmitReq &q, int64_t cell, int gb
 // shared memory as well as the record to q.cell.  s0 / n0: this cell's first
 // pass, loaded.
 // MF: the form of n when the caller knows it (0 general, 1 dust-mass), -1 to
-// read it from the request.
-template <int NB, bool SMEM, bool TONLY = false, int MF = -1>
+// read it from the request; EMIT: the emission is known to follow (the fused
+// kernel, whose launch has NB = ceil(G8 / 32), so a cell is one pass when
+// NB < NB_MAX).
+template <int NB, bool SMEM, bool TONLY = false, int MF = -1, bool EMIT = false>
 __device__ __forceinline__ void solve_cell(const EmitReq &q, int64_t cell, int lane, const float (&s0)[NB],
                                            const float (&n0)[NB], float2 *spairs, CellInfo *srec) {
     const DevTables &tb = q.tb;
     const int G = tb.G, G8 = tb.G8;
-    const bool emit = !TONLY && (q.mode & EMIT_ON) != 0, rs = (q.mode & EMIT_RESID) != 0;
-    const bool one = G8 <= 32 * NB;
+    const bool emit = EMIT || (!TONLY && (q.mode & EMIT_ON) != 0), rs = (q.mode & EMIT_RESID) != 0;
+    const bool one = (EMIT && NB < NB_MAX) || G8 <= 32 * NB;  // known at compile time in the fused kernel
     const bool mass = MF >= 0 ? MF == 1 : (q.mode & EMIT_MASS) != 0;
     int mc = 0;
     float ms = 0.f;  // dust-mass form: m_c = ms 2^mc
@@ -647,7 +649,7 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
                 const bool more = tn < ntiles && cn < TC && un < q.C;
                 float s1[NB], n1[NB];
                 if (more) load_pass<NB>(q, un, 0, lane, s1, n1);
-                solve_cell<NB, true, false, MASS ? 1 : 0>(q, cell, lane, s0, n0, reinterpret_cast<float2 *>(sP + ((size_t)b * TC + cl) * PS * PW),
+                solve_cell<NB, true, false, MASS ? 1 : 0, true>(q, cell, lane, s0, n0, reinterpret_cast<float2 *>(sP + ((size_t)b * TC + cl) * PS * PW),
                                      sI + b * TC + cl);
 #pragma unroll
                 for (int i = 0; i < NB; ++i) { s0[i] = s1[i]; n0[i] = n1[i]; }
