@@ -33,7 +33,7 @@ WORKLOAD = "2^18 cells x 200 wavelengths (0.09-1000 um) x 96 grains (3 species x
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the step's dominant
 # kernel on this workload, from one `ncu --set full` capture of that launch
 # (None until captured); to be retaken whenever that kernel changes
-DOMINANT_TRAFFIC_BYTES = 206.082816e6 + 338.131712e6
+DOMINANT_TRAFFIC_BYTES = 206.069504e6 + 337.327616e6
 
 
 def parse():
