@@ -12,6 +12,8 @@ from .workloads import (  # noqa: F401
     Workload,
     blackbody_shape,
     cross_sections,
+    fluctuating_selection,
+    heat_capacity_params,
     grain_table,
     make_workload,
     wavelength_grid,

@@ -251,3 +251,36 @@ def serve_requests(n_requests: int = 2000, n_snapshots: int = 64, rate_hz: float
     cells = np.exp(rng.uniform(lo, hi, n_requests)).astype(np.int64)
     return [dict(t=float(t[i]), snapshot=int(snaps[i]), K=int(ks[i]), G=int(gs[i]),
                  n_cells=int(cells[i])) for i in range(n_requests)]
+
+
+# ------------------------------------------------------- fluctuating grains
+#: Toy heat-capacity model of each species: an Einstein solid of N atoms with
+#: one characteristic temperature theta, E(T) = 3 N k_B theta / (exp(theta/T) - 1)
+#: (zero-point energy removed).  Bulk density [kg m^-3], mean mass per atom
+#: [kg] and theta [K].  The paper names no heat capacity; these give the
+#: enthalpy a small grain needs to be heated by one photon.
+_AMU = 1.66053906660e-27
+HEAT_CAPACITY = {
+    "silicate": {"rho": 3500.0, "m_atom": 24.0 * _AMU, "theta": 500.0},
+    "graphite": {"rho": 2240.0, "m_atom": 12.0 * _AMU, "theta": 900.0},
+    "pah": {"rho": 2240.0, "m_atom": 12.0 * _AMU, "theta": 900.0},
+}
+
+
+def heat_capacity_params(species: Sequence[str], sp_of_g: np.ndarray, a_of_g: np.ndarray):
+    """Atoms per grain and Einstein temperature of every grain g: the two
+    numbers of its enthalpy E(T) = 3 N k_B theta / (exp(theta / T) - 1)."""
+    N = np.empty(len(a_of_g))
+    theta = np.empty(len(a_of_g))
+    for g, (s, a) in enumerate(zip(sp_of_g, a_of_g)):
+        prm = HEAT_CAPACITY[species[s]]
+        N[g] = (4.0 / 3.0) * math.pi * a ** 3 * prm["rho"] / prm["m_atom"]
+        theta[g] = prm["theta"]
+    return N, theta
+
+
+def fluctuating_selection(a_of_g: np.ndarray, a_min: float = 0.5 * NM, a_max: float = 10.0 * NM):
+    """Indices of the grains treated as thermally fluctuating: radii in
+    [a_min, a_max] (grains much smaller hold too little energy for one UV
+    photon on any useful level grid, larger ones are near equilibrium)."""
+    return np.nonzero((a_of_g >= a_min) & (a_of_g <= a_max))[0]
