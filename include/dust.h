@@ -339,6 +339,47 @@ int dust_ctx_set_grain_sizes(dust_ctx *ctx, const double *a_m);
 int dust_solve_T_newton(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, float *T,
                         uint8_t *iters, uint8_t *flags, void *stream);
 
+/* ------------------------------------------------ fluctuating grains
+ * The temperature probability distribution of small grains, which a single
+ * photon heats far above their equilibrium temperature, and its emission.
+ * The paper names this calculation as its follow-up (Sections 1 and 6): per
+ * grain species and cell a transition-matrix problem between the grain's
+ * energy levels, after Guhathakurta & Draine (1989).  The method here:
+ *  - enthalpy of grain g: an Einstein solid of N_g atoms with characteristic
+ *    temperature theta_g, E_g(T) = 3 N_g k_B theta_g / (exp(theta_g/T) - 1);
+ *  - per (cell, grain) M levels E_j = j dE, E_top = (M-1) dE =
+ *    min(2 (E_g(T_eq) + h c / lambda_0), E_g(T_max)), T_eq the equilibrium
+ *    temperature of Eq. 7 and T_j = E_g^-1(E_j);
+ *  - heating: photons of lambda_k are absorbed at 4 pi w_k C[g,k] J[c,k] /
+ *    (h c / lambda_k) per second and move the grain to the two levels around
+ *    E_i + h c / lambda_k with the weights that keep the energy on average;
+ *    landings past the top level end on it (that energy is lost);
+ *  - cooling: j -> j-1 only, at 4 pi P_g(max(T_j, T_min)) / dE (P_g of Eq. 7);
+ *  - steady state: the probability flux up across each cut between two
+ *    levels equals the flux down, solved level by level from P_0;
+ *  - emission L[c,k] = 4 pi sum_g n[c,g] sum_j P_j C[g,k] B_k(T_j).
+ * FP32 throughout (the equilibrium temperature uses the context's tables
+ * with an FP32 absorbed power whatever the context's precision).
+ *
+ * dust_ctx_set_fluctuating: Gf >= 1 grains (indices into the context's
+ *   grains, host int[Gf]), their atom counts n_atoms[Gf] and Einstein
+ *   temperatures theta[Gf] (host FP64, > 0), and the number of levels M
+ *   (32, 64, 128, 256 or 512).  Synchronous; may be called again to replace
+ *   the set.  Needs K <= 2048.
+ * dust_solve_fluct: J [C x ld] device FP32 as in dust_solve; n [C x Gf]
+ *   device FP32, the numbers of the fluctuating grains (row stride Gf);
+ *   L [C x ld] device FP32 out or NULL, their emission (columns K..ld-1 not
+ *   written); P [C x Gf x M] device FP32 out or NULL, the normalised level
+ *   probabilities; dE [C x Gf] device FP32 out or NULL, the level spacing in
+ *   joules.  A cell whose J gives an invalid equilibrium solve (NaN,
+ *   negative, infinite) gets NaN in P, dE and L.  Asynchronous on `stream`.
+ *   DUST_EINVAL before dust_ctx_set_fluctuating, or when K and M need more
+ *   shared memory than one CTA has. */
+int dust_ctx_set_fluctuating(dust_ctx *ctx, int Gf, const int *grains, const double *n_atoms,
+                             const double *theta, int M);
+int dust_solve_fluct(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n, float *L,
+                     float *P, float *dE, void *stream);
+
 /* Failure-detection probe (no counterpart in the paper): one thread waits on
  * an mbarrier phase that nothing completes, through the same bounded wait the
  * tensor-core absorption kernel uses for every pipeline hand-off, with a

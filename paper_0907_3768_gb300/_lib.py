@@ -43,6 +43,8 @@ _SIGS = {
     "dust_ctx_profile": (_i, [_p, _i]),
     "dust_ctx_profile_read": (_i, [_p, _p, _p, _p, _p]),
     "dust_ctx_set_grain_sizes": (_i, [_p, _p]),
+    "dust_ctx_set_fluctuating": (_i, [_p, _i, _p, _p, _p, _i]),
+    "dust_solve_fluct": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p]),
     "dust_solve_T_newton": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p]),
     "dust_solve_coupled": (_i, [_p, _i64, _p, _i64, _p, _p, _i, _d, _p, _p, _p, _p, _p, _p, _p]),
     "dust_ctx_set_grain_numbers": (_i, [_p, _p]),
@@ -253,6 +255,14 @@ def dust_diag_wait_timeout(device, limit_ms):
 
 def dust_ctx_set_grain_sizes(ctx, a_m):
     return check(lib().dust_ctx_set_grain_sizes(ctx, a_m))
+
+
+def dust_ctx_set_fluctuating(ctx, Gf, grains, n_atoms, theta, M):
+    return check(lib().dust_ctx_set_fluctuating(ctx, Gf, grains, n_atoms, theta, M))
+
+
+def dust_solve_fluct(ctx, n_cells, J, ld, n, L, P, dE, stream):
+    return check(lib().dust_solve_fluct(ctx, n_cells, J, ld, n, L, P, dE, stream))
 
 
 def dust_solve_T_newton(ctx, n_cells, J, ld, T, iters, flags, stream):

@@ -209,6 +209,44 @@ class Context:
                                  out["iters"].data_ptr(), out["flags"].data_ptr(), sptr)
         return out
 
+    def set_fluctuating(self, grains, n_atoms, theta, M=128):
+        """Treat grains `grains` as thermally fluctuating: Einstein-solid
+        enthalpy with n_atoms atoms and characteristic temperature theta [K]
+        each, distributions on M levels."""
+        g = np.ascontiguousarray(grains, dtype=np.int32)
+        na = np.ascontiguousarray(n_atoms, dtype=np.float64)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        if g.ndim != 1 or na.shape != g.shape or th.shape != g.shape:
+            raise ValueError("grains, n_atoms and theta must be 1-D of one length")
+        _lib.dust_ctx_set_fluctuating(self.handle, len(g), g.ctypes.data, na.ctypes.data, th.ctypes.data, int(M))
+        self.fluct_Gf, self.fluct_M = len(g), int(M)
+
+    def solve_fluct(self, J, n_f, want_L=True, want_P=False, want_dE=True, out=None, stream=None):
+        """Level distributions and emission of the fluctuating grains: J as in
+        solve ([C, ld] rows), n_f [C, Gf] their numbers.  Returns dict L
+        [C, ld] (columns >= K unwritten), P [C, Gf, M], dE [C, Gf] (J)."""
+        C, ld = J.shape[0], J.stride(0)
+        if J.dtype != torch.float32 or J.stride(1) != 1 or not J.is_cuda or J.shape[1] < self.K:
+            raise ValueError("J must be a [C, >=K] float32 CUDA tensor with unit-stride rows")
+        Gf, M = self.fluct_Gf, self.fluct_M
+        if n_f.shape != (C, Gf) or n_f.dtype != torch.float32 or not n_f.is_contiguous() or not n_f.is_cuda:
+            raise ValueError(f"n_f must be a contiguous [C, {Gf}] float32 CUDA tensor")
+        dev = torch.device("cuda", self.device)
+        if out is None:
+            out = {}
+            if want_L:
+                out["L"] = torch.empty((C, ld), dtype=torch.float32, device=dev)
+            if want_P:
+                out["P"] = torch.empty((C, Gf, M), dtype=torch.float32, device=dev)
+            if want_dE:
+                out["dE"] = torch.empty((C, Gf), dtype=torch.float32, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        ptr = lambda k: out[k].data_ptr() if out.get(k) is not None else None
+        _lib.dust_solve_fluct(self.handle, C, J.data_ptr(), ld, n_f.data_ptr(), ptr("L"), ptr("P"), ptr("dE"), sptr)
+        return out
+
     def solve_host(self, J, n, T=None, L=None, resid=None, flags=None):
         """The hot path on host arrays (numpy or CPU tensors, ideally pinned);
         outputs are written into / returned as host arrays."""

@@ -413,6 +413,7 @@ void free_context(dust_ctx *ctx) {
     cudaFree(ctx->newton_grain);
     cudaFree(ctx->mass_mem);
     cudaFree(ctx->cpl);
+    cudaFree(ctx->fl_mem);
     auto &hs = ctx->hs;
     for (int i = 0; i < dust_ctx::NHB; ++i) {
         cudaFree(hs.J[i]); cudaFree(hs.n[i]); cudaFree(hs.T[i]); cudaFree(hs.L[i]);

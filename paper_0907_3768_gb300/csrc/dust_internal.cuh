@@ -191,6 +191,12 @@ struct dust_ctx {
     void *mass_mem = nullptr;
     size_t mass_bytes = 0;
     std::vector<double> lam_h, w_h, C_h;  // host copies of the context's inputs
+    // thermally fluctuating grains (dust_ctx_set_fluctuating): one device block
+    // with the photon energies, heating weights and grain constants
+    void *fl_mem = nullptr;
+    size_t fl_off[3] = {0, 0, 0};
+    int fl_Gf = 0, fl_M = 0;
+    float fl_eps_ref = 0.f;
     // working J, previous L and a change word of dust_solve_coupled
     void *cpl = nullptr;
     size_t cpl_bytes = 0;

@@ -1,0 +1,497 @@
+// Thermally fluctuating grains: the temperature probability distribution of
+// small grains and its emission.  The paper computes equilibrium temperatures
+// only and names this calculation as its follow-up (Sections 1 and 6): one
+// transition-matrix solve per grain species and cell, after Guhathakurta &
+// Draine (1989).
+//
+// Per (cell c, fluctuating grain g), all in FP32:
+//   1. equilibrium temperature T_eq (Eq. 7) from the context's table solve,
+//      with the absorbed power S = sum_k J W32 summed in FP32;
+//   2. level grid E_j = j dE, j < M, E_top = (M-1) dE =
+//      min(2 (E_g(T_eq) + eps_max), E_g(T_max)), with the Einstein enthalpy
+//      E_g(T) = c_g / (exp(theta_g / T) - 1) and eps_max = h c / lambda_0;
+//   3. upward rates: photons of lambda_k arrive at R_k = 4 pi w_k C J / eps_k
+//      and lift the grain by x_k = eps_k / dE levels, split between floor and
+//      ceiling so that the energy is kept on average; the rate of jumps of at
+//      least m levels from any level is
+//        Phi(m) = sum_k R_k clamp(x_k - m + 1, 0, 1)
+//      (landings past the top level end there), which is two prefix sums
+//      over the wavelengths (x_k falls as k rises):
+//        Phi(m) = Sh[kb(m)] + Sf[kb(m-1)] - Sf[kb(m)],  kb(m) = #{k : x_k >= m},
+//        Sh, Sf = exclusive prefix sums of R_k and R_k frac(x_k);
+//   4. thermal-continuous cooling j -> j-1 at 4 pi P_g(max(T_j, T_min)) / dE
+//      (P_g from the context's Hermite table);
+//   5. steady state by the balance of the probability fluxes across each cut
+//      between levels j-1 and j:  P_j = sum_{i<j} P_i Phi(j-i) / cool_j,
+//      computed forward: every new P_j adds P_j Phi(f-j) to the flux into
+//      each level f > j (one warp, lanes owning levels), so each step is
+//      M/32 FMAs per lane and one shuffle;
+//   6. emission L[c,k] = 4 pi sum_g n sum_j P_j C[g,k] B_k(T_j) (Eqs. 8-10),
+//      one MUFU ex2 per (level, wavelength), the level sum accumulated as a
+//      fraction with one reciprocal per 8 levels.
+//
+// Scaled units: energies in units of eps_ref = h c / lambda_0 (photon energies
+// eps~_k = lambda_0 / lambda_k <= 1); rates in units of 4 pi P_g(T_min) /
+// eps_ref 2^(f'_g + sigma), where Rhat[g,k] = w C / (eps~ P_g(T_min)) 2^-f'_g
+// <= 1 and sigma is the exponent of the cell's total sum_k J Rhat; the
+// cooling rate of level j is then 2^(t_j - f'_g - sigma) / dE~ with
+// t_j = log2(P_g(T_j) / P_g(T_min)) the table value.  The distribution and
+// the fluxes run in a common frame (a power of two), re-based exactly by a
+// power of two whenever a new value would pass 2^64.
+#include "dust_internal.cuh"
+#include "solve_core.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace dust {
+namespace {
+
+constexpr double H_PL = 6.62607015e-34;
+constexpr double C_LI = 299792458.0;
+constexpr double K_BO = 1.380649e-23;
+constexpr int FL_WARPS_MAX = 12;  // fluctuating grains handled at once per cell
+
+struct FlGrain {
+    int g;          // context grain index
+    float ctil;     // 3 N k_B theta / eps_ref
+    float theta;    // Einstein temperature [K]
+    float Etop;     // E_g(T_max) / eps_ref
+    float fprime;   // exponent f'_g of Rhat
+    float pad[3];
+};
+
+struct FlDev {
+    const float *epst;     // [K] eps_k / eps_ref
+    const float *Rhat;     // [Gf][K]
+    const FlGrain *gr;     // [Gf]
+    int Gf, M;
+};
+
+constexpr int FL_NPL = 4;  // emission: wavelength pairs per lane per pass (256 wavelengths a pass)
+
+__host__ __device__ constexpr int fl_k4(int K) { return (K + 3) & ~3; }
+__host__ __device__ constexpr int fl_kl(int K) { return (K + 255) & ~255; }
+// per-warp shared memory, every array 16-byte aligned:
+//   1/T [M], P [M], phi [M], kb [M], x [K4], Sh [K4+4], Sf [K4+4], Lw [KL]
+__host__ __device__ constexpr size_t fl_warp_floats(int K, int M) {
+    return (size_t)4 * M + 3 * (size_t)fl_k4(K) + 8 + fl_kl(K);
+}
+__host__ __device__ constexpr size_t fl_lw_offset(int K, int M) { return (size_t)4 * M + 3 * (size_t)fl_k4(K) + 8; }
+
+// One level's term for two wavelengths, folded into the group's fraction
+// N/D (sum of p t/(1-t) = N/D): N += t (p D - N), D -= t D.  The first level
+// of a group starts from N = p t, D = 1 - t.
+__device__ __forceinline__ void fl_term(float2 nax, float iT, float p, float2 &N, float2 &D) {
+    const float2 a = __fmul2_rn(nax, make_float2(iT, iT));
+    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+    const float2 e = __ffma2_rn(make_float2(p, p), D, make_float2(-N.x, -N.y));
+    N = __ffma2_rn(t, e, N);
+    D = __ffma2_rn(make_float2(-t.x, -t.y), D, D);
+}
+__device__ __forceinline__ void fl_first(float2 nax, float iT, float p, float2 &N, float2 &D) {
+    const float2 a = __fmul2_rn(nax, make_float2(iT, iT));
+    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+    N = __fmul2_rn(make_float2(p, p), t);
+    D = __ffma2_rn(make_float2(-t.x, -t.y), make_float2(1.f, 1.f), make_float2(1.f, 1.f));
+}
+
+// One CTA per cell; warp w takes fluctuating grains w, w + FW, ...
+template <int MR>
+__global__ void __launch_bounds__(FL_WARPS_MAX * 32) k_fluct(const DevTables tb, const FlDev fd, const float *W32,
+                                                             int Kw, int64_t C, const float *J, int64_t ld,
+                                                             const float *n, float *L, float *P, float *dE_out,
+                                                             float eps_ref) {
+    constexpr int M = MR * 32;
+    extern __shared__ float sm[];
+    const int K = tb.K, lane = threadIdx.x & 31, w = threadIdx.x >> 5, FW = blockDim.x >> 5;
+    const int64_t c = blockIdx.x;
+    if (c >= C) return;
+    const int Kp4 = (K + 3) & ~3;
+    float *Jc = sm;
+    float *base = sm + Kp4 + (size_t)w * fl_warp_floats(K, M);
+    float *iT = base, *Ps = iT + M, *phi = Ps + M;
+    int *kb = (int *)(phi + M);
+    float *x = (float *)(kb + M), *Sh = x + fl_k4(K), *Sf = Sh + fl_k4(K) + 4;
+    float *Lw = base + fl_lw_offset(K, M);
+    const unsigned full = 0xffffffffu;
+
+    for (int k = threadIdx.x; k < K; k += blockDim.x) Jc[k] = J[c * ld + k];
+    for (int k = lane; k < fl_kl(K); k += 32) Lw[k] = 0.f;
+    __syncthreads();
+
+    for (int q = w; q < fd.Gf; q += FW) {
+        const FlGrain gr = fd.gr[q];
+        const int g = gr.g;
+        // 1. equilibrium temperature of the cell's absorbed power (Eq. 7)
+        float s = 0.f;
+        for (int k = lane; k < K; k += 32) s = fmaf(Jc[k], __ldg(W32 + (size_t)g * Kw + k), s);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(full, s, o);
+        float Teq[1];
+        int fl[1];
+        {
+            const int gg[1] = {g};
+            const float ss[1] = {s};
+            const GrainParam gp = tb.gp[g];
+            const float4 gq[1] = {make_float4(gp.f, gp.tmax, gp.invdy, gp.pad)};
+            solve_batch<1>(tb, gg, ss, gq, Teq, fl);
+        }
+        const float nq = n[c * fd.Gf + q];
+        if (fl[0] == DUST_FLAG_INVALID) {  // NaN / negative / infinite field
+            const float qnan = __int_as_float(0x7fc00000);
+            if (P)
+                for (int j = lane; j < M; j += 32) P[((size_t)c * fd.Gf + q) * M + j] = qnan;
+            if (dE_out && lane == 0) dE_out[c * fd.Gf + q] = qnan;
+            for (int k = lane; k < K; k += 32) Lw[k] = qnan;
+            __syncwarp();
+            continue;
+        }
+        // 2. level grid
+        const float Eeq = gr.ctil / expm1f(gr.theta / Teq[0]);
+        const float Etop = fminf(2.f * (Eeq + 1.f), gr.Etop);
+        const float dEt = Etop / (float)(M - 1);
+        const float idE = 1.f / dEt;
+        // 3. photon landings and prefix sums over wavelength
+        float carry_h = 0.f, carry_f = 0.f;
+        for (int k0 = 0; k0 < K; k0 += 32) {
+            const int k = k0 + lane;
+            float h = 0.f, hf = 0.f;
+            if (k < K) {
+                const float xk = __ldg(fd.epst + k) * idE;
+                x[k] = xk;
+                h = Jc[k] * __ldg(fd.Rhat + (size_t)q * K + k);
+                hf = h * (xk - floorf(xk));
+            }
+            float ih = h, ihf = hf;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float a = __shfl_up_sync(full, ih, o), b = __shfl_up_sync(full, ihf, o);
+                if (lane >= o) { ih += a; ihf += b; }
+            }
+            if (k < K) {
+                Sh[k] = carry_h + (ih - h);
+                Sf[k] = carry_f + (ihf - hf);
+            }
+            carry_h += __shfl_sync(full, ih, 31);
+            carry_f += __shfl_sync(full, ihf, 31);
+        }
+        if (lane == 0) {
+            Sh[K] = carry_h;
+            Sf[K] = carry_f;
+        }
+        __syncwarp();
+        // sigma: Phi 2^-sigma <= 1 (the total rate bounds every Phi(m))
+        const int sigma = (carry_h > 0.f && carry_h < INFINITY) ? ilogbf(carry_h) + 1 : 0;
+        for (int m = lane; m < M; m += 32) {
+            int lo = 0, hi = K;  // x is non-increasing: count of x_k >= m
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (x[mid] >= (float)m) lo = mid + 1; else hi = mid;
+            }
+            kb[m] = lo;
+        }
+        __syncwarp();
+        for (int m = lane; m < M; m += 32) {
+            float v = 0.f;
+            if (m > 0) {
+                const int a = kb[m], b = kb[m - 1];
+                v = ldexpf(Sh[a] + (Sf[b] - Sf[a]), -sigma);
+            }
+            phi[m] = v;
+        }
+        // 4. levels owned by this lane: 1/T and the cooling factor
+        //    P_f = acc_f * mul_f * 2^ei_f (before the frame's 2^-S)
+        float acc[MR], mul[MR];
+        int ei[MR];
+#pragma unroll
+        for (int r = 0; r < MR; ++r) {
+            const int f = lane + 32 * r;
+            acc[r] = 0.f;
+            mul[r] = 0.f;
+            ei[r] = 0;
+            if (f == 0) {
+                iT[0] = PAD_INV_T;  // level 0 (T = 0) emits nothing: every t is 0
+                continue;
+            }
+            const float T = gr.theta / log1pf(gr.ctil / ((float)f * dEt));
+            iT[f] = 1.f / T;
+            const float u = log2f(fminf(fmaxf(T, tb.Tmin), tb.Tmax));
+            const float fj = (u - tb.log2Tmin) / tb.h2;
+            const int j0 = min(max((int)floorf(fj), 0), tb.NT - 2);
+            const float tau = fminf(fmaxf(fj - (float)j0, 0.f), 1.f);
+            const float4 f4 = __ldg(tb.fw + (size_t)g * (tb.NT - 1) + j0);
+            const float t = hermite(f4.x, f4.y, f4.z, f4.w, tau);
+            const float e = gr.fprime + (float)sigma - t;
+            const float fe = floorf(e);
+            ei[r] = (int)fe;
+            mul[r] = dEt * exp2f(e - fe);
+        }
+        __syncwarp();
+        // 5. forward cut-flux recursion from P_0 = 1
+        float pj = 1.f;
+        if (lane == 0) Ps[0] = 1.f;
+#pragma unroll
+        for (int r0 = 0; r0 < MR; ++r0) {
+            const int rn = r0 + 1 < MR ? r0 + 1 : r0;
+            for (int jj = 0; jj < 32; ++jj) {
+                const int j = 32 * r0 + jj;
+                if (j >= M - 1) break;
+#pragma unroll
+                for (int r = 0; r < MR; ++r) {
+                    const int d = lane + 32 * r - j;
+                    acc[r] = fmaf(phi[d > 0 ? d : 0], pj, acc[r]);
+                }
+                const bool nxt = jj == 31;
+                const float a = nxt ? acc[rn] * mul[rn] : acc[r0] * mul[r0];
+                const int ea = nxt ? ei[rn] : ei[r0];
+                const int own = (j + 1) & 31;
+                const float v = __shfl_sync(full, a, own);
+                const int E = __shfl_sync(full, ea, own);  // the frame is inside acc already
+                const int ve = (v > 0.f && v < INFINITY) ? ilogbf(v) : -1000;
+                if (ve + E > 64) {
+                    // re-base the frame so that this value is v 2^-ve in [1, 2)
+                    const int sh = ve + E;
+                    __syncwarp();  // the stored values of other lanes
+#pragma unroll
+                    for (int r = 0; r < MR; ++r) acc[r] = ldexpf(acc[r], -sh);
+                    for (int i = lane; i <= j; i += 32) Ps[i] = ldexpf(Ps[i], -sh);
+                    pj = ldexpf(v, -ve);
+                } else {
+                    pj = ldexpf(v, E);
+                }
+                if (lane == own) Ps[j + 1] = pj;
+            }
+        }
+        __syncwarp();
+        // normalisation
+        float z = 0.f;
+        for (int j = lane; j < M; j += 32) z += Ps[j];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) z += __shfl_xor_sync(full, z, o);
+        const float iz = 1.f / z;
+        for (int j = lane; j < M; j += 32) {
+            const float p = Ps[j] * iz;
+            Ps[j] = p;
+            if (P) P[((size_t)c * fd.Gf + q) * M + j] = p;
+        }
+        if (dE_out && lane == 0) dE_out[c * fd.Gf + q] = dEt * eps_ref;
+        __syncwarp();
+        // 6. emission of the distribution, accumulated per warp: each lane
+        //    carries FL_NPL wavelength pairs through the level sum at once
+        for (int k0 = 0; k0 < K; k0 += 64 * FL_NPL) {
+            float2 nx[FL_NPL], N[FL_NPL], D[FL_NPL], sum[FL_NPL];
+#pragma unroll
+            for (int u = 0; u < FL_NPL; ++u) {
+                const int k = k0 + 2 * (lane + 32 * u);
+                nx[u] = k < tb.Kp ? *reinterpret_cast<const float2 *>(tb.nax + k) : make_float2(-1e30f, -1e30f);
+                sum[u] = make_float2(0.f, 0.f);
+            }
+            for (int j0 = 0; j0 < M; j0 += 8) {
+                const float4 ta = *reinterpret_cast<const float4 *>(iT + j0);
+                const float4 tb4 = *reinterpret_cast<const float4 *>(iT + j0 + 4);
+                const float4 pa = *reinterpret_cast<const float4 *>(Ps + j0);
+                const float4 pb = *reinterpret_cast<const float4 *>(Ps + j0 + 4);
+                const float it[8] = {ta.x, ta.y, ta.z, ta.w, tb4.x, tb4.y, tb4.z, tb4.w};
+                const float pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+#pragma unroll
+                for (int u = 0; u < FL_NPL; ++u) fl_first(nx[u], it[0], pp[0], N[u], D[u]);
+#pragma unroll
+                for (int l = 1; l < 8; ++l)
+#pragma unroll
+                    for (int u = 0; u < FL_NPL; ++u) fl_term(nx[u], it[l], pp[l], N[u], D[u]);
+#pragma unroll
+                for (int u = 0; u < FL_NPL; ++u) {
+                    sum[u].x = fmaf(N[u].x, rcp_approx(D[u].x), sum[u].x);
+                    sum[u].y = fmaf(N[u].y, rcp_approx(D[u].y), sum[u].y);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < FL_NPL; ++u) {
+                const int k = k0 + 2 * (lane + 32 * u);
+                if (k < K) {
+                    const float2 ch = *reinterpret_cast<const float2 *>(
+                        tb.Chat + ((size_t)(k / KQ) * tb.G8 + g) * KQ + (k % KQ));
+                    Lw[k] = fmaf(nq * ch.x, sum[u].x, Lw[k]);
+                    Lw[k + 1] = fmaf(nq * ch.y, sum[u].y, Lw[k + 1]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    if (L) {
+        const float *L0 = sm + Kp4;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            float v = 0.f;
+            for (int i = 0; i < FW; ++i) v += L0[(size_t)i * fl_warp_floats(K, M) + fl_lw_offset(K, M) + k];
+            L[c * ld + k] = ldexpf(v, __ldg(tb.qexp + k));
+        }
+    }
+}
+
+template <int MR>
+cudaError_t launch_fluct_mr(const dust_ctx *ctx, const FlDev &fd, int64_t C, const float *J, int64_t ld,
+                            const float *n, float *L, float *P, float *dE, int FW, size_t smem, cudaStream_t st) {
+    auto kern = k_fluct<MR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)C, FW * 32, smem, st>>>(ctx->tb, fd, ctx->W32, ctx->Kw, C, J, ld, n, L, P, dE,
+                                             ctx->fl_eps_ref);
+    return cudaGetLastError();
+}
+
+int check_device_ptr(const dust_ctx *ctx, const void *p) {
+    if (!p) return DUST_OK;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(DUST_EINVAL, "an argument is not a CUDA pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return set_error(DUST_EINVAL, "J, n, L, P and dE must be device memory");
+    if (a.type == cudaMemoryTypeDevice && a.device != ctx->device)
+        return set_error(DUST_EINVAL, "an argument lives on device %d, the context on device %d", a.device,
+                         ctx->device);
+    return DUST_OK;
+}
+
+}  // namespace
+}  // namespace dust
+
+using namespace dust;
+
+extern "C" int dust_ctx_set_fluctuating(dust_ctx *ctx, int Gf, const int *grains, const double *n_atoms,
+                                        const double *theta, int M) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    if (Gf < 1 || Gf > ctx->G) return set_error(DUST_EINVAL, "Gf=%d outside [1, G=%d]", Gf, ctx->G);
+    if (!grains || !n_atoms || !theta) return set_error(DUST_EINVAL, "grains, n_atoms and theta must be non-NULL");
+    if (M != 32 && M != 64 && M != 128 && M != 256 && M != 512)
+        return set_error(DUST_EINVAL, "M=%d: levels must be 32, 64, 128, 256 or 512", M);
+    const int K = ctx->K;
+    if (K > 2048) return set_error(DUST_EINVAL, "K=%d > 2048", K);
+    const double lam0 = ctx->lam_h[0];
+    const double eps_ref = H_PL * C_LI / lam0;
+    std::vector<double> P0(ctx->G);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return set_error(DUST_ECUDA, "cudaGetDevice failed");
+    if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess)
+        return set_error(DUST_ECUDA, "cudaSetDevice(%d) failed", ctx->device);
+    int rc = DUST_OK;
+    [&] {
+        if (cudaMemcpy(P0.data(), ctx->tb.P0, sizeof(double) * ctx->G, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(DUST_ECUDA, "reading P_g(T_min) failed");
+            return;
+        }
+        std::vector<float> epst(K);
+        for (int k = 0; k < K; ++k) epst[k] = (float)(lam0 / ctx->lam_h[k]);
+        std::vector<float> Rhat((size_t)Gf * K);
+        std::vector<FlGrain> gr(Gf);
+        for (int q = 0; q < Gf; ++q) {
+            const int g = grains[q];
+            if (g < 0 || g >= ctx->G) { rc = set_error(DUST_EINVAL, "grains[%d]=%d outside [0, G)", q, g); return; }
+            if (!(n_atoms[q] > 0.0) || !(theta[q] > 0.0) || !std::isfinite(n_atoms[q]) || !std::isfinite(theta[q])) {
+                rc = set_error(DUST_EINVAL, "grain %d: n_atoms and theta must be finite and > 0", q);
+                return;
+            }
+            const double c = 3.0 * n_atoms[q] * K_BO * theta[q] / eps_ref;
+            const double Etop = c / std::expm1(theta[q] / ctx->Tmax);
+            double mx = 0.0;
+            std::vector<double> r(K);
+            for (int k = 0; k < K; ++k) {
+                r[k] = ctx->w_h[k] * ctx->C_h[(size_t)g * K + k] * (ctx->lam_h[k] / lam0) / P0[g];
+                mx = std::max(mx, r[k]);
+            }
+            if (!(mx > 0.0) || !std::isfinite(mx) || !std::isfinite(c) || !(Etop > 0.0) || !std::isfinite(Etop) ||
+                c > 1e30) {
+                rc = set_error(DUST_EINVAL, "grain %d: heating or enthalpy constants out of range", q);
+                return;
+            }
+            const int fp = (int)std::ceil(std::log2(mx));
+            for (int k = 0; k < K; ++k) Rhat[(size_t)q * K + k] = (float)std::ldexp(r[k], -fp);
+            gr[q] = FlGrain{g, (float)c, (float)theta[q], (float)Etop, (float)fp, {0.f, 0.f, 0.f}};
+        }
+        const size_t o_e = 0, o_r = (sizeof(float) * K + 255) & ~(size_t)255;
+        const size_t o_g = (o_r + sizeof(float) * Rhat.size() + 255) & ~(size_t)255;
+        const size_t bytes = o_g + sizeof(FlGrain) * Gf;
+        void *mem = nullptr;
+        if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(DUST_ENOMEM, "fluctuating-grain tables: cudaMalloc(%zu) failed", bytes);
+            return;
+        }
+        char *b = (char *)mem;
+        if (cudaMemcpy(b + o_e, epst.data(), sizeof(float) * K, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(b + o_r, Rhat.data(), sizeof(float) * Rhat.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(b + o_g, gr.data(), sizeof(FlGrain) * Gf, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(mem);
+            rc = set_error(DUST_ECUDA, "fluctuating-grain tables: copy failed");
+            return;
+        }
+        cudaFree(ctx->fl_mem);
+        ctx->fl_mem = mem;
+        ctx->fl_Gf = Gf;
+        ctx->fl_M = M;
+        ctx->fl_eps_ref = (float)eps_ref;
+        ctx->fl_off[0] = o_e;
+        ctx->fl_off[1] = o_r;
+        ctx->fl_off[2] = o_g;
+    }();
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return rc;
+}
+
+extern "C" int dust_solve_fluct(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n,
+                                float *L, float *P, float *dE, void *stream) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    if (!ctx->fl_mem) return set_error(DUST_EINVAL, "no fluctuating grains: call dust_ctx_set_fluctuating");
+    if (n_cells < 0) return set_error(DUST_EINVAL, "n_cells < 0");
+    if (ld < ctx->K) return set_error(DUST_EINVAL, "ld=%lld < K=%d", (long long)ld, ctx->K);
+    if (n_cells == 0) return DUST_OK;
+    if (!J || !n) return set_error(DUST_EINVAL, "J and n must be non-NULL");
+    if (n_cells > 0x7fffffffLL) return set_error(DUST_EINVAL, "n_cells too large for one launch");
+    for (const void *p : {(const void *)J, (const void *)n, (const void *)L, (const void *)P, (const void *)dE}) {
+        const int r = check_device_ptr(ctx, p);
+        if (r != DUST_OK) return r;
+    }
+    const int K = ctx->K, M = ctx->fl_M, Gf = ctx->fl_Gf;
+    const size_t per_warp = sizeof(float) * fl_warp_floats(K, M);
+    const size_t fixed = sizeof(float) * ((K + 3) & ~3);
+    const size_t budget = std::min<size_t>(ctx->smem_optin ? ctx->smem_optin : 232448, 200 * 1024);
+    int FW = std::min(Gf, FL_WARPS_MAX);
+    // balance: the fewest passes over the grains, then the fewest warps
+    const int passes = (Gf + FW - 1) / FW;
+    FW = (Gf + passes - 1) / passes;
+    while (FW > 1 && fixed + per_warp * FW > budget) --FW;
+    const size_t smem = fixed + per_warp * FW;
+    if (smem > budget) return set_error(DUST_EINVAL, "K=%d, M=%d need more shared memory than one CTA has", K, M);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return set_error(DUST_ECUDA, "cudaGetDevice failed");
+    if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess)
+        return set_error(DUST_ECUDA, "cudaSetDevice(%d) failed", ctx->device);
+    const char *b = (const char *)ctx->fl_mem;
+    FlDev fd{(const float *)(b + ctx->fl_off[0]), (const float *)(b + ctx->fl_off[1]),
+             (const FlGrain *)(b + ctx->fl_off[2]), Gf, M};
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    switch (M) {
+        case 32: e = launch_fluct_mr<1>(ctx, fd, n_cells, J, ld, n, L, P, dE, FW, smem, st); break;
+        case 64: e = launch_fluct_mr<2>(ctx, fd, n_cells, J, ld, n, L, P, dE, FW, smem, st); break;
+        case 128: e = launch_fluct_mr<4>(ctx, fd, n_cells, J, ld, n, L, P, dE, FW, smem, st); break;
+        case 256: e = launch_fluct_mr<8>(ctx, fd, n_cells, J, ld, n, L, P, dE, FW, smem, st); break;
+        default: e = launch_fluct_mr<16>(ctx, fd, n_cells, J, ld, n, L, P, dE, FW, smem, st); break;
+    }
+    int rc = DUST_OK;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rc = set_error(DUST_ECUDA, "fluctuating-grain kernel launch failed: %s", cudaGetErrorString(e));
+    } else {
+        ctx->launches += 1;
+    }
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return rc;
+}

@@ -73,6 +73,8 @@ def test_null_arguments(L):
     assert L.dust_solve_host(None, 10, None, 4, None, None, None, None, None) == _lib.DUST_EINVAL
     assert L.dust_ctx_set_precision(None, 0) == _lib.DUST_EINVAL
     assert L.dust_ctx_check(None, None) == _lib.DUST_EINVAL
+    assert L.dust_ctx_set_fluctuating(None, 1, None, None, None, 128) == _lib.DUST_EINVAL
+    assert L.dust_solve_fluct(None, 10, None, 4, None, None, None, None, None) == _lib.DUST_EINVAL
     L.dust_ctx_destroy(None)
 
 
