@@ -73,32 +73,37 @@ constexpr int FL_NPL = 4;  // emission: wavelength pairs per lane per pass (256 
 __host__ __device__ constexpr int fl_k4(int K) { return (K + 3) & ~3; }
 __host__ __device__ constexpr int fl_kl(int K) { return (K + 255) & ~255; }
 // per-warp shared memory, every array 16-byte aligned:
-//   1/T [M], P [M], phi [M], kb [M], x [K4], Sh [K4+4], Sf [K4+4], Lw [KL]
-__host__ __device__ constexpr size_t fl_warp_floats(int K, int M) {
-    return (size_t)4 * M + 3 * (size_t)fl_k4(K) + 8 + fl_kl(K);
-}
-__host__ __device__ constexpr size_t fl_lw_offset(int K, int M) { return (size_t)4 * M + 3 * (size_t)fl_k4(K) + 8; }
+//   (1/T, P) [M] pairs, M zeros then phi [M], kb [M], x [K4], Sh [K4+4],
+//   Sf [K4+4], Lw [KL]
+__host__ __device__ constexpr size_t fl_lw_offset(int K, int M) { return (size_t)5 * M + 3 * (size_t)fl_k4(K) + 8; }
+__host__ __device__ constexpr size_t fl_warp_floats(int K, int M) { return fl_lw_offset(K, M) + fl_kl(K); }
 
 // One level's term for two wavelengths, folded into the group's fraction
-// N/D (sum of p t/(1-t) = N/D): N += t (p D - N), D -= t D.  The first level
-// of a group starts from N = p t, D = 1 - t.
-__device__ __forceinline__ void fl_term(float2 nax, float iT, float p, float2 &N, float2 &D) {
+// (sum of p t/(1-t) = N/D), kept as Nn = -N and D:
+//   Nn -= t (p D + Nn),  D -= t D,
+// five packed operations with -t formed once.  The first level of a group
+// starts from Nn = -p t, D = 1 - t.
+__device__ __forceinline__ void fl_term(float2 nax, float iT, float p, float2 &Nn, float2 &D) {
     const float2 a = __fmul2_rn(nax, make_float2(iT, iT));
-    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
-    const float2 e = __ffma2_rn(make_float2(p, p), D, make_float2(-N.x, -N.y));
-    N = __ffma2_rn(t, e, N);
-    D = __ffma2_rn(make_float2(-t.x, -t.y), D, D);
+    const float2 tn = __fmul2_rn(make_float2(ex2_approx(a.x), ex2_approx(a.y)), make_float2(-1.f, -1.f));
+    const float2 e = __ffma2_rn(make_float2(p, p), D, Nn);
+    Nn = __ffma2_rn(tn, e, Nn);
+    D = __ffma2_rn(tn, D, D);
 }
-__device__ __forceinline__ void fl_first(float2 nax, float iT, float p, float2 &N, float2 &D) {
+__device__ __forceinline__ void fl_first(float2 nax, float iT, float p, float2 &Nn, float2 &D) {
     const float2 a = __fmul2_rn(nax, make_float2(iT, iT));
-    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
-    N = __fmul2_rn(make_float2(p, p), t);
-    D = __ffma2_rn(make_float2(-t.x, -t.y), make_float2(1.f, 1.f), make_float2(1.f, 1.f));
+    const float2 tn = __fmul2_rn(make_float2(ex2_approx(a.x), ex2_approx(a.y)), make_float2(-1.f, -1.f));
+    Nn = __fmul2_rn(make_float2(p, p), tn);
+    D = __ffma2_rn(tn, make_float2(1.f, 1.f), make_float2(1.f, 1.f));
 }
 
 // One CTA per cell; warp w takes fluctuating grains w, w + FW, ...
+// resident CTAs per SM the register budget is set for: the recursion is a
+// chain of dependent steps, so its latency is hidden by other warps
+constexpr int fl_min_ctas(int mr) { return mr <= 8 ? 2 : 1; }
+
 template <int MR>
-__global__ void __launch_bounds__(FL_WARPS_MAX * 32) k_fluct(const DevTables tb, const FlDev fd, const float *W32,
+__global__ void __launch_bounds__(FL_WARPS_MAX * 32, fl_min_ctas(MR)) k_fluct(const DevTables tb, const FlDev fd, const float *W32,
                                                              int Kw, int64_t C, const float *J, int64_t ld,
                                                              const float *n, float *L, float *P, float *dE_out,
                                                              float eps_ref) {
@@ -110,7 +115,8 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32) k_fluct(const DevTables tb,
     const int Kp4 = (K + 3) & ~3;
     float *Jc = sm;
     float *base = sm + Kp4 + (size_t)w * fl_warp_floats(K, M);
-    float *iT = base, *Ps = iT + M, *phi = Ps + M;
+    float2 *LT = reinterpret_cast<float2 *>(base);  // level j: (1/T_j, P_j)
+    float *phi = base + 3 * M;  // phi[-M..-1] = 0
     int *kb = (int *)(phi + M);
     float *x = (float *)(kb + M), *Sh = x + fl_k4(K), *Sf = Sh + fl_k4(K) + 4;
     float *Lw = base + fl_lw_offset(K, M);
@@ -118,6 +124,7 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32) k_fluct(const DevTables tb,
 
     for (int k = threadIdx.x; k < K; k += blockDim.x) Jc[k] = J[c * ld + k];
     for (int k = lane; k < fl_kl(K); k += 32) Lw[k] = 0.f;
+    for (int i = lane; i < M; i += 32) phi[i - M] = 0.f;
     __syncthreads();
 
     for (int q = w; q < fd.Gf; q += FW) {
@@ -200,22 +207,24 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32) k_fluct(const DevTables tb,
             }
             phi[m] = v;
         }
-        // 4. levels owned by this lane: 1/T and the cooling factor
-        //    P_f = acc_f * mul_f * 2^ei_f (before the frame's 2^-S)
-        float acc[MR], mul[MR];
+        // 4. levels owned by this lane: 1/T and the cooling factor,
+        //    P_f = acc_f mul_f 2^ei_f in the frame of acc; mulx = mul 2^ei
+        //    where that is a normal float (NaN otherwise: exact path)
+        float acc[MR], mul[MR], mulx[MR];
         int ei[MR];
 #pragma unroll
         for (int r = 0; r < MR; ++r) {
             const int f = lane + 32 * r;
             acc[r] = 0.f;
             mul[r] = 0.f;
+            mulx[r] = 0.f;
             ei[r] = 0;
             if (f == 0) {
-                iT[0] = PAD_INV_T;  // level 0 (T = 0) emits nothing: every t is 0
+                LT[0].x = PAD_INV_T;  // level 0 (T = 0) emits nothing: every t is 0
                 continue;
             }
             const float T = gr.theta / log1pf(gr.ctil / ((float)f * dEt));
-            iT[f] = 1.f / T;
+            LT[f].x = 1.f / T;
             const float u = log2f(fminf(fmaxf(T, tb.Tmin), tb.Tmax));
             const float fj = (u - tb.log2Tmin) / tb.h2;
             const int j0 = min(max((int)floorf(fj), 0), tb.NT - 2);
@@ -226,53 +235,58 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32) k_fluct(const DevTables tb,
             const float fe = floorf(e);
             ei[r] = (int)fe;
             mul[r] = dEt * exp2f(e - fe);
+            const float mx = ldexpf(mul[r], ei[r]);
+            mulx[r] = (mx >= 1.17549435e-38f && mx < INFINITY) ? mx : __int_as_float(0x7fc00000);
         }
         __syncwarp();
-        // 5. forward cut-flux recursion from P_0 = 1
+        // 5. forward cut-flux recursion from P_0 = 1: step j adds P_j's flux
+        //    to every level above j, then reads P_{j+1} off its owner lane
         float pj = 1.f;
-        if (lane == 0) Ps[0] = 1.f;
+        if (lane == 0) LT[0].y = 1.f;
+        const float *ph = phi + lane;
+#define FL_STEP(J, RS)                                                                        \
+    {                                                                                         \
+        const int j_ = (J);                                                                   \
+        _Pragma("unroll") for (int r = 0; r < MR; ++r) acc[r] = fmaf(ph[32 * r - j_], pj, acc[r]); \
+        const int own = (j_ + 1) & 31;                                                        \
+        const float cand = acc[RS] * mulx[RS];                                                \
+        const float v = __shfl_sync(full, cand < 0x1p64f ? cand : -1.f, own);                 \
+        if (v >= 0.f) {                                                                       \
+            pj = v;                                                                           \
+        } else { /* exact path: rescale the frame, or an exponent out of float range */       \
+            const float raw = __shfl_sync(full, acc[RS] * mul[RS], own);                      \
+            const int E = __shfl_sync(full, ei[RS], own);                                     \
+            const int ve = (raw > 0.f && raw < INFINITY) ? ilogbf(raw) : -1000;               \
+            if (ve + E > 64) {                                                                \
+                const int sh = ve + E;                                                        \
+                __syncwarp();                                                                 \
+                _Pragma("unroll") for (int r = 0; r < MR; ++r) acc[r] = ldexpf(acc[r], -sh);  \
+                for (int i = lane; i <= j_; i += 32) LT[i].y = ldexpf(LT[i].y, -sh);          \
+                pj = ldexpf(raw, -ve);                                                        \
+            } else {                                                                          \
+                pj = ldexpf(raw, E);                                                          \
+            }                                                                                 \
+        }                                                                                     \
+        if (lane == own) LT[j_ + 1].y = pj;                                                   \
+    }
 #pragma unroll
         for (int r0 = 0; r0 < MR; ++r0) {
-            const int rn = r0 + 1 < MR ? r0 + 1 : r0;
-            for (int jj = 0; jj < 32; ++jj) {
-                const int j = 32 * r0 + jj;
-                if (j >= M - 1) break;
-#pragma unroll
-                for (int r = 0; r < MR; ++r) {
-                    const int d = lane + 32 * r - j;
-                    acc[r] = fmaf(phi[d > 0 ? d : 0], pj, acc[r]);
-                }
-                const bool nxt = jj == 31;
-                const float a = nxt ? acc[rn] * mul[rn] : acc[r0] * mul[r0];
-                const int ea = nxt ? ei[rn] : ei[r0];
-                const int own = (j + 1) & 31;
-                const float v = __shfl_sync(full, a, own);
-                const int E = __shfl_sync(full, ea, own);  // the frame is inside acc already
-                const int ve = (v > 0.f && v < INFINITY) ? ilogbf(v) : -1000;
-                if (ve + E > 64) {
-                    // re-base the frame so that this value is v 2^-ve in [1, 2)
-                    const int sh = ve + E;
-                    __syncwarp();  // the stored values of other lanes
-#pragma unroll
-                    for (int r = 0; r < MR; ++r) acc[r] = ldexpf(acc[r], -sh);
-                    for (int i = lane; i <= j; i += 32) Ps[i] = ldexpf(Ps[i], -sh);
-                    pj = ldexpf(v, -ve);
-                } else {
-                    pj = ldexpf(v, E);
-                }
-                if (lane == own) Ps[j + 1] = pj;
-            }
+            // levels 32 r0 + 1 .. 32 r0 + 31 (this register of lanes 1..31)
+            for (int jj = 0; jj < 31; ++jj) FL_STEP(32 * r0 + jj, r0)
+            // level 32 (r0 + 1) (the next register of lane 0)
+            if (r0 + 1 < MR) FL_STEP(32 * r0 + 31, r0 + 1 < MR ? r0 + 1 : r0)
         }
+#undef FL_STEP
         __syncwarp();
         // normalisation
         float z = 0.f;
-        for (int j = lane; j < M; j += 32) z += Ps[j];
+        for (int j = lane; j < M; j += 32) z += LT[j].y;
 #pragma unroll
         for (int o = 16; o; o >>= 1) z += __shfl_xor_sync(full, z, o);
         const float iz = 1.f / z;
         for (int j = lane; j < M; j += 32) {
-            const float p = Ps[j] * iz;
-            Ps[j] = p;
+            const float p = LT[j].y * iz;
+            LT[j].y = p;
             if (P) P[((size_t)c * fd.Gf + q) * M + j] = p;
         }
         if (dE_out && lane == 0) dE_out[c * fd.Gf + q] = dEt * eps_ref;
@@ -288,22 +302,19 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32) k_fluct(const DevTables tb,
                 sum[u] = make_float2(0.f, 0.f);
             }
             for (int j0 = 0; j0 < M; j0 += 8) {
-                const float4 ta = *reinterpret_cast<const float4 *>(iT + j0);
-                const float4 tb4 = *reinterpret_cast<const float4 *>(iT + j0 + 4);
-                const float4 pa = *reinterpret_cast<const float4 *>(Ps + j0);
-                const float4 pb = *reinterpret_cast<const float4 *>(Ps + j0 + 4);
-                const float it[8] = {ta.x, ta.y, ta.z, ta.w, tb4.x, tb4.y, tb4.z, tb4.w};
-                const float pp[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+                float2 lt = LT[j0];
 #pragma unroll
-                for (int u = 0; u < FL_NPL; ++u) fl_first(nx[u], it[0], pp[0], N[u], D[u]);
+                for (int u = 0; u < FL_NPL; ++u) fl_first(nx[u], lt.x, lt.y, N[u], D[u]);
 #pragma unroll
-                for (int l = 1; l < 8; ++l)
+                for (int l = 1; l < 8; ++l) {
+                    lt = LT[j0 + l];
 #pragma unroll
-                    for (int u = 0; u < FL_NPL; ++u) fl_term(nx[u], it[l], pp[l], N[u], D[u]);
+                    for (int u = 0; u < FL_NPL; ++u) fl_term(nx[u], lt.x, lt.y, N[u], D[u]);
+                }
 #pragma unroll
                 for (int u = 0; u < FL_NPL; ++u) {
-                    sum[u].x = fmaf(N[u].x, rcp_approx(D[u].x), sum[u].x);
-                    sum[u].y = fmaf(N[u].y, rcp_approx(D[u].y), sum[u].y);
+                    sum[u].x = fmaf(-N[u].x, rcp_approx(D[u].x), sum[u].x);
+                    sum[u].y = fmaf(-N[u].y, rcp_approx(D[u].y), sum[u].y);
                 }
             }
 #pragma unroll
