@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-coupled", action="store_true", help="skip the self-absorbing (coupled) solve")
     ap.add_argument("--no-mass", action="store_true", help="skip the dust-mass form n[c,g] = n_g m_c")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused absorption + solve kernel")
+    ap.add_argument("--no-fluct", action="store_true", help="skip the thermally fluctuating grains")
+    ap.add_argument("--fluct-levels", type=int, default=128)
     ap.add_argument("--large-cells", type=int, default=1 << 20,
                     help="cells of the K=500, G=240 solve (the full case is 2^20; fewer for profiling captures)")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -359,6 +361,9 @@ def run_ours(args):
     if not args.no_coupled:
         line["coupled_self_absorption"] = coupled_solve(ctxs[main], wl, J, n, stream)
 
+    if not args.no_fluct:
+        line["fluctuating_grains"] = fluctuating(ctxs[main], wl, J, n, stream, args, world, ex2_rate,
+                                                 oracle_sample=rank == 0 and world == 1 and not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], line["err_vs_oracle"] = cpu_baseline(args, wl, res)
     del out_main, res, Jbuf, J, n
@@ -374,6 +379,83 @@ def run_ours(args):
         c.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def fluctuating(ctx, wl, J, n, stream, args, world, ex2_rate, oracle_sample):
+    """Temperature distributions of the workload's 0.5-10 nm grains (36 of
+    96) on M levels each, and their emission: one kernel per step over the
+    same resident J.  Planck terms counted are C Gf (M - 1) K; the oracle of
+    the same method is timed on a bounded sample of cells."""
+    import time
+
+    import numpy as np
+    import torch
+
+    import synth
+    from synth.workloads import heat_capacity_params
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from metrics import l_err
+
+    grains = synth.fluctuating_selection(wl.a_of_g)
+    N, th = heat_capacity_params(synth.CONFIGS[1]["species"], wl.sp_of_g, wl.a_of_g)
+    M = args.fluct_levels
+    ctx.set_fluctuating(grains, N[grains], th[grains], M)
+    C, K, Gf = J.shape[0], ctx.K, len(grains)
+    n_f = n[:, torch.from_numpy(grains).to(n.device)].contiguous()
+    out = ctx.solve_fluct(J, n_f, want_dE=False, stream=stream)
+    for _ in range(max(3, args.warmup) - 1):
+        ctx.solve_fluct(J, n_f, want_dE=False, out=out, stream=stream)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 10))
+    l0 = _lib_launches(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.solve_fluct(J, n_f, want_dE=False, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = (_lib_launches(ctx) - l0) / steps
+    assert ctx.check() == 0
+    terms = C * Gf * (M - 1) * K
+    r = {"workload": f"{C} cells x {K} wavelengths; {Gf} fluctuating grains of 0.5-10 nm (Einstein enthalpy) "
+                     f"x {M} levels; inputs resident in HBM",
+         "method": "per (cell, grain): level grid from the equilibrium T, photon-bin heating rates by two prefix "
+                   "sums, thermal-continuous cooling from the P_g table, cut-flux recursion, ex2 emission (FP32)",
+         "ms_per_step": round(ms, 3), "distributions_per_s": aggregate_rate(C * Gf, world, ms * 1e-3),
+         "planck_terms_per_s": aggregate_rate(terms, world, ms * 1e-3), "launches_per_step": launches,
+         "roofline": {"kernel": "k_fluct", "bound": "alu", "unit": "G Planck terms/s",
+                      "achieved": round(terms / (ms * 1e-3) / 1e9, 1), "peak": round(ex2_rate / 1e9, 1),
+                      "frac": round(terms / (ms * 1e-3) / ex2_rate, 4),
+                      "peak_source": "measured MUFU ex2.approx rate (dust_diag_throughput)"}}
+    if oracle_sample:
+        from oracle import fluct as ofl
+
+        cells = np.array([0, C // 3, (2 * C) // 3])[: max(1, min(3, C))]
+        t0 = time.perf_counter()
+        ref = ofl.run(wl.lam, wl.w, wl.C_abs, wl.J[cells], wl.n[cells][:, grains], grains, N[grains], th[grains], M,
+                      wl.T_min, wl.T_max, want_P=True)
+        sec = time.perf_counter() - t0
+        o = ctx.solve_fluct(J[torch.from_numpy(cells).to(J.device)], n_f[torch.from_numpy(cells).to(J.device)],
+                            want_P=True, stream=stream)
+        torch.cuda.synchronize()
+        P = o["P"].cpu().numpy()
+        r["cpu_baseline"] = {"value": len(cells) * Gf / sec, "unit": "distributions/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(cells)} cells x {Gf} grains x {M} levels (FP64 numpy, "
+                                       "transition matrix built one photon landing at a time)"}
+        r["err_vs_oracle"] = {"L_max": float(l_err(o["L"][:, :K].cpu().numpy(), ref["L"]).max()),
+                              "P_max_abs_over_peak": float((np.abs(P - ref["P"]) /
+                                                            ref["P"].max(axis=2, keepdims=True)).max()),
+                              "cells": len(cells)}
+    del out
+    return r
+
+
+def _lib_launches(ctx):
+    from paper_0907_3768_gb300 import _lib
+
+    return _lib.dust_ctx_launch_count(ctx.handle)
 
 
 def paper_newton_ablation(ctx, wl, J, stream, ms_table_T_only):

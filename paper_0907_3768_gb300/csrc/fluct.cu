@@ -98,6 +98,55 @@ __device__ __forceinline__ void fl_first(float2 nax, float iT, float p, float2 &
 }
 
 // One CTA per cell; warp w takes fluctuating grains w, w + FW, ...
+// Sum over levels [j0, j1) (a multiple of 8 long) of P_j t/(1-t) for NP
+// wavelength pairs at once: the level data is read once per level for all
+// pairs; one reciprocal per pair and 8 levels.
+template <int NP>
+__device__ __forceinline__ void fl_levels(const float2 *LT, int j0, int j1, const float2 (&nx)[NP],
+                                          float2 (&sum)[NP]) {
+    float2 Nn[NP], D[NP];
+    for (int jb = j0; jb < j1; jb += 8) {
+        float2 lt = LT[jb];
+#pragma unroll
+        for (int u = 0; u < NP; ++u) fl_first(nx[u], lt.x, lt.y, Nn[u], D[u]);
+#pragma unroll
+        for (int l = 1; l < 8; ++l) {
+            lt = LT[jb + l];
+#pragma unroll
+            for (int u = 0; u < NP; ++u) fl_term(nx[u], lt.x, lt.y, Nn[u], D[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < NP; ++u) {
+            sum[u].x = fmaf(-Nn[u].x, rcp_approx(D[u].x), sum[u].x);
+            sum[u].y = fmaf(-Nn[u].y, rcp_approx(D[u].y), sum[u].y);
+        }
+    }
+}
+
+// One pass over 64 NP wavelengths from k0: lane takes pairs k0 + 2 (lane + 32 u).
+template <int NP>
+__device__ __forceinline__ void fl_pass(const DevTables &tb, const float2 *LT, int M, int k0, int K, int g, float nq,
+                                        int lane, float *Lw) {
+    float2 nx[NP], sum[NP];
+#pragma unroll
+    for (int u = 0; u < NP; ++u) {
+        const int k = k0 + 2 * (lane + 32 * u);
+        nx[u] = k < tb.Kp ? *reinterpret_cast<const float2 *>(tb.nax + k) : make_float2(-1e30f, -1e30f);
+        sum[u] = make_float2(0.f, 0.f);
+    }
+    fl_levels<NP>(LT, 0, M, nx, sum);
+#pragma unroll
+    for (int u = 0; u < NP; ++u) {
+        const int k = k0 + 2 * (lane + 32 * u);
+        if (k < K) {
+            const float2 ch =
+                *reinterpret_cast<const float2 *>(tb.Chat + ((size_t)(k / KQ) * tb.G8 + g) * KQ + (k % KQ));
+            Lw[k] = fmaf(nq * ch.x, sum[u].x, Lw[k]);
+            Lw[k + 1] = fmaf(nq * ch.y, sum[u].y, Lw[k + 1]);
+        }
+    }
+}
+
 // resident CTAs per SM the register budget is set for: the recursion is a
 // chain of dependent steps, so its latency is hidden by other warps
 constexpr int fl_min_ctas(int mr) { return mr <= 8 ? 2 : 1; }
@@ -291,41 +340,36 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32, fl_min_ctas(MR)) k_fluct(co
         }
         if (dE_out && lane == 0) dE_out[c * fd.Gf + q] = dEt * eps_ref;
         __syncwarp();
-        // 6. emission of the distribution, accumulated per warp: each lane
-        //    carries FL_NPL wavelength pairs through the level sum at once
-        for (int k0 = 0; k0 < K; k0 += 64 * FL_NPL) {
-            float2 nx[FL_NPL], N[FL_NPL], D[FL_NPL], sum[FL_NPL];
-#pragma unroll
-            for (int u = 0; u < FL_NPL; ++u) {
-                const int k = k0 + 2 * (lane + 32 * u);
-                nx[u] = k < tb.Kp ? *reinterpret_cast<const float2 *>(tb.nax + k) : make_float2(-1e30f, -1e30f);
-                sum[u] = make_float2(0.f, 0.f);
+        // 6. emission of the distribution, accumulated per warp: whole passes
+        //    of 4 pairs per lane, then floor(rest / 64) pairs per lane, then
+        //    the last < 64 wavelengths with the levels split between lanes
+        int k0 = 0;
+        for (; k0 + 64 * FL_NPL <= K; k0 += 64 * FL_NPL) fl_pass<FL_NPL>(tb, LT, M, k0, K, g, nq, lane, Lw);
+        switch ((K - k0) / 64) {
+            case 3: fl_pass<3>(tb, LT, M, k0, K, g, nq, lane, Lw); k0 += 192; break;
+            case 2: fl_pass<2>(tb, LT, M, k0, K, g, nq, lane, Lw); k0 += 128; break;
+            case 1: fl_pass<1>(tb, LT, M, k0, K, g, nq, lane, Lw); k0 += 64; break;
+            default: break;
+        }
+        if (k0 < K) {
+            const int np = (K - k0 + 1) / 2;  // <= 32 pairs
+            int lp = 32;                        // lanes per pair: a power of two, >= 8 levels each
+            while (lp > 1 && (lp * np > 32 || M / lp < 8)) lp >>= 1;
+            const int pr = lane / lp, ch0 = lane % lp, nl = M / lp;
+            const int k = k0 + 2 * pr;
+            float2 nx[1] = {pr < np && k < tb.Kp ? *reinterpret_cast<const float2 *>(tb.nax + k)
+                                                 : make_float2(-1e30f, -1e30f)};
+            float2 sum[1] = {make_float2(0.f, 0.f)};
+            fl_levels<1>(LT, ch0 * nl, ch0 * nl + nl, nx, sum);
+            for (int o = 1; o < lp; o <<= 1) {
+                sum[0].x += __shfl_xor_sync(full, sum[0].x, o);
+                sum[0].y += __shfl_xor_sync(full, sum[0].y, o);
             }
-            for (int j0 = 0; j0 < M; j0 += 8) {
-                float2 lt = LT[j0];
-#pragma unroll
-                for (int u = 0; u < FL_NPL; ++u) fl_first(nx[u], lt.x, lt.y, N[u], D[u]);
-#pragma unroll
-                for (int l = 1; l < 8; ++l) {
-                    lt = LT[j0 + l];
-#pragma unroll
-                    for (int u = 0; u < FL_NPL; ++u) fl_term(nx[u], lt.x, lt.y, N[u], D[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < FL_NPL; ++u) {
-                    sum[u].x = fmaf(-N[u].x, rcp_approx(D[u].x), sum[u].x);
-                    sum[u].y = fmaf(-N[u].y, rcp_approx(D[u].y), sum[u].y);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < FL_NPL; ++u) {
-                const int k = k0 + 2 * (lane + 32 * u);
-                if (k < K) {
-                    const float2 ch = *reinterpret_cast<const float2 *>(
-                        tb.Chat + ((size_t)(k / KQ) * tb.G8 + g) * KQ + (k % KQ));
-                    Lw[k] = fmaf(nq * ch.x, sum[u].x, Lw[k]);
-                    Lw[k + 1] = fmaf(nq * ch.y, sum[u].y, Lw[k + 1]);
-                }
+            if (ch0 == 0 && pr < np && k < K) {
+                const float2 c2 =
+                    *reinterpret_cast<const float2 *>(tb.Chat + ((size_t)(k / KQ) * tb.G8 + g) * KQ + (k % KQ));
+                Lw[k] = fmaf(nq * c2.x, sum[0].x, Lw[k]);
+                Lw[k + 1] = fmaf(nq * c2.y, sum[0].y, Lw[k + 1]);
             }
         }
         __syncwarp();

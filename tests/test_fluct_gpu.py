@@ -74,6 +74,18 @@ def test_fluct_matches_oracle(M):
     _compare(g, ref, wl.K)
 
 
+@pytest.mark.parametrize("K,M", [(300, 64), (48, 32), (130, 256)])
+def test_fluct_wavelength_passes(K, M):
+    """Whole 256-wavelength passes, 1-3 pairs per lane, and the last < 64
+    wavelengths with the levels split between 1 to 8 lanes."""
+    wl, N, th = _workload(8, K=K, n_sizes=3)
+    grains = np.arange(wl.G)
+    g = _gpu(wl, grains, N, th, M)
+    ref = ofl.run(wl.lam, wl.w, wl.C_abs, wl.J, wl.n[:, grains], grains, N[grains], th[grains], M,
+                  wl.T_min, wl.T_max)
+    _compare(g, ref, wl.K)
+
+
 def test_fluct_many_levels_and_ragged_grain_count():
     """M = 512 (16 levels per lane), 13 grains over 7 warps, odd K."""
     wl, N, th = _workload(6, K=37, n_sizes=7, species=("silicate", "graphite"))
