@@ -50,7 +50,6 @@ namespace {
 constexpr double H_PL = 6.62607015e-34;
 constexpr double C_LI = 299792458.0;
 constexpr double K_BO = 1.380649e-23;
-constexpr int FL_WARPS_MAX = 12;  // fluctuating grains handled at once per cell
 
 struct FlGrain {
     int g;          // context grain index
@@ -76,7 +75,11 @@ __host__ __device__ constexpr int fl_kl(int K) { return (K + 255) & ~255; }
 //   (1/T, P) [M] pairs, M zeros then phi [M], kb [M], x [K4], Sh [K4+4],
 //   Sf [K4+4], Lw [KL]
 __host__ __device__ constexpr size_t fl_lw_offset(int K, int M) { return (size_t)5 * M + 3 * (size_t)fl_k4(K) + 8; }
-__host__ __device__ constexpr size_t fl_warp_floats(int K, int M) { return fl_lw_offset(K, M) + fl_kl(K); }
+// slot stride: 16 more than a multiple of 32 floats, so that the two problems
+// of a warp (one per half) sit 16 banks apart
+__host__ __device__ constexpr size_t fl_warp_floats(int K, int M) {
+    return ((fl_lw_offset(K, M) + fl_kl(K) + 31) & ~(size_t)31) + 16;
+}
 
 // One level's term for two wavelengths, folded into the group's fraction
 // (sum of p t/(1-t) = N/D), kept as Nn = -N and D:
@@ -98,20 +101,21 @@ __device__ __forceinline__ void fl_first(float2 nax, float iT, float p, float2 &
 }
 
 // One CTA per cell; warp w takes fluctuating grains w, w + FW, ...
-// Sum over levels [j0, j1) (a multiple of 8 long) of P_j t/(1-t) for NP
-// wavelength pairs at once: the level data is read once per level for all
+// Sum over the levels j0 + s i, i < n (n a multiple of 8), of P_j t/(1-t) for
+// NP wavelength pairs at once: the level data is read once per level for all
 // pairs; one reciprocal per pair and 8 levels.
 template <int NP>
-__device__ __forceinline__ void fl_levels(const float2 *LT, int j0, int j1, const float2 (&nx)[NP],
+__device__ __forceinline__ void fl_levels(const float2 *LT, int j0, int s, int n, const float2 (&nx)[NP],
                                           float2 (&sum)[NP]) {
     float2 Nn[NP], D[NP];
-    for (int jb = j0; jb < j1; jb += 8) {
-        float2 lt = LT[jb];
+    for (int ib = 0; ib < n; ib += 8) {
+        const float2 *lp = LT + j0 + s * ib;
+        float2 lt = lp[0];
 #pragma unroll
         for (int u = 0; u < NP; ++u) fl_first(nx[u], lt.x, lt.y, Nn[u], D[u]);
 #pragma unroll
         for (int l = 1; l < 8; ++l) {
-            lt = LT[jb + l];
+            lt = lp[s * l];
 #pragma unroll
             for (int u = 0; u < NP; ++u) fl_term(nx[u], lt.x, lt.y, Nn[u], D[u]);
         }
@@ -123,21 +127,22 @@ __device__ __forceinline__ void fl_levels(const float2 *LT, int j0, int j1, cons
     }
 }
 
-// One pass over 64 NP wavelengths from k0: lane takes pairs k0 + 2 (lane + 32 u).
-template <int NP>
+// One pass over 2 LW NP wavelengths from k0: lane hl of the problem takes the
+// pairs k0 + 2 (hl + LW u).
+template <int NP, int LW>
 __device__ __forceinline__ void fl_pass(const DevTables &tb, const float2 *LT, int M, int k0, int K, int g, float nq,
-                                        int lane, float *Lw) {
+                                        int hl, float *Lw) {
     float2 nx[NP], sum[NP];
 #pragma unroll
     for (int u = 0; u < NP; ++u) {
-        const int k = k0 + 2 * (lane + 32 * u);
+        const int k = k0 + 2 * (hl + LW * u);
         nx[u] = k < tb.Kp ? *reinterpret_cast<const float2 *>(tb.nax + k) : make_float2(-1e30f, -1e30f);
         sum[u] = make_float2(0.f, 0.f);
     }
-    fl_levels<NP>(LT, 0, M, nx, sum);
+    fl_levels<NP>(LT, 0, 1, M, nx, sum);
 #pragma unroll
     for (int u = 0; u < NP; ++u) {
-        const int k = k0 + 2 * (lane + 32 * u);
+        const int k = k0 + 2 * (hl + LW * u);
         if (k < K) {
             const float2 ch =
                 *reinterpret_cast<const float2 *>(tb.Chat + ((size_t)(k / KQ) * tb.G8 + g) * KQ + (k % KQ));
@@ -147,43 +152,53 @@ __device__ __forceinline__ void fl_pass(const DevTables &tb, const float2 *LT, i
     }
 }
 
-// resident CTAs per SM the register budget is set for: the recursion is a
-// chain of dependent steps, so its latency is hidden by other warps
-constexpr int fl_min_ctas(int mr) { return mr <= 8 ? 2 : 1; }
+// Lanes per (cell, grain) problem: 16 up to 64 levels (two problems per
+// warp, whose recursion chains overlap in one instruction stream; measured
+// 6 % faster at M = 64), 32 above (measured faster from M = 128 on, where a
+// half-warp carries 8 or more levels per lane).  Every collective below is
+// scoped to the problem's lanes (mask and width), so the two halves of a
+// warp may also diverge.
+__host__ __device__ constexpr int fl_lanes(int M) { return M <= 64 ? 16 : 32; }
+// threads per CTA at most: 8 warps of two problems, or 12 warps of one
+__host__ __device__ constexpr int fl_threads(int M) { return fl_lanes(M) == 16 ? 256 : 384; }
 
-template <int MR>
-__global__ void __launch_bounds__(FL_WARPS_MAX * 32, fl_min_ctas(MR)) k_fluct(const DevTables tb, const FlDev fd, const float *W32,
-                                                             int Kw, int64_t C, const float *J, int64_t ld,
-                                                             const float *n, float *L, float *P, float *dE_out,
-                                                             float eps_ref) {
-    constexpr int M = MR * 32;
+template <int M>
+__global__ void __launch_bounds__(fl_threads(M), M <= 256 ? 2 : 1) k_fluct(const DevTables tb, const FlDev fd,
+                                                                      const float *W32, int Kw, int64_t C,
+                                                                      const float *J, int64_t ld, const float *n,
+                                                                      float *L, float *P, float *dE_out,
+                                                                      float eps_ref) {
+    constexpr int LW = fl_lanes(M);
+    constexpr int MR = M / LW;    // levels per lane
+    constexpr int PPW = 32 / LW;  // problems per warp
     extern __shared__ float sm[];
-    const int K = tb.K, lane = threadIdx.x & 31, w = threadIdx.x >> 5, FW = blockDim.x >> 5;
+    const int K = tb.K, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int hl = lane % LW, slot = w * PPW + lane / LW, NPB = (blockDim.x >> 5) * PPW;
+    const unsigned hmask = LW == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
     const int64_t c = blockIdx.x;
     if (c >= C) return;
     const int Kp4 = (K + 3) & ~3;
     float *Jc = sm;
-    float *base = sm + Kp4 + (size_t)w * fl_warp_floats(K, M);
+    float *base = sm + Kp4 + (size_t)slot * fl_warp_floats(K, M);
     float2 *LT = reinterpret_cast<float2 *>(base);  // level j: (1/T_j, P_j)
-    float *phi = base + 3 * M;  // phi[-M..-1] = 0
+    float *phi = base + 3 * M;                      // phi[-M..-1] = 0
     int *kb = (int *)(phi + M);
     float *x = (float *)(kb + M), *Sh = x + fl_k4(K), *Sf = Sh + fl_k4(K) + 4;
     float *Lw = base + fl_lw_offset(K, M);
-    const unsigned full = 0xffffffffu;
 
     for (int k = threadIdx.x; k < K; k += blockDim.x) Jc[k] = J[c * ld + k];
-    for (int k = lane; k < fl_kl(K); k += 32) Lw[k] = 0.f;
-    for (int i = lane; i < M; i += 32) phi[i - M] = 0.f;
+    for (int k = hl; k < fl_kl(K); k += LW) Lw[k] = 0.f;
+    for (int i = hl; i < M; i += LW) phi[i - M] = 0.f;
     __syncthreads();
 
-    for (int q = w; q < fd.Gf; q += FW) {
+    for (int q = slot; q < fd.Gf; q += NPB) {
         const FlGrain gr = fd.gr[q];
         const int g = gr.g;
         // 1. equilibrium temperature of the cell's absorbed power (Eq. 7)
         float s = 0.f;
-        for (int k = lane; k < K; k += 32) s = fmaf(Jc[k], __ldg(W32 + (size_t)g * Kw + k), s);
+        for (int k = hl; k < K; k += LW) s = fmaf(Jc[k], __ldg(W32 + (size_t)g * Kw + k), s);
 #pragma unroll
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(full, s, o);
+        for (int o = LW / 2; o; o >>= 1) s += __shfl_xor_sync(hmask, s, o);
         float Teq[1];
         int fl[1];
         {
@@ -197,10 +212,10 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32, fl_min_ctas(MR)) k_fluct(co
         if (fl[0] == DUST_FLAG_INVALID) {  // NaN / negative / infinite field
             const float qnan = __int_as_float(0x7fc00000);
             if (P)
-                for (int j = lane; j < M; j += 32) P[((size_t)c * fd.Gf + q) * M + j] = qnan;
-            if (dE_out && lane == 0) dE_out[c * fd.Gf + q] = qnan;
-            for (int k = lane; k < K; k += 32) Lw[k] = qnan;
-            __syncwarp();
+                for (int j = hl; j < M; j += LW) P[((size_t)c * fd.Gf + q) * M + j] = qnan;
+            if (dE_out && hl == 0) dE_out[c * fd.Gf + q] = qnan;
+            for (int k = hl; k < K; k += LW) Lw[k] = qnan;
+            __syncwarp(hmask);
             continue;
         }
         // 2. level grid
@@ -210,8 +225,8 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32, fl_min_ctas(MR)) k_fluct(co
         const float idE = 1.f / dEt;
         // 3. photon landings and prefix sums over wavelength
         float carry_h = 0.f, carry_f = 0.f;
-        for (int k0 = 0; k0 < K; k0 += 32) {
-            const int k = k0 + lane;
+        for (int k0 = 0; k0 < K; k0 += LW) {
+            const int k = k0 + hl;
             float h = 0.f, hf = 0.f;
             if (k < K) {
                 const float xk = __ldg(fd.epst + k) * idE;
@@ -221,25 +236,25 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32, fl_min_ctas(MR)) k_fluct(co
             }
             float ih = h, ihf = hf;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float a = __shfl_up_sync(full, ih, o), b = __shfl_up_sync(full, ihf, o);
-                if (lane >= o) { ih += a; ihf += b; }
+            for (int o = 1; o < LW; o <<= 1) {
+                const float a = __shfl_up_sync(hmask, ih, o, LW), b = __shfl_up_sync(hmask, ihf, o, LW);
+                if (hl >= o) { ih += a; ihf += b; }
             }
             if (k < K) {
                 Sh[k] = carry_h + (ih - h);
                 Sf[k] = carry_f + (ihf - hf);
             }
-            carry_h += __shfl_sync(full, ih, 31);
-            carry_f += __shfl_sync(full, ihf, 31);
+            carry_h += __shfl_sync(hmask, ih, LW - 1, LW);
+            carry_f += __shfl_sync(hmask, ihf, LW - 1, LW);
         }
-        if (lane == 0) {
+        if (hl == 0) {
             Sh[K] = carry_h;
             Sf[K] = carry_f;
         }
-        __syncwarp();
+        __syncwarp(hmask);
         // sigma: Phi 2^-sigma <= 1 (the total rate bounds every Phi(m))
         const int sigma = (carry_h > 0.f && carry_h < INFINITY) ? ilogbf(carry_h) + 1 : 0;
-        for (int m = lane; m < M; m += 32) {
+        for (int m = hl; m < M; m += LW) {
             int lo = 0, hi = K;  // x is non-increasing: count of x_k >= m
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
@@ -247,8 +262,8 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32, fl_min_ctas(MR)) k_fluct(co
             }
             kb[m] = lo;
         }
-        __syncwarp();
-        for (int m = lane; m < M; m += 32) {
+        __syncwarp(hmask);
+        for (int m = hl; m < M; m += LW) {
             float v = 0.f;
             if (m > 0) {
                 const int a = kb[m], b = kb[m - 1];
@@ -263,7 +278,7 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32, fl_min_ctas(MR)) k_fluct(co
         int ei[MR];
 #pragma unroll
         for (int r = 0; r < MR; ++r) {
-            const int f = lane + 32 * r;
+            const int f = hl + LW * r;
             acc[r] = 0.f;
             mul[r] = 0.f;
             mulx[r] = 0.f;
@@ -287,83 +302,83 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32, fl_min_ctas(MR)) k_fluct(co
             const float mx = ldexpf(mul[r], ei[r]);
             mulx[r] = (mx >= 1.17549435e-38f && mx < INFINITY) ? mx : __int_as_float(0x7fc00000);
         }
-        __syncwarp();
+        __syncwarp(hmask);
         // 5. forward cut-flux recursion from P_0 = 1: step j adds P_j's flux
         //    to every level above j, then reads P_{j+1} off its owner lane
         float pj = 1.f;
-        if (lane == 0) LT[0].y = 1.f;
-        const float *ph = phi + lane;
+        if (hl == 0) LT[0].y = 1.f;
+        const float *ph = phi + hl;
 #define FL_STEP(J, RS)                                                                        \
     {                                                                                         \
         const int j_ = (J);                                                                   \
-        _Pragma("unroll") for (int r = 0; r < MR; ++r) acc[r] = fmaf(ph[32 * r - j_], pj, acc[r]); \
-        const int own = (j_ + 1) & 31;                                                        \
+        _Pragma("unroll") for (int r = 0; r < MR; ++r) acc[r] = fmaf(ph[LW * r - j_], pj, acc[r]); \
+        const int own = (j_ + 1) % LW;                                                        \
         const float cand = acc[RS] * mulx[RS];                                                \
-        const float v = __shfl_sync(full, cand < 0x1p64f ? cand : -1.f, own);                 \
+        const float v = __shfl_sync(hmask, cand < 0x1p64f ? cand : -1.f, own, LW);            \
         if (v >= 0.f) {                                                                       \
             pj = v;                                                                           \
         } else { /* exact path: rescale the frame, or an exponent out of float range */       \
-            const float raw = __shfl_sync(full, acc[RS] * mul[RS], own);                      \
-            const int E = __shfl_sync(full, ei[RS], own);                                     \
+            const float raw = __shfl_sync(hmask, acc[RS] * mul[RS], own, LW);                 \
+            const int E = __shfl_sync(hmask, ei[RS], own, LW);                                \
             const int ve = (raw > 0.f && raw < INFINITY) ? ilogbf(raw) : -1000;               \
             if (ve + E > 64) {                                                                \
                 const int sh = ve + E;                                                        \
-                __syncwarp();                                                                 \
+                __syncwarp(hmask);                                                            \
                 _Pragma("unroll") for (int r = 0; r < MR; ++r) acc[r] = ldexpf(acc[r], -sh);  \
-                for (int i = lane; i <= j_; i += 32) LT[i].y = ldexpf(LT[i].y, -sh);          \
+                for (int i = hl; i <= j_; i += LW) LT[i].y = ldexpf(LT[i].y, -sh);            \
                 pj = ldexpf(raw, -ve);                                                        \
             } else {                                                                          \
                 pj = ldexpf(raw, E);                                                          \
             }                                                                                 \
         }                                                                                     \
-        if (lane == own) LT[j_ + 1].y = pj;                                                   \
+        if (hl == own) LT[j_ + 1].y = pj;                                                     \
     }
 #pragma unroll
         for (int r0 = 0; r0 < MR; ++r0) {
-            // levels 32 r0 + 1 .. 32 r0 + 31 (this register of lanes 1..31)
-            for (int jj = 0; jj < 31; ++jj) FL_STEP(32 * r0 + jj, r0)
-            // level 32 (r0 + 1) (the next register of lane 0)
-            if (r0 + 1 < MR) FL_STEP(32 * r0 + 31, r0 + 1 < MR ? r0 + 1 : r0)
+            // levels LW r0 + 1 .. LW r0 + LW - 1 (this register of lanes 1..LW-1)
+            for (int jj = 0; jj < LW - 1; ++jj) FL_STEP(LW * r0 + jj, r0)
+            // level LW (r0 + 1) (the next register of lane 0)
+            if (r0 + 1 < MR) FL_STEP(LW * r0 + LW - 1, r0 + 1 < MR ? r0 + 1 : r0)
         }
 #undef FL_STEP
-        __syncwarp();
+        __syncwarp(hmask);
         // normalisation
         float z = 0.f;
-        for (int j = lane; j < M; j += 32) z += LT[j].y;
+        for (int j = hl; j < M; j += LW) z += LT[j].y;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) z += __shfl_xor_sync(full, z, o);
+        for (int o = LW / 2; o; o >>= 1) z += __shfl_xor_sync(hmask, z, o);
         const float iz = 1.f / z;
-        for (int j = lane; j < M; j += 32) {
+        for (int j = hl; j < M; j += LW) {
             const float p = LT[j].y * iz;
             LT[j].y = p;
             if (P) P[((size_t)c * fd.Gf + q) * M + j] = p;
         }
-        if (dE_out && lane == 0) dE_out[c * fd.Gf + q] = dEt * eps_ref;
-        __syncwarp();
-        // 6. emission of the distribution, accumulated per warp: whole passes
-        //    of 4 pairs per lane, then floor(rest / 64) pairs per lane, then
-        //    the last < 64 wavelengths with the levels split between lanes
+        if (dE_out && hl == 0) dE_out[c * fd.Gf + q] = dEt * eps_ref;
+        __syncwarp(hmask);
+        // 6. emission of the distribution, accumulated per problem slot: whole
+        //    passes of 4 pairs per lane, then floor(rest / 2LW) pairs per lane,
+        //    then the last < 2 LW wavelengths with the levels split between lanes
         int k0 = 0;
-        for (; k0 + 64 * FL_NPL <= K; k0 += 64 * FL_NPL) fl_pass<FL_NPL>(tb, LT, M, k0, K, g, nq, lane, Lw);
-        switch ((K - k0) / 64) {
-            case 3: fl_pass<3>(tb, LT, M, k0, K, g, nq, lane, Lw); k0 += 192; break;
-            case 2: fl_pass<2>(tb, LT, M, k0, K, g, nq, lane, Lw); k0 += 128; break;
-            case 1: fl_pass<1>(tb, LT, M, k0, K, g, nq, lane, Lw); k0 += 64; break;
+        for (; k0 + 8 * LW <= K; k0 += 8 * LW) fl_pass<FL_NPL, LW>(tb, LT, M, k0, K, g, nq, hl, Lw);
+        switch ((K - k0) / (2 * LW)) {
+            case 3: fl_pass<3, LW>(tb, LT, M, k0, K, g, nq, hl, Lw); k0 += 6 * LW; break;
+            case 2: fl_pass<2, LW>(tb, LT, M, k0, K, g, nq, hl, Lw); k0 += 4 * LW; break;
+            case 1: fl_pass<1, LW>(tb, LT, M, k0, K, g, nq, hl, Lw); k0 += 2 * LW; break;
             default: break;
         }
         if (k0 < K) {
-            const int np = (K - k0 + 1) / 2;  // <= 32 pairs
-            int lp = 32;                        // lanes per pair: a power of two, >= 8 levels each
-            while (lp > 1 && (lp * np > 32 || M / lp < 8)) lp >>= 1;
-            const int pr = lane / lp, ch0 = lane % lp, nl = M / lp;
+            const int np = (K - k0 + 1) / 2;  // <= LW pairs
+            int lp = LW;                        // lanes per pair: a power of two, >= 8 levels each
+            while (lp > 1 && (lp * np > LW || M / lp < 8)) lp >>= 1;
+            const int pr = hl / lp, ch0 = hl % lp, nl = M / lp;
             const int k = k0 + 2 * pr;
             float2 nx[1] = {pr < np && k < tb.Kp ? *reinterpret_cast<const float2 *>(tb.nax + k)
                                                  : make_float2(-1e30f, -1e30f)};
             float2 sum[1] = {make_float2(0.f, 0.f)};
-            fl_levels<1>(LT, ch0 * nl, ch0 * nl + nl, nx, sum);
+            fl_levels<1>(LT, ch0, lp, nl, nx, sum);  // levels ch0 + lp i: the lanes of a pair read neighbours
             for (int o = 1; o < lp; o <<= 1) {
-                sum[0].x += __shfl_xor_sync(full, sum[0].x, o);
-                sum[0].y += __shfl_xor_sync(full, sum[0].y, o);
+                sum[0].x += __shfl_xor_sync(hmask, sum[0].x, o);
+                sum[0].y += __shfl_xor_sync(hmask, sum[0].y, o);
             }
             if (ch0 == 0 && pr < np && k < K) {
                 const float2 c2 =
@@ -372,27 +387,59 @@ __global__ void __launch_bounds__(FL_WARPS_MAX * 32, fl_min_ctas(MR)) k_fluct(co
                 Lw[k + 1] = fmaf(nq * c2.y, sum[0].y, Lw[k + 1]);
             }
         }
-        __syncwarp();
+        __syncwarp(hmask);
     }
     __syncthreads();
     if (L) {
-        const float *L0 = sm + Kp4;
+        const float *L0 = sm + Kp4 + fl_lw_offset(K, M);
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
             float v = 0.f;
-            for (int i = 0; i < FW; ++i) v += L0[(size_t)i * fl_warp_floats(K, M) + fl_lw_offset(K, M) + k];
+            for (int i = 0; i < NPB; ++i) v += L0[(size_t)i * fl_warp_floats(K, M) + k];
             L[c * ld + k] = ldexpf(v, __ldg(tb.qexp + k));
         }
     }
 }
 
-template <int MR>
-cudaError_t launch_fluct_mr(const dust_ctx *ctx, const FlDev &fd, int64_t C, const float *J, int64_t ld,
-                            const float *n, float *L, float *P, float *dE, int FW, size_t smem, cudaStream_t st) {
-    auto kern = k_fluct<MR>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// CTA size.  Two problems per warp: the number of warps whose resident CTAs
+// per SM (occupancy API) times problem slots, discounted by the idle slots of
+// the last pass over the grains, is largest.  One problem per warp: up to 12
+// warps, as few passes over the grains as that allows, balanced.
+template <int M>
+cudaError_t launch_fluct_m(const dust_ctx *ctx, const FlDev &fd, int64_t C, const float *J, int64_t ld,
+                           const float *n, float *L, float *P, float *dE, cudaStream_t st, int *fw_out) {
+    auto kern = k_fluct<M>;
+    const int K = ctx->K, Gf = fd.Gf, ppw = 32 / fl_lanes(M);
+    const size_t per_slot = sizeof(float) * fl_warp_floats(K, M);
+    const size_t fixed = sizeof(float) * ((K + 3) & ~3);
+    const size_t optin = ctx->smem_optin ? ctx->smem_optin : 232448;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)optin);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)C, FW * 32, smem, st>>>(ctx->tb, fd, ctx->W32, ctx->Kw, C, J, ld, n, L, P, dE,
-                                             ctx->fl_eps_ref);
+    int best = 0;
+    double best_score = -1.0;
+    if (ppw == 1) {
+        int fw = std::min(Gf, fl_threads(M) / 32);
+        const int passes = (Gf + fw - 1) / fw;
+        fw = (Gf + passes - 1) / passes;
+        while (fw > 1 && fixed + per_slot * fw > optin) --fw;
+        best = fw;
+        best_score = 1.0;
+    }
+    for (int fw = 1; ppw == 2 && fw <= fl_threads(M) / 32; ++fw) {
+        const size_t sm_b = fixed + per_slot * fw * ppw;
+        if (sm_b > optin) break;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, fw * 32, sm_b) != cudaSuccess) {
+            cudaGetLastError();
+            nb = 0;
+        }
+        const int slots = fw * ppw, passes = (Gf + slots - 1) / slots;
+        const double score = (double)nb * slots * ((double)Gf / ((double)slots * passes));
+        if (score > best_score + 1e-9) { best_score = score; best = fw; }
+    }
+    if (best == 0 || best_score <= 0.0) return cudaErrorInvalidConfiguration;
+    *fw_out = best;
+    kern<<<(unsigned)C, best * 32, fixed + per_slot * best * ppw, st>>>(ctx->tb, fd, ctx->W32, ctx->Kw, C, J, ld, n,
+                                                                       L, P, dE, ctx->fl_eps_ref);
     return cudaGetLastError();
 }
 
@@ -513,16 +560,9 @@ extern "C" int dust_solve_fluct(dust_ctx *ctx, int64_t n_cells, const float *J, 
         if (r != DUST_OK) return r;
     }
     const int K = ctx->K, M = ctx->fl_M, Gf = ctx->fl_Gf;
-    const size_t per_warp = sizeof(float) * fl_warp_floats(K, M);
-    const size_t fixed = sizeof(float) * ((K + 3) & ~3);
-    const size_t budget = std::min<size_t>(ctx->smem_optin ? ctx->smem_optin : 232448, 200 * 1024);
-    int FW = std::min(Gf, FL_WARPS_MAX);
-    // balance: the fewest passes over the grains, then the fewest warps
-    const int passes = (Gf + FW - 1) / FW;
-    FW = (Gf + passes - 1) / passes;
-    while (FW > 1 && fixed + per_warp * FW > budget) --FW;
-    const size_t smem = fixed + per_warp * FW;
-    if (smem > budget) return set_error(DUST_EINVAL, "K=%d, M=%d need more shared memory than one CTA has", K, M);
+    // one problem slot of shared memory per (cell, grain) in flight
+    if (sizeof(float) * (((K + 3) & ~3) + fl_warp_floats(K, M)) > (ctx->smem_optin ? ctx->smem_optin : 232448))
+        return set_error(DUST_EINVAL, "K=%d, M=%d need more shared memory than one CTA has", K, M);
     std::lock_guard<std::mutex> lk(ctx->mu);
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return set_error(DUST_ECUDA, "cudaGetDevice failed");
@@ -533,12 +573,13 @@ extern "C" int dust_solve_fluct(dust_ctx *ctx, int64_t n_cells, const float *J, 
              (const FlGrain *)(b + ctx->fl_off[2]), Gf, M};
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
+    int fw = 0;
     switch (M) {
-        case 32: e = launch_fluct_mr<1>(ctx, fd, n_cells, J, ld, n, L, P, dE, FW, smem, st); break;
-        case 64: e = launch_fluct_mr<2>(ctx, fd, n_cells, J, ld, n, L, P, dE, FW, smem, st); break;
-        case 128: e = launch_fluct_mr<4>(ctx, fd, n_cells, J, ld, n, L, P, dE, FW, smem, st); break;
-        case 256: e = launch_fluct_mr<8>(ctx, fd, n_cells, J, ld, n, L, P, dE, FW, smem, st); break;
-        default: e = launch_fluct_mr<16>(ctx, fd, n_cells, J, ld, n, L, P, dE, FW, smem, st); break;
+        case 32: e = launch_fluct_m<32>(ctx, fd, n_cells, J, ld, n, L, P, dE, st, &fw); break;
+        case 64: e = launch_fluct_m<64>(ctx, fd, n_cells, J, ld, n, L, P, dE, st, &fw); break;
+        case 128: e = launch_fluct_m<128>(ctx, fd, n_cells, J, ld, n, L, P, dE, st, &fw); break;
+        case 256: e = launch_fluct_m<256>(ctx, fd, n_cells, J, ld, n, L, P, dE, st, &fw); break;
+        default: e = launch_fluct_m<512>(ctx, fd, n_cells, J, ld, n, L, P, dE, st, &fw); break;
     }
     int rc = DUST_OK;
     if (e != cudaSuccess) {
