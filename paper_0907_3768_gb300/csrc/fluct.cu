@@ -308,10 +308,11 @@ __global__ void __launch_bounds__(fl_threads(M), M <= 256 ? 2 : 1) k_fluct(const
         float pj = 1.f;
         if (hl == 0) LT[0].y = 1.f;
         const float *ph = phi + hl;
-#define FL_STEP(J, RS)                                                                        \
+        // (registers below R0 hold levels at or below j: their updates add 0)
+#define FL_STEP(J, RS, R0)                                                                    \
     {                                                                                         \
         const int j_ = (J);                                                                   \
-        _Pragma("unroll") for (int r = 0; r < MR; ++r) acc[r] = fmaf(ph[LW * r - j_], pj, acc[r]); \
+        _Pragma("unroll") for (int r = (R0); r < MR; ++r) acc[r] = fmaf(ph[LW * r - j_], pj, acc[r]); \
         const int own = (j_ + 1) % LW;                                                        \
         const float cand = acc[RS] * mulx[RS];                                                \
         const float v = __shfl_sync(hmask, cand < 0x1p64f ? cand : -1.f, own, LW);            \
@@ -336,9 +337,9 @@ __global__ void __launch_bounds__(fl_threads(M), M <= 256 ? 2 : 1) k_fluct(const
 #pragma unroll
         for (int r0 = 0; r0 < MR; ++r0) {
             // levels LW r0 + 1 .. LW r0 + LW - 1 (this register of lanes 1..LW-1)
-            for (int jj = 0; jj < LW - 1; ++jj) FL_STEP(LW * r0 + jj, r0)
+            for (int jj = 0; jj < LW - 1; ++jj) FL_STEP(LW * r0 + jj, r0, r0)
             // level LW (r0 + 1) (the next register of lane 0)
-            if (r0 + 1 < MR) FL_STEP(LW * r0 + LW - 1, r0 + 1 < MR ? r0 + 1 : r0)
+            if (r0 + 1 < MR) FL_STEP(LW * r0 + LW - 1, r0 + 1 < MR ? r0 + 1 : r0, r0 + 1)
         }
 #undef FL_STEP
         __syncwarp(hmask);
