@@ -24,8 +24,9 @@
 //   5. steady state by the balance of the probability fluxes across each cut
 //      between levels j-1 and j:  P_j = sum_{i<j} P_i Phi(j-i) / cool_j,
 //      computed forward: every new P_j adds P_j Phi(f-j) to the flux into
-//      each level f > j (one warp, lanes owning levels), so each step is
-//      M/32 FMAs per lane and one shuffle;
+//      each level f > j (the problem's lanes own the levels: a half-warp
+//      for up to 64 levels, two problems per warp, a whole warp from 128
+//      levels on), so each step is M/lanes FMAs per lane and one shuffle;
 //   6. emission L[c,k] = 4 pi sum_g n sum_j P_j C[g,k] B_k(T_j) (Eqs. 8-10),
 //      one MUFU ex2 per (level, wavelength), the level sum accumulated as a
 //      fraction with one reciprocal per 8 levels.
@@ -100,7 +101,7 @@ __device__ __forceinline__ void fl_first(float2 nax, float iT, float p, float2 &
     D = __ffma2_rn(tn, make_float2(1.f, 1.f), make_float2(1.f, 1.f));
 }
 
-// One CTA per cell; warp w takes fluctuating grains w, w + FW, ...
+// One CTA per cell; its problem slots take the fluctuating grains in turn.
 // Sum over the levels j0 + s i, i < n (n a multiple of 8), of P_j t/(1-t) for
 // NP wavelength pairs at once: the level data is read once per level for all
 // pairs; one reciprocal per pair and 8 levels.
