@@ -180,3 +180,27 @@ def test_fluct_full_size_sampled():
     ref = ofl.run(wl.lam, wl.w, wl.C_abs, wl.J[cells], wl.n[cells][:, grains], grains, N[grains], th[grains], 128,
                   wl.T_min, wl.T_max)
     _compare(g, ref, wl.K)
+
+
+def test_fluct_rejects_bad_arguments():
+    """Argument errors come back as DUST_EINVAL before any launch."""
+    from paper_0907_3768_gb300 import Context, _lib
+
+    wl, N, th = _workload(4)
+    with Context.from_workload(wl) as ctx:
+        J = torch.from_numpy(wl.J).cuda()
+        with pytest.raises(_lib.DustError):  # before dust_ctx_set_fluctuating
+            _lib.dust_solve_fluct(ctx.handle, 4, J.data_ptr(), wl.K, J.data_ptr(), None, None, None, None)
+        for grains, na, t, M in (([0], [50.0], [500.0], 100),      # M not a power of two in range
+                                 ([0], [50.0], [500.0], 1024),
+                                 ([wl.G], [50.0], [500.0], 64),    # grain index out of range
+                                 ([0], [0.0], [500.0], 64),        # no atoms
+                                 ([0], [50.0], [-1.0], 64)):       # negative theta
+            with pytest.raises(_lib.DustError) as e:
+                ctx.set_fluctuating(grains, na, t, M)
+            assert e.value.code == _lib.DUST_EINVAL
+        ctx.set_fluctuating([0, 1], N[:2], th[:2], 64)
+        with pytest.raises(ValueError):  # n_f of the wrong width
+            ctx.solve_fluct(J, torch.zeros((4, 3), dtype=torch.float32, device="cuda"))
+        with pytest.raises(_lib.DustError):  # ld < K
+            _lib.dust_solve_fluct(ctx.handle, 4, J.data_ptr(), wl.K - 1, J.data_ptr(), None, None, None, None)

@@ -158,3 +158,13 @@ def test_grid_rule_and_field_monotonicity():
         np.testing.assert_allclose(r["L"], 3.0 * r1["L"], rtol=1e-13)
         np.testing.assert_array_equal(r["P"], r1["P"])
     assert all(a < b for a, b in zip(means, means[1:]))
+
+
+def test_zero_field_sits_in_the_ground_level():
+    """No photons: nothing leaves level 0, so P = (1, 0, ...) and L = 0."""
+    wl, N, th = _wl(cells=2)
+    grains = np.arange(wl.G)
+    J = np.zeros_like(wl.J)
+    r = fluct.run(wl.lam, wl.w, wl.C_abs, J, wl.n, grains, N, th, 32, wl.T_min, wl.T_max)
+    assert (r["P"][:, :, 0] == 1.0).all() and (r["P"][:, :, 1:] == 0.0).all()
+    assert (r["L"] == 0.0).all() and (r["heat"] == 0.0).all()
