@@ -160,11 +160,16 @@ __device__ __forceinline__ void fl_pass(const DevTables &tb, const float2 *LT, i
 // scoped to the problem's lanes (mask and width), so the two halves of a
 // warp may also diverge.
 __host__ __device__ constexpr int fl_lanes(int M) { return M <= 64 ? 16 : 32; }
-// threads per CTA at most: 8 warps of two problems, or 12 warps of one
-__host__ __device__ constexpr int fl_threads(int M) { return fl_lanes(M) == 16 ? 256 : 384; }
+// threads per CTA at most: 8 warps (of two problems up to M = 64, of one at
+// M = 128), 12 warps above
+__host__ __device__ constexpr int fl_threads(int M) { return M <= 128 ? 256 : 384; }
+// resident CTAs the register budget is set for.  M = 128: four 8-warp CTAs
+// (64 registers, small spills) measured 84 ms against 91 ms for two 12-warp
+// CTAs at 80 registers; the recursion's chains want more warps per SM.
+__host__ __device__ constexpr int fl_min_ctas(int M) { return M <= 64 ? 2 : (M == 128 ? 4 : (M == 256 ? 2 : 1)); }
 
 template <int M>
-__global__ void __launch_bounds__(fl_threads(M), M <= 256 ? 2 : 1) k_fluct(const DevTables tb, const FlDev fd,
+__global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const DevTables tb, const FlDev fd,
                                                                       const float *W32, int Kw, int64_t C,
                                                                       const float *J, int64_t ld, const float *n,
                                                                       float *L, float *P, float *dE_out,
@@ -404,8 +409,8 @@ __global__ void __launch_bounds__(fl_threads(M), M <= 256 ? 2 : 1) k_fluct(const
 
 // CTA size.  Two problems per warp: the number of warps whose resident CTAs
 // per SM (occupancy API) times problem slots, discounted by the idle slots of
-// the last pass over the grains, is largest.  One problem per warp: up to 12
-// warps, as few passes over the grains as that allows, balanced.
+// the last pass over the grains, is largest.  One problem per warp: up to 8
+// or 12 warps, as few passes over the grains as that allows, balanced.
 template <int M>
 cudaError_t launch_fluct_m(const dust_ctx *ctx, const FlDev &fd, int64_t C, const float *J, int64_t ld,
                            const float *n, float *L, float *P, float *dE, cudaStream_t st, int *fw_out) {
