@@ -540,6 +540,13 @@ extern "C" int dust_ctx_set_fluctuating(dust_ctx *ctx, int Gf, const int *grains
             rc = set_error(DUST_ECUDA, "fluctuating-grain tables: copy failed");
             return;
         }
+        // a solve still in flight may read the tables being replaced
+        if (ctx->fl_mem && cudaDeviceSynchronize() != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(mem);
+            rc = set_error(DUST_ECUDA, "synchronising before replacing the fluctuating-grain tables failed");
+            return;
+        }
         cudaFree(ctx->fl_mem);
         ctx->fl_mem = mem;
         ctx->fl_Gf = Gf;
