@@ -168,3 +168,32 @@ def test_zero_field_sits_in_the_ground_level():
     r = fluct.run(wl.lam, wl.w, wl.C_abs, J, wl.n, grains, N, th, 32, wl.T_min, wl.T_max)
     assert (r["P"][:, :, 0] == 1.0).all() and (r["P"][:, :, 1:] == 0.0).all()
     assert (r["L"] == 0.0).all() and (r["heat"] == 0.0).all()
+
+
+@pytest.mark.parametrize("cell,grain,M", [(0, 0, 24), (3, 5, 40), (5, 2, 64)])
+def test_cumulative_rates_are_two_prefix_sums(cell, grain, M):
+    """On a uniform level grid the rate of jumps of at least m levels, from
+    any level i below the top, is one function Phi(m) = sum_k R_k
+    clamp(x_k - m + 1, 0, 1) of m = f - i (x_k = eps_k / dE), which the CUDA
+    kernel reads off two exclusive prefix sums over the wavelengths (x_k
+    falls as k rises):  Phi(m) = Sh[kb(m)] + Sf[kb(m-1)] - Sf[kb(m)] with
+    kb(m) = #{k : x_k >= m}.  Checked against the full transition matrix the
+    oracle builds one photon landing at a time."""
+    wl, N, th = _wl(log10U=(0.0, 3.0))
+    lam, w, C, J = wl.lam, wl.w, wl.C_abs[grain], wl.J[cell].astype(np.float64)
+    eps = fluct.H_PL * fluct.C_LI / lam
+    R = 4 * math.pi * w * C * J / eps
+    dE = eps[0] / 9.37
+    A, _ = fluct.rate_matrix(eps, R, dE, np.ones(M))
+    x = eps / dE
+    assert (np.diff(x) < 0).all()
+    Sh = np.concatenate([[0.0], np.cumsum(R)])
+    Sf = np.concatenate([[0.0], np.cumsum(R * (x - np.floor(x)))])
+    kb = np.array([np.count_nonzero(x >= m) for m in range(M)])
+    phi = np.zeros(M)
+    for m in range(1, M):
+        phi[m] = Sh[kb[m]] + Sf[kb[m - 1]] - Sf[kb[m]]
+    up = np.tril(A, -1)
+    for i in range(M - 1):
+        for f in range(i + 1, M):
+            np.testing.assert_allclose(up[f:, i].sum(), phi[f - i], rtol=1e-12, atol=1e-300)
