@@ -381,6 +381,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# k_fluct DRAM traffic of a 2^14-cell launch at 200 wavelengths, 36 grains, 128 levels
+# (ncu dram__bytes_read.sum + dram__bytes_write.sum: 17.55 MB + 1 KB)
+FLUCT_TRAFFIC_2E14_CELLS = 17.553920e6 + 1.024e3
+
+
 def fluctuating(ctx, wl, J, n, stream, args, world, ex2_rate, oracle_sample):
     """Temperature distributions of the workload's 0.5-10 nm grains (36 of
     96) on M levels each, and their emission: one kernel per step over the
@@ -428,7 +433,12 @@ def fluctuating(ctx, wl, J, n, stream, args, world, ex2_rate, oracle_sample):
          "roofline": {"kernel": "k_fluct", "bound": "alu", "unit": "G Planck terms/s",
                       "achieved": round(terms / (ms * 1e-3) / 1e9, 1), "peak": round(ex2_rate / 1e9, 1),
                       "frac": round(terms / (ms * 1e-3) / ex2_rate, 4),
-                      "peak_source": "measured MUFU ex2.approx rate (dust_diag_throughput)"}}
+                      "peak_source": "measured MUFU ex2.approx rate (dust_diag_throughput)",
+                      "traffic": None,
+                      "traffic_2e14_cells": FLUCT_TRAFFIC_2E14_CELLS if M == 128 and K == 200 else None,
+                      "traffic_note": "full-size launch not captured; ncu DRAM read + write of the first 2^14 cells "
+                                      "(its L writes stay in L2), not scaled: the tables are read once per launch",
+                      "algorithmic_bytes": C * (2 * K + Gf) * 4}}
     if oracle_sample:
         from oracle import fluct as ofl
 
