@@ -24,6 +24,9 @@ constexpr int RG = 8;
 constexpr int GPAD = 16;
 // K-chunk (FP32 columns) of the tensor-core absorption kernel.
 constexpr int KC = 32;
+// Buckets of the cell ordering (order.cu): the exponent and two mantissa bits
+// of a positive float key, i.e. quarter-octave classes of absorbed power.
+constexpr int NBK = 1024;
 
 // Per-grain constants of the temperature solve (float4-packed for one load).
 struct GrainParam {
@@ -89,6 +92,9 @@ struct ScratchView {
     float2 *prep;
     CellInfo *cell;
     float2 *part;  // [C][NKG] float-float partial sums of w_k L_k (residual)
+    int *order;    // [C] the cells in emission order (temperature classes)
+    uint16_t *bkt; // [C] each cell's class
+    unsigned *hist;  // [2][NBK] cells per class, then the scatter cursors
 };
 
 // One request of the solve / emission kernels.
@@ -102,6 +108,7 @@ struct EmitReq {
     float2 *prep;
     CellInfo *cell;
     float2 *part;
+    const int *order;  // emission order of the request's cells (NULL: ascending)
     int TC, GC, resident, mode;
     int nth;        // emission threads per CTA (256: two CTAs per SM; 512: one, for streamed weights)
     uint32_t smem;  // its emission kernel's shared memory
@@ -111,6 +118,24 @@ struct EmitBatch {
     int nreq;
     int64_t ntiles, ncells;
     EmitReq req[MAXREQ];
+};
+
+// One request of the cell ordering: a positive float key per cell at
+// key[c * kstride] (an absorbed power or an inverse temperature of one
+// reference grain) sorted into NBK classes, then scattered into `order`.
+struct OrderReq {
+    const float *key;
+    int64_t kstride, C;
+    uint16_t *bkt;
+    unsigned *hist;  // [2][NBK], zeroed by the launch
+    int *order;
+    int block_begin;  // first CTA of the request in the classify / scatter grids
+};
+
+struct OrderBatch {
+    int nreq;
+    int nblocks;
+    OrderReq req[MAXREQ];
 };
 
 // Solve requests of a fused absorption + solve launch (index i belongs to
@@ -281,6 +306,14 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
 // there (fused absorption + solve) and only the emission runs.
 int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, cudaEvent_t between = nullptr,
                       bool solved = false, int *nlaunch = nullptr);
+
+// Orders the cells of every request of the batch by the class of its key
+// (three launches: zero the counts, classify, scatter).  Cells of one class
+// run together in the emission, so that the 32 lanes of a warp take the same
+// regime branches; the order never changes a result.
+int launch_order(OrderBatch &B, cudaStream_t st, int *nlaunch);
+// Key of the ordering: the reference grain of a context.
+inline int order_ref_grain(int G) { return G / 2; }
 
 // Warp-specialized solve + emission over one request: the plan (its tile of
 // TC cells and shared memory, 0 where it does not apply) and the launch (the

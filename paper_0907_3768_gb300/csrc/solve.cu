@@ -122,6 +122,30 @@ int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_
     if (rc == DUST_OK) ctx->launches += 1;
     int ftc = 0;
     const size_t fsmem = !fused && ctx->fused_emit ? plan_solve_emit(ctx, L || resid, mass, &ftc) : 0;
+    if (rc == DUST_OK && (L || resid)) {
+        // emission order: cells classed by the absorbed power of the reference
+        // grain (S), or by its inverse temperature where S stayed in tensor memory
+        const int gref = order_ref_grain(ctx->G);
+        OrderBatch ob;
+        ob.nreq = 1;
+        OrderReq &o = ob.req[0];
+        if (fused) {
+            const int pw = mass ? 1 : 2;
+            o.key = reinterpret_cast<const float *>(sv.prep) + pw * gref;
+            o.kstride = (int64_t)pw * ctx->tb.G8;
+        } else {
+            o.key = sv.S + gref;
+            o.kstride = ctx->tb.Gs;
+        }
+        o.C = C;
+        o.bkt = sv.bkt;
+        o.hist = sv.hist;
+        o.order = sv.order;
+        int nl = 0;
+        rc = launch_order(ob, st, &nl);
+        ctx->launches += (uint64_t)nl;
+        B.req[0].order = sv.order;
+    }
     if (rc == DUST_OK) {
         if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[1], st));
         int nl = 0;

@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(SOLVE_TH, TONLY ? solve_tonly_ctas(NB) : (NB >
 // One grain's term for two wavelengths of one cell, folded into the group's
 // fraction N/D.  Every FP32 step is a packed (f32x2) operation: the FMA pipe,
 // not the MUFU, is the limit of this loop (an f32x2 FMA costs the FMA pipe
-// as much as two scalar ones, and each ex2 takes dispatch cycles from it),
+// as much as two scalar ones, and each ex2 takes a cycle from it as well),
 // so the step is kept to five packed operations per two terms.
 __device__ __forceinline__ void emit_pair(float2 nax, float2 iT, float2 nn, float2 cw, float2 &N, float2 &D) {
     const float2 a = __fmul2_rn(nax, iT);
@@ -262,6 +262,136 @@ __device__ __forceinline__ void emit_first(float2 nax, float2 iT, float2 nn, flo
     const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
     N = __fmul2_rn(__fmul2_rn(nn, cw), t);
     D = __ffma2_rn(make_float2(-t.x, -t.y), make_float2(1.f, 1.f), make_float2(1.f, 1.f));
+}
+
+// min that returns NaN when either operand is NaN: a grain with an invalid
+// temperature keeps its group on the full form, so that its NaN reaches L.
+__device__ __forceinline__ float fmin_nan(float a, float b) {
+    float y;
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+    return y;
+}
+
+// Regimes of a group of RG grains x the item's 8 wavelengths, on the largest
+// exponent a = nax_k / T_g in it (nax_k < 0).  Below A_ZERO every
+// t = ex2.approx.ftz(a) is flushed to 0, so the group adds nothing and is
+// skipped: its terms would leave N, D and the sum unchanged, so skipping it
+// gives the same bits.  Below A_WIEN every t <= 2^-24, so t / (1 - t) equals
+// t to within one FP32 rounding (Wien's law) and the term is w t: no
+// denominator, no reciprocal, three packed operations per two terms instead
+// of five.  Below A_MID every t <= 2^-12, so t / (1 - t) = t + t^2 to within
+// t^3 / t = t^2 <= 2^-24 relative, and the term is w (t + t t): four packed
+// operations, still no reciprocal.
+constexpr float A_ZERO = -127.f;
+constexpr float A_WIEN = -24.f;
+constexpr float A_MID = -12.f;
+
+// Eq. 10 for one emission item: one cell x the 8 wavelengths of one k-group,
+// over grains [0, gn) (gn a multiple of RG), added to acc[p] (wavelengths
+// 2p, 2p+1).  tn: the cell's (1/T, n 2^-m_c) pairs (float2; 1/T alone in the
+// dust-mass form), PST floats apart from grain to grain; cp: the k-group's
+// weights [g][2] float4 (Chat of 8 wavelengths per grain); nax2: its nax
+// pairs; naxl: the largest of its eight nax.
+//   amax = naxl * min_g 1/T_g is the largest exponent of the group (both
+//   factors' extremes are taken exactly and rounding is monotone), so the
+//   regime test is exact for every term of the group.
+// Every lane's arithmetic depends only on its own cell, so results are the
+// same in any batch, kernel or lane arrangement.
+template <bool MASS, int PST>
+__device__ __forceinline__ void emit_item(const float *tn, const float4 *cp, int gn, const float2 (&nax2)[4],
+                                          float naxl, float2 (&acc)[4]) {
+    for (int gg0 = 0; gg0 < gn; gg0 += RG) {
+        float iT[RG], nv[RG];
+#pragma unroll
+        for (int u = 0; u < RG; ++u) {
+            if (MASS) {
+                iT[u] = tn[(gg0 + u) * PST];
+                nv[u] = 0.f;
+            } else {
+                const float2 pr = *reinterpret_cast<const float2 *>(tn + (gg0 + u) * PST);
+                iT[u] = pr.x;
+                nv[u] = pr.y;
+            }
+        }
+        float m = iT[0];
+#pragma unroll
+        for (int u = 1; u < RG; ++u) m = fmin_nan(m, iT[u]);
+        const float amax = naxl * m;
+        if (amax < A_ZERO) continue;  // every term is 0
+        const float4 *cg = cp + 2 * gg0;
+        if (amax < A_WIEN) {
+#pragma unroll
+            for (int u = 0; u < RG; ++u) {
+                const float4 ca = cg[2 * u], cb = cg[2 * u + 1];
+                const float2 cw[4] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w), make_float2(cb.x, cb.y),
+                                      make_float2(cb.z, cb.w)};
+                const float2 i2 = make_float2(iT[u], iT[u]);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const float2 a = __fmul2_rn(nax2[p], i2);
+                    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+                    const float2 w = MASS ? cw[p] : __fmul2_rn(make_float2(nv[u], nv[u]), cw[p]);
+                    acc[p] = __ffma2_rn(w, t, acc[p]);
+                }
+            }
+        } else if (amax < A_MID) {
+#pragma unroll
+            for (int u = 0; u < RG; ++u) {
+                const float4 ca = cg[2 * u], cb = cg[2 * u + 1];
+                const float2 cw[4] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w), make_float2(cb.x, cb.y),
+                                      make_float2(cb.z, cb.w)};
+                const float2 i2 = make_float2(iT[u], iT[u]);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const float2 a = __fmul2_rn(nax2[p], i2);
+                    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+                    const float2 w = MASS ? cw[p] : __fmul2_rn(make_float2(nv[u], nv[u]), cw[p]);
+                    acc[p] = __ffma2_rn(w, __ffma2_rn(t, t, t), acc[p]);
+                }
+            }
+        } else {
+            float2 N[4], D[4];
+#pragma unroll
+            for (int u = 0; u < RG; ++u) {
+                const float4 ca = cg[2 * u], cb = cg[2 * u + 1];
+                const float2 cw[4] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w), make_float2(cb.x, cb.y),
+                                      make_float2(cb.z, cb.w)};
+                const float2 i2 = make_float2(iT[u], iT[u]);
+                const float2 n2 = make_float2(nv[u], nv[u]);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    if (MASS) {
+                        if (u == 0) emit_first_m(nax2[p], i2, cw[p], N[p], D[p]);
+                        else emit_pair_m(nax2[p], i2, cw[p], N[p], D[p]);
+                    } else {
+                        if (u == 0) emit_first(nax2[p], i2, n2, cw[p], N[p], D[p]);
+                        else emit_pair(nax2[p], i2, n2, cw[p], N[p], D[p]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                acc[p].x = fmaf(N[p].x, rcp_approx(D[p].x), acc[p].x);
+                acc[p].y = fmaf(N[p].y, rcp_approx(D[p].y), acc[p].y);
+            }
+        }
+    }
+}
+
+// nax pairs of k-group ikg and the largest of its eight values.
+__device__ __forceinline__ float load_nax(const DevTables &tb, int ikg, float2 (&nax2)[4]) {
+    float l = -INFINITY;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        nax2[p] = __ldg(reinterpret_cast<const float2 *>(tb.nax + ikg * KQ) + p);
+        l = fmaxf(l, fmaxf(nax2[p].x, nax2[p].y));
+    }
+    return l;
+}
+
+// Cell of slot i of a request's emission order.
+__device__ __forceinline__ int64_t ordered_cell(const EmitReq &q, int64_t i) {
+    return q.order ? (int64_t)__ldg(q.order + i) : i;
 }
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
@@ -341,7 +471,7 @@ __device__ __forceinline__ int emit_req_of(const EmitBatch &B, int64_t tile, int
 
 // Issue the cp.async copies of a tile's (1/T, n) pairs into the pair-major
 // shared layout [pair][grain][2 cells] (padding cells of a ragged tile read
-// the dummy values instead).
+// the dummy values instead).  Tile slots follow the request's emission order.
 template <bool MASS, int NT>
 __device__ __forceinline__ void prefetch_tile(const EmitReq &q, int64_t local_tile, float *dstTN, int TNP, int tid) {
     const int G8 = q.tb.G8, TC = q.TC;
@@ -353,11 +483,11 @@ __device__ __forceinline__ void prefetch_tile(const EmitReq &q, int64_t local_ti
     for (int i = tid; i < TC * G8; i += NT) {
         if (MASS) {  // 1/T only: [pair][grain][2 cells] floats
             float *dst = dstTN + (size_t)(c >> 1) * TNP + 2 * g + (c & 1);
-            if (c < nc) cp_async4(dst, reinterpret_cast<const float *>(q.prep) + (c0 + c) * G8 + g);
+            if (c < nc) cp_async4(dst, reinterpret_cast<const float *>(q.prep) + ordered_cell(q, c0 + c) * G8 + g);
             else *dst = PAD_INV_T;
         } else {  // (1/T, n): [pair][grain][2 cells] float2
             float *dst = dstTN + (size_t)(c >> 1) * TNP + 4 * g + 2 * (c & 1);
-            if (c < nc) cp_async8(dst, q.prep + (c0 + c) * G8 + g);
+            if (c < nc) cp_async8(dst, q.prep + ordered_cell(q, c0 + c) * G8 + g);
             else *reinterpret_cast<float2 *>(dst) = make_float2(PAD_INV_T, 0.f);
         }
         c += dc;
@@ -439,11 +569,11 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) k_emit(const __grid_con
         }
         // ---- emission (two cells x 8 wavelengths per thread)
         float2 acc[2][4], nax2[4];
+        const float naxl = load_nax(tb, ikg, nax2);
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             acc[0][p] = make_float2(0.f, 0.f);
             acc[1][p] = make_float2(0.f, 0.f);
-            nax2[p] = __ldg(reinterpret_cast<const float2 *>(tb.nax + ikg * KQ) + p);
         }
         const int GC = q.resident ? G8 : q.GC;
         for (int g0 = 0; g0 < G8; g0 += GC) {
@@ -458,53 +588,10 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) k_emit(const __grid_con
                 __syncthreads();
             }
             const int goff = q.resident ? g0 : 0;
-            const float4 *tnp = reinterpret_cast<const float4 *>(sTN + (size_t)ipair * TNP) + g0;
-            const float2 *tnm = reinterpret_cast<const float2 *>(sTN + (size_t)ipair * TNP) + g0;
+            const float *tnp = sTN + (size_t)ipair * TNP + (MASS ? 2 : 4) * g0;
             const float4 *cp = sC + (size_t)ikg * CST + 2 * goff;
-            for (int gg0 = 0; gg0 < gn; gg0 += RG) {
-                float2 N[2][4], D[2][4];
-#pragma unroll
-                for (int u = 0; u < RG; ++u) {
-                    const float4 ca = cp[2 * (gg0 + u)], cb = cp[2 * (gg0 + u) + 1];
-                    const float2 cw[4] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w), make_float2(cb.x, cb.y),
-                                          make_float2(cb.z, cb.w)};
-                    if (MASS) {
-                        const float2 tm = tnm[gg0 + u];  // 1/T of both cells
-                        const float2 iTa = make_float2(tm.x, tm.x), iTb = make_float2(tm.y, tm.y);
-#pragma unroll
-                        for (int p = 0; p < 4; ++p) {
-                            if (u == 0) {
-                                emit_first_m(nax2[p], iTa, cw[p], N[0][p], D[0][p]);
-                                emit_first_m(nax2[p], iTb, cw[p], N[1][p], D[1][p]);
-                            } else {
-                                emit_pair_m(nax2[p], iTa, cw[p], N[0][p], D[0][p]);
-                                emit_pair_m(nax2[p], iTb, cw[p], N[1][p], D[1][p]);
-                            }
-                        }
-                    } else {
-                        const float4 tn = tnp[gg0 + u];  // (1/T, n) of both cells
-                        const float2 iTa = make_float2(tn.x, tn.x), na = make_float2(tn.y, tn.y);
-                        const float2 iTb = make_float2(tn.z, tn.z), nb = make_float2(tn.w, tn.w);
-#pragma unroll
-                        for (int p = 0; p < 4; ++p) {
-                            if (u == 0) {
-                                emit_first(nax2[p], iTa, na, cw[p], N[0][p], D[0][p]);
-                                emit_first(nax2[p], iTb, nb, cw[p], N[1][p], D[1][p]);
-                            } else {
-                                emit_pair(nax2[p], iTa, na, cw[p], N[0][p], D[0][p]);
-                                emit_pair(nax2[p], iTb, nb, cw[p], N[1][p], D[1][p]);
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < 2; ++r)
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        acc[r][p].x = fmaf(N[r][p].x, rcp_approx(D[r][p].x), acc[r][p].x);
-                        acc[r][p].y = fmaf(N[r][p].y, rcp_approx(D[r][p].y), acc[r][p].y);
-                    }
-            }
+            emit_item<MASS, MASS ? 2 : 4>(tnp, cp, gn, nax2, naxl, acc[0]);
+            emit_item<MASS, MASS ? 2 : 4>(tnp + (MASS ? 1 : 2), cp, gn, nax2, naxl, acc[1]);
         }
         // ---- epilogue: scale, store, residual partials.  An item's 8
         // wavelengths of a cell are one 32-byte sector of L, written as two
@@ -517,7 +604,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) k_emit(const __grid_con
         for (int r = 0; r < 2; ++r) {
             const int c = 2 * ipair + r;
             if (c >= nc) continue;
-            const int64_t cell = c0 + c;
+            const int64_t cell = ordered_cell(q, c0 + c);
             const CellInfo ci = q.cell[cell];
             const int mc = ci.mc;
             const float ms = MASS ? __int_as_float(ci.ms_bits) : 1.f;  // the cell's mass mantissa
@@ -574,27 +661,50 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) k_emit(const __grid_con
 // Solve and emission of one request in one warp-specialized kernel, for
 // either form of n (general, or the dust-mass form n_g m_c with 1/T-only
 // pairs), with the emission weights resident in shared memory.
-// One CTA per SM walks tiles of TC = q.TC cells.  Its FS_W solver warps run
-// k_solve's per-cell solve (solve_cell) on the tile after the one being
-// emitted, writing T and the flags to global memory and the pairs (1/T, n
-// 2^-m_c) and cell records into one of FSE_NBUF shared-memory tile buffers; its
-// FE_W emission warps take one cell x 8 wavelengths per thread from an
-// earlier buffer, with k_emit's arithmetic in k_emit's order.  The solve is a
-// latency-bound chain of table lookups and the emission is bound by the FMA
-// pipe, so the two overlap on the same SM.  Two mbarriers per buffer hand it
-// over (full: the solvers' writes are done; empty: the emission has read
-// it); every wait is bounded, and on expiry the kernel records
-// DUST_ETIMEOUT and both roles wind down.
-constexpr int FE_W = 16;  // emission warps
+// One CTA per SM walks tiles of FSE_TC = 32 cells, taken in the request's
+// emission order (cells of like temperatures together).  Its FS_W solver
+// warps run k_solve's per-cell solve (solve_cell) on the tiles ahead of the
+// emission, writing T and the flags to global memory and the pairs (1/T, n
+// 2^-m_c) and cell records into one of FSE_NBUF shared-memory tile buffers.
+// Its FE_W emission warps claim work items from a shared counter: an item is
+// one k-group of one tile, its 32 cells on the 32 lanes (emit_item), items of
+// a tile claimed from the longest wavelengths (the most work) down, so that
+// warps stay balanced although items differ in cost by regime.  The solve is
+// a latency-bound chain of table lookups and the emission is bound by the FMA
+// pipe, so the two overlap on the same SM.
+// Hand-over: two mbarriers per buffer (full: the solvers' writes are done,
+// FS_W arrivals; empty: every item of the tile is done, NKG arrivals); every
+// wait is bounded, and on expiry the kernel records DUST_ETIMEOUT and both
+// roles wind down.  Buffer phases: a warp waits on full[b] for tile ti only
+// once that buffer's previous tile (ti - FSE_NBUF) is filled.  Claims run in
+// order and each emission warp holds at most one unfinished item, so with
+// fewer than NKG (FSE_NBUF - 1) emission warps active, a claim in tile ti
+// implies a finished item in tiles ti - FSE_NBUF + 1 .. ti - 1, hence (tiles
+// are filled in order) a filled tile ti - FSE_NBUF.  The kernel keeps the
+// active emission warps below that bound.
+constexpr int FE_W = 12;  // emission warps
 constexpr int FS_W = 8;   // solver warps
-constexpr int FSE_TH = (FE_W + FS_W) * 32;
+constexpr int FSE_TH = (FE_W + FS_W) * 32;  // 640 threads: 96 registers each
 constexpr int FSE_NBUF = 3;  // pair-tile buffers: the solvers run up to FSE_NBUF tiles ahead
+constexpr int FSE_TC = 32;   // cells per tile: one per lane of an emission item
+
+// The CTA's it-th tile.  Its tiles are blockIdx.x + j gridDim.x, coldest
+// cells first (the emission order); they are taken from both ends in turn
+// (first, last, second, second to last, ...), so that tiles of cheap
+// emission (cold cells: many groups skipped) alternate with expensive ones
+// and the solve, whose cost per tile is even, stays in step.
+__device__ __forceinline__ int64_t fse_tile(int64_t it, int64_t ntiles) {
+    const int64_t nb = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;  // this CTA's tiles
+    const int64_t j = (it & 1) ? nb - 1 - (it >> 1) : (it >> 1);
+    return it < nb ? blockIdx.x + j * gridDim.x : ntiles;
+}
 
 template <int NB, bool MASS>
 __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant__ EmitReq q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevTables &tb = q.tb;
-    const int G8 = tb.G8, NKG = tb.NKG, TC = q.TC;
+    const int G8 = tb.G8, NKG = tb.NKG;
+    constexpr int TC = FSE_TC;
     const int CST = 2 * G8 + 1;
     // odd row stride of a pair tile (in float2, or floats for 1/T alone): a warp's cells fall in distinct banks
     const int PS = G8 + 1;
@@ -605,6 +715,7 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
     uint64_t *full = reinterpret_cast<uint64_t *>(sI + FSE_NBUF * TC);         // [FSE_NBUF]
     uint64_t *empty = full + FSE_NBUF;                                         // [FSE_NBUF]
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + FSE_NBUF);
+    int *claim = const_cast<int *>(abort_flag) + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t ntiles = (q.C + TC - 1) / TC;
 
@@ -616,8 +727,9 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
         }
     }
     if (tid == 0) {
-        for (int b = 0; b < FSE_NBUF; ++b) { mbar_init(&full[b], FS_W); mbar_init(&empty[b], FE_W); }
+        for (int b = 0; b < FSE_NBUF; ++b) { mbar_init(&full[b], FS_W); mbar_init(&empty[b], NKG); }
         *abort_flag = 0;
+        *claim = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -625,32 +737,31 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
     if (warp >= FE_W) {
         // ------------------------------------------------------------ solvers
         const int sw = warp - FE_W;
-        int64_t tile = blockIdx.x;
-        int cl = sw;  // this warp's cells of a tile: sw, sw + FS_W, ...
         int it = 0;
-        // first cell of this warp (tiles whose share for it is empty are skipped by the loop)
-        auto cell_of = [&](int64_t t, int c) { return t * TC + c; };
+        int64_t tile = fse_tile(0, ntiles);
         float s0[NB], n0[NB];
-        bool have = tile < ntiles && cl < TC && cell_of(tile, cl) < q.C;
-        if (have) load_pass<NB>(q, cell_of(tile, cl), 0, lane, s0, n0);
+        int64_t pf = -1;  // the tile whose first slot of this warp s0 / n0 hold
         bool ok = true;
-        for (; tile < ntiles && ok; tile += gridDim.x, ++it) {
+        for (; tile < ntiles && ok; tile = fse_tile(++it, ntiles)) {
             const int b = it % FSE_NBUF;
             const uint32_t ph = (uint32_t)((it / FSE_NBUF) & 1);
-            if (!(ok = mbar_wait(&empty[b], ph ^ 1, abort_flag, tb.status))) break;
             const int nc = (int)min((int64_t)TC, q.C - tile * TC);
-            for (cl = sw; cl < nc; cl += FS_W) {
-                const int64_t cell = cell_of(tile, cl);
+            // a warp with no slot in the previous tile (a ragged one) prefetched nothing
+            if (sw < nc && pf != tile) load_pass<NB>(q, ordered_cell(q, tile * TC + sw), 0, lane, s0, n0);
+            if (!(ok = mbar_wait(&empty[b], ph ^ 1, abort_flag, tb.status))) break;
+            for (int cl = sw; cl < nc; cl += FS_W) {
+                const int64_t cell = ordered_cell(q, tile * TC + cl);
                 // next cell of this warp: in this tile, else its first in the next tile
                 int64_t tn = tile;
                 int cn = cl + FS_W;
-                if (cn >= nc) { tn = tile + gridDim.x; cn = sw; }
-                const int64_t un = cell_of(tn, cn);
-                const bool more = tn < ntiles && cn < TC && un < q.C;
+                if (cn >= nc) { tn = fse_tile(it + 1, ntiles); cn = sw; }
+                const bool more = tn < ntiles && tn * TC + cn < q.C;
                 float s1[NB], n1[NB];
-                if (more) load_pass<NB>(q, un, 0, lane, s1, n1);
-                solve_cell<NB, true, false, MASS ? 1 : 0, true>(q, cell, lane, s0, n0, reinterpret_cast<float2 *>(sP + ((size_t)b * TC + cl) * PS * PW),
-                                     sI + b * TC + cl);
+                if (more) load_pass<NB>(q, ordered_cell(q, tn * TC + cn), 0, lane, s1, n1);
+                pf = more ? tn : -1;
+                solve_cell<NB, true, false, MASS ? 1 : 0, true>(q, cell, lane, s0, n0,
+                                                                reinterpret_cast<float2 *>(sP + ((size_t)b * TC + cl) * PS * PW),
+                                                                sI + b * TC + cl);
 #pragma unroll
                 for (int i = 0; i < NB; ++i) { s0[i] = s1[i]; n0[i] = n1[i]; }
             }
@@ -659,62 +770,30 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
         }
     } else {
         // ------------------------------------------------------------ emission
-        const int icell = tid % TC, ikg = tid / TC;
-        const bool active = ikg < NKG;
-        const int kgi = active ? ikg : 0;
-        float2 nax2[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) nax2[p] = __ldg(reinterpret_cast<const float2 *>(tb.nax + kgi * KQ) + p);
-        const float4 *cp = sC + (size_t)kgi * CST;
+        if (warp >= NKG * (FSE_NBUF - 1) - 1) return;  // see the phase argument above
         const bool rs = (q.mode & EMIT_RESID) != 0, storeL = (q.mode & EMIT_STORE_L) != 0;
         const bool vecL = storeL && ((reinterpret_cast<uintptr_t>(q.L) & 15) == 0) && (q.ld % 4 == 0);
-        int it = 0;
-        bool ok = true;
-        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
-            const int b = it % FSE_NBUF;
-            const uint32_t ph = (uint32_t)((it / FSE_NBUF) & 1);
-            if (!(ok = mbar_wait(&full[b], ph, abort_flag, tb.status))) break;
+        for (;;) {
+            int w = 0;
+            if (lane == 0) w = atomicAdd(claim, 1);
+            w = __shfl_sync(0xffffffffu, w, 0);
+            const int ti = w / NKG;
+            const int ikg = NKG - 1 - (w - ti * NKG);
+            const int64_t tile = fse_tile(ti, ntiles);
+            if (tile >= ntiles) break;
+            const int b = ti % FSE_NBUF;
+            const uint32_t ph = (uint32_t)((ti / FSE_NBUF) & 1);
+            if (!mbar_wait(&full[b], ph, abort_flag, tb.status)) break;
             const int nc = (int)min((int64_t)TC, q.C - tile * TC);
-            if (active && icell < nc) {
-                const float *tnp = sP + ((size_t)b * TC + icell) * PS * PW;
-                float2 acc[4];
+            if (lane < nc) {
+                float2 nax2[4], acc[4];
+                const float naxl = load_nax(tb, ikg, nax2);
 #pragma unroll
                 for (int p = 0; p < 4; ++p) acc[p] = make_float2(0.f, 0.f);
-                for (int gg0 = 0; gg0 < G8; gg0 += RG) {
-                    float2 N[4], D[4];
-#pragma unroll
-                    for (int u = 0; u < RG; ++u) {
-                        const float4 ca = cp[2 * (gg0 + u)], cb = cp[2 * (gg0 + u) + 1];
-                        const float2 cw[4] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w), make_float2(cb.x, cb.y),
-                                              make_float2(cb.z, cb.w)};
-                        if (MASS) {  // 1/T of this cell; the weights carry n_g
-                            const float t = tnp[gg0 + u];
-                            const float2 iT = make_float2(t, t);
-#pragma unroll
-                            for (int p = 0; p < 4; ++p) {
-                                if (u == 0) emit_first_m(nax2[p], iT, cw[p], N[p], D[p]);
-                                else emit_pair_m(nax2[p], iT, cw[p], N[p], D[p]);
-                            }
-                        } else {  // (1/T, n) of this cell
-                            const float2 tn = reinterpret_cast<const float2 *>(tnp)[gg0 + u];
-                            const float2 iT = make_float2(tn.x, tn.x), nn = make_float2(tn.y, tn.y);
-#pragma unroll
-                            for (int p = 0; p < 4; ++p) {
-                                if (u == 0) emit_first(nax2[p], iT, nn, cw[p], N[p], D[p]);
-                                else emit_pair(nax2[p], iT, nn, cw[p], N[p], D[p]);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        acc[p].x = fmaf(N[p].x, rcp_approx(D[p].x), acc[p].x);
-                        acc[p].y = fmaf(N[p].y, rcp_approx(D[p].y), acc[p].y);
-                    }
-                }
-                // epilogue, the emission kernel's
-                const int64_t cell = tile * TC + icell;
-                const CellInfo ci = sI[b * TC + icell];
-                emit_item_out<MASS>(q, cell, ikg, acc, ci.mc, MASS ? __int_as_float(ci.ms_bits) : 1.f, storeL, vecL, rs);
+                emit_item<MASS, PW>(sP + ((size_t)b * TC + lane) * PS * PW, sC + (size_t)ikg * CST, G8, nax2, naxl, acc);
+                const CellInfo ci = sI[b * TC + lane];
+                emit_item_out<MASS>(q, ordered_cell(q, tile * TC + lane), ikg, acc, ci.mc,
+                                    MASS ? __int_as_float(ci.ms_bits) : 1.f, storeL, vecL, rs);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[b]);
@@ -776,13 +855,19 @@ EmitPlan plan_emit(const dust_ctx *ctx, bool emit, bool mass) {
 }
 
 // Scratch bytes of a request of C cells: S [C][Gs] FP32, then (emission)
-// the (1/T, n) pairs [C][G8], one CellInfo per cell and the residual
-// partials [C][NKG] float2, each 16-byte aligned.
+// the (1/T, n) pairs [C][G8], one CellInfo per cell, the residual partials
+// [C][NKG] float2, the emission order [C] int32, the cells' classes [C]
+// uint16 and the class counts and cursors [2][NBK] uint32, each 16-byte
+// aligned.
+namespace {
+inline size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
+}  // namespace
+
 size_t scratch_bytes(const dust_ctx *ctx, int64_t C, bool emit) {
-    size_t b = ((size_t)C * ctx->tb.Gs * 4 + 15) & ~(size_t)15;
+    size_t b = al16((size_t)C * ctx->tb.Gs * 4);
     if (emit)
-        b += (((size_t)C * ctx->tb.G8 * 8 + 15) & ~(size_t)15) + (size_t)C * sizeof(CellInfo) +
-             (((size_t)C * ctx->tb.NKG * 8 + 15) & ~(size_t)15);
+        b += al16((size_t)C * ctx->tb.G8 * 8) + (size_t)C * sizeof(CellInfo) + al16((size_t)C * ctx->tb.NKG * 8) +
+             al16((size_t)C * 4) + al16((size_t)C * 2) + (size_t)2 * NBK * 4;
     return b;
 }
 
@@ -790,12 +875,18 @@ ScratchView scratch_view(const dust_ctx *ctx, int64_t C, void *base) {
     ScratchView v;
     char *p = static_cast<char *>(base);
     v.S = reinterpret_cast<float *>(p);
-    p += ((size_t)C * ctx->tb.Gs * 4 + 15) & ~(size_t)15;
+    p += al16((size_t)C * ctx->tb.Gs * 4);
     v.prep = reinterpret_cast<float2 *>(p);
-    p += ((size_t)C * ctx->tb.G8 * 8 + 15) & ~(size_t)15;
+    p += al16((size_t)C * ctx->tb.G8 * 8);
     v.cell = reinterpret_cast<CellInfo *>(p);
     p += (size_t)C * sizeof(CellInfo);
     v.part = reinterpret_cast<float2 *>(p);
+    p += al16((size_t)C * ctx->tb.NKG * 8);
+    v.order = reinterpret_cast<int *>(p);
+    p += al16((size_t)C * 4);
+    v.bkt = reinterpret_cast<uint16_t *>(p);
+    p += al16((size_t)C * 2);
+    v.hist = reinterpret_cast<unsigned *>(p);
     return v;
 }
 
@@ -815,6 +906,7 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
     r.prep = sv.prep;
     r.cell = sv.cell;
     r.part = sv.part;
+    r.order = nullptr;
     r.TC = p.TC;
     r.GC = p.GC;
     r.resident = p.resident;
@@ -929,8 +1021,7 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
 size_t plan_solve_emit(const dust_ctx *ctx, bool emit, bool mass, int *TC) {
     if (!emit || (mass && !ctx->mass_ready)) return 0;
     const DevTables &tb = mass ? ctx->tbm : ctx->tb;
-    const int tc = std::min(64, (FE_W * 32) / tb.NKG);
-    if (tc < 1) return 0;
+    const int tc = FSE_TC;
     const size_t smem = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + (((size_t)FSE_NBUF * tc * (tb.G8 + 1) * (mass ? 4 : 8) + 15) & ~(size_t)15) +
                         (size_t)FSE_NBUF * tc * sizeof(CellInfo) + 2 * FSE_NBUF * sizeof(uint64_t) + 16;
     if (smem > 160 * 1024) return 0;
