@@ -95,6 +95,7 @@ struct ScratchView {
     int *order;    // [C] the cells in emission order (temperature classes)
     uint16_t *bkt; // [C] each cell's class
     unsigned *hist;  // [2][NBK] cells per class, then the scatter cursors
+    float2 *accp;  // [C][NKG][4] emission sums carried between grain passes (NULL: one pass)
 };
 
 // One request of the solve / emission kernels.
@@ -109,8 +110,12 @@ struct EmitReq {
     CellInfo *cell;
     float2 *part;
     const int *order;  // emission order of the request's cells (NULL: ascending)
-    int TC, GC, resident, mode;
-    int nth;        // emission threads per CTA (256: two CTAs per SM; 512: one, for streamed weights)
+    float2 *accp;      // sums carried between grain passes, [C][NKG][4] float2
+    int TC, mode;
+    int g0, g1;     // grains [g0, g1) this entry emits: a pass, when the weights of every
+                    // k-group for all grains exceed shared memory (multiples of RG)
+    int gcp;        // grains per pass of the request's plan
+    int64_t unit_begin, tpu;  // two-kernel emission: first work unit, tiles per unit
     uint32_t smem;  // its emission kernel's shared memory
 };
 
@@ -119,6 +124,8 @@ struct EmitBatch {
     int64_t ntiles, ncells;
     EmitReq req[MAXREQ];
 };
+// The two-kernel emission: tiles of its work units (one CTA each).
+constexpr int KE_TC = 32;
 
 // One request of the cell ordering: a positive float key per cell at
 // key[c * kstride] (an absorbed power or an inverse temperature of one
@@ -144,8 +151,12 @@ struct SolveList {
     EmitReq req[MAXREQ];
 };
 
+// Emission geometry of a request in the two-kernel form: its grains are
+// emitted in passes of gcp (all of them when the weights of every k-group
+// for all grains fit in shared memory beside the pair tiles), smem bytes per
+// CTA.
 struct EmitPlan {
-    int TC, GC, resident, nth;
+    int TC, gcp;
     size_t smem;
 };
 
@@ -304,7 +315,7 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
 // on `st` between the two kernels.
 // With solved = true the temperatures, pairs and cell records are already
 // there (fused absorption + solve) and only the emission runs.
-int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, cudaEvent_t between = nullptr,
+int launch_emit_batch(EmitBatch &B, int num_sms, cudaStream_t st, cudaEvent_t between = nullptr,
                       bool solved = false, int *nlaunch = nullptr);
 
 // Orders the cells of every request of the batch by the class of its key

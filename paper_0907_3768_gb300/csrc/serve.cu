@@ -212,11 +212,20 @@ std::vector<Part> build_round(dust_server *s) {
     return parts;
 }
 
-// Scratch of one part: rows c0.. of its request's S, (1/T, n) pairs and cell records.
+// Scratch of one part: rows c0.. of its request's S, (1/T, n) pairs, cell
+// records, residual partials and grain-pass sums.  Parts are emitted in
+// ascending cell order (no class ordering), so order, classes and counts stay
+// unset.
 ScratchView part_view(const Part &p) {
     const ScratchView v = scratch_view(p.r->ctx, p.r->C, p.r->S);
-    return {v.S + p.c0 * p.r->ctx->tb.Gs, v.prep + p.c0 * p.r->ctx->tb.G8, v.cell + p.c0,
-            v.part + p.c0 * p.r->ctx->tb.NKG};
+    const DevTables &tb = p.r->ctx->tb;
+    ScratchView w{};
+    w.S = v.S + p.c0 * tb.Gs;
+    w.prep = v.prep + p.c0 * tb.G8;
+    w.cell = v.cell + p.c0;
+    w.part = v.part + p.c0 * tb.NKG;
+    w.accp = v.accp ? v.accp + p.c0 * tb.NKG * 4 : nullptr;
+    return w;
 }
 
 int launch_round(dust_server *s, const std::vector<Part> &parts) {
@@ -275,8 +284,6 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
     // solve + emission over every chunk of the round
     EmitBatch E;
     E.nreq = 0;
-    size_t smem = 0;
-    bool emit = false, resid = false;
     for (const Part &p : parts) {
         ServeReq *r = p.r;
         dust_ctx *ctx = r->ctx;
@@ -285,13 +292,11 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
         fill_emit_req(ctx, pl, p.cn, part_view(p), r->n + p.c0 * G, r->T + p.c0 * G,
                       r->L ? r->L + p.c0 * r->ld : nullptr, r->ld, r->resid ? r->resid + p.c0 : nullptr,
                       r->flags ? r->flags + p.c0 * G : nullptr, E.req[E.nreq++], false);
-        smem = std::max(smem, pl.smem);
-        emit = emit || r->L || r->resid;
-        resid = resid || r->resid;
     }
-    int rc = launch_emit_batch(E, smem, s->num_sms, s->st);
+    int nl = 0;
+    int rc = launch_emit_batch(E, s->num_sms, s->st, nullptr, false, &nl);
     if (rc != DUST_OK) return rc;
-    s->launches += 1 + (emit ? 1 : 0) + (resid ? 1 : 0);
+    s->launches += (uint64_t)nl;
     return DUST_OK;
 }
 

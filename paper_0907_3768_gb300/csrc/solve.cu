@@ -154,7 +154,7 @@ int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_
             if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[2], st));
             rc = launch_solve_emit_fused(B.req[0], ftc, fsmem, ctx->num_sms, st, &nl);
         } else {
-            rc = launch_emit_batch(B, p.smem, ctx->num_sms, st, prof ? ev[2] : nullptr, fused, &nl);
+            rc = launch_emit_batch(B, ctx->num_sms, st, prof ? ev[2] : nullptr, fused, &nl);
         }
         ctx->launches += (uint64_t)nl;
         if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[3], st));

@@ -47,8 +47,6 @@
 namespace dust {
 namespace {
 
-constexpr int NTH = 256;      // emission threads per CTA (resident weights; 512 when streamed)
-constexpr int EMIT_STREAM_NTH = 512;  // threads of the streamed-weights emission CTA
 constexpr int SOLVE_TH = 128; // solve threads per CTA (one warp per cell)
 constexpr int NB_MAX = 4;     // grains per lane per pass in the solve, at most
 // temperature-only solve: CTAs of SOLVE_TH per SM (measured best: 8 at up to 3 grains per
@@ -297,7 +295,9 @@ constexpr float A_MID = -12.f;
 //   regime test is exact for every term of the group.
 // Every lane's arithmetic depends only on its own cell, so results are the
 // same in any batch, kernel or lane arrangement.
-template <bool MASS, int PST>
+// GLB: tn is the cell's row of the solve's scratch in global memory, read
+// through the read-only path (L1), instead of a shared-memory tile.
+template <bool MASS, int PST, bool GLB = false>
 __device__ __forceinline__ void emit_item(const float *tn, const float4 *cp, int gn, const float2 (&nax2)[4],
                                           float naxl, float2 (&acc)[4]) {
     for (int gg0 = 0; gg0 < gn; gg0 += RG) {
@@ -305,10 +305,11 @@ __device__ __forceinline__ void emit_item(const float *tn, const float4 *cp, int
 #pragma unroll
         for (int u = 0; u < RG; ++u) {
             if (MASS) {
-                iT[u] = tn[(gg0 + u) * PST];
+                iT[u] = GLB ? __ldg(tn + (gg0 + u) * PST) : tn[(gg0 + u) * PST];
                 nv[u] = 0.f;
             } else {
-                const float2 pr = *reinterpret_cast<const float2 *>(tn + (gg0 + u) * PST);
+                const float2 *pp = reinterpret_cast<const float2 *>(tn + (gg0 + u) * PST);
+                const float2 pr = GLB ? __ldg(pp) : *pp;
                 iT[u] = pr.x;
                 nv[u] = pr.y;
             }
@@ -394,18 +395,6 @@ __device__ __forceinline__ int64_t ordered_cell(const EmitReq &q, int64_t i) {
     return q.order ? (int64_t)__ldg(q.order + i) : i;
 }
 
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Epilogue of one emission item (one cell, the 8 wavelengths of k-group
 // ikg) in the warp-specialized kernel, the same arithmetic in the same order
@@ -463,201 +452,169 @@ __device__ __forceinline__ void emit_item_out(const EmitReq &q, int64_t cell, in
     if (rs) q.part[cell * tb.NKG + ikg] = make_float2(sh, sl);
 }
 
-// Request and first cell of global emission tile `tile`.
-__device__ __forceinline__ int emit_req_of(const EmitBatch &B, int64_t tile, int ri) {
-    while (ri + 1 < B.nreq && tile >= B.req[ri + 1].tile_begin) ++ri;
-    return ri;
-}
+// ---- the two-kernel emission: pairs from the solve kernel's scratch
+// k_emit runs over a work list of requests whose temperatures are solved,
+// each split into work units of up to tpu tiles (32 cells in the request's
+// emission order), one CTA per unit, so that a CTA serves one request and
+// loads its weights once.  Where the weights of every k-group for all grains
+// do not fit in shared memory beside the pair tiles, a request is emitted
+// in passes over grain chunks [g0, g1): a pass starts its sums from those
+// the previous pass left in the scratch (accp) and the last one finishes
+// them, so every item adds its groups in the same order as one pass would.
+// Per CTA one copier warp fills KE_NBUF pair-tile buffers from the scratch
+// (cp.async, 8 bytes per pair) and KE_W emission warps claim the items in
+// order (one k-group of one tile, its cells on the 32 lanes, emit_item), the
+// longest wavelengths of a tile first.  Hand-over through monotone counters
+// per buffer: the copier adds 1 to filled[b] per tile, emission warps add 1
+// to drained[b] per item; the i-th tile of the unit (buffer i % KE_NBUF) is
+// emitted once filled[b] >= i / KE_NBUF + 1, and refilled once drained[b]
+// counts every item of the tiles put there before it.  Waits poll with a
+// short sleep, are bounded, and record DUST_ETIMEOUT.
+constexpr int KE_W = 15;                // emission warps
+constexpr int KE_TH = (KE_W + 1) * 32;  // and one copier warp: 512 threads, 128 registers
+constexpr int KE_NBUF = 3;
 
-// Issue the cp.async copies of a tile's (1/T, n) pairs into the pair-major
-// shared layout [pair][grain][2 cells] (padding cells of a ragged tile read
-// the dummy values instead).  Tile slots follow the request's emission order.
-template <bool MASS, int NT>
-__device__ __forceinline__ void prefetch_tile(const EmitReq &q, int64_t local_tile, float *dstTN, int TNP, int tid) {
-    const int G8 = q.tb.G8, TC = q.TC;
-    const int64_t c0 = local_tile * TC;
-    const int nc = (int)((q.C - c0) < (int64_t)TC ? (q.C - c0) : (int64_t)TC);
-    // (c, g) of element i = tid + j NT, advanced without a division per step
-    const int dc = NT / G8, dg = NT - dc * G8;
-    int c = tid / G8, g = tid - c * G8;
-    for (int i = tid; i < TC * G8; i += NT) {
-        if (MASS) {  // 1/T only: [pair][grain][2 cells] floats
-            float *dst = dstTN + (size_t)(c >> 1) * TNP + 2 * g + (c & 1);
-            if (c < nc) cp_async4(dst, reinterpret_cast<const float *>(q.prep) + ordered_cell(q, c0 + c) * G8 + g);
-            else *dst = PAD_INV_T;
-        } else {  // (1/T, n): [pair][grain][2 cells] float2
-            float *dst = dstTN + (size_t)(c >> 1) * TNP + 4 * g + 2 * (c & 1);
-            if (c < nc) cp_async8(dst, q.prep + ordered_cell(q, c0 + c) * G8 + g);
-            else *reinterpret_cast<float2 *>(dst) = make_float2(PAD_INV_T, 0.f);
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ int ld_acquire_cta(const int *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void add_release_cta(int *p, int v) {
+    asm volatile("red.release.cta.shared.add.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+// Lane 0 waits until *ctr >= target (bounded, polling with a short sleep);
+// the warp learns the outcome and is ordered after the writes it waited for.
+__device__ __forceinline__ bool warp_wait_geq(const int *ctr, int target, volatile int *abort_flag, int *status,
+                                              int lane) {
+    int ok = 1;
+    if (lane == 0 && ld_acquire_cta(ctr) < target) {
+        const unsigned long long t0 = globaltimer_ns();
+        for (;;) {
+            __nanosleep(100);
+            if (ld_acquire_cta(ctr) >= target) break;
+            if (*abort_flag) { ok = 0; break; }
+            if (globaltimer_ns() - t0 > WAIT_NS) {
+                *abort_flag = 1;
+                record_status(status, DUST_ETIMEOUT);
+                ok = 0;
+                break;
+            }
         }
-        c += dc;
-        g += dg;
-        if (g >= G8) { g -= G8; ++c; }
     }
-    cp_async_commit();
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
 }
 
-template <bool MASS, int NT>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) k_emit(const __grid_constant__ EmitBatch B) {
+template <bool MASS>
+__global__ void __launch_bounds__(KE_TH, 1) k_emit(const __grid_constant__ EmitBatch B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int tid = threadIdx.x;
+    constexpr int TC = KE_TC;
+    constexpr int PW = MASS ? 1 : 2;  // floats per pair
+    int ri = 0;
+    while (ri + 1 < B.nreq && (int64_t)blockIdx.x >= B.req[ri + 1].unit_begin) ++ri;
+    const EmitReq &q = B.req[ri];
+    const DevTables &tb = q.tb;
+    const int G8 = tb.G8, NKG = tb.NKG, gc = q.g1 - q.g0, PS = gc + 1, CST = 2 * gc + 1;
+    const int64_t ntiles = (q.C + TC - 1) / TC;
+    const int64_t t0 = ((int64_t)blockIdx.x - q.unit_begin) * q.tpu;
+    const int ntl = (int)min(q.tpu, ntiles - t0);
+    // shared memory: counters, the pair buffers [KE_NBUF][TC][PS][PW], the weights [NKG][CST] of the grain chunk
+    int *filled = reinterpret_cast<int *>(smem_raw);  // [KE_NBUF]
+    int *drained = filled + 4;                        // [KE_NBUF]
+    int *claim = drained + 4;
+    volatile int *abort_flag = claim + 1;
+    float *sP = reinterpret_cast<float *>(smem_raw + 64);
+    float4 *sC = reinterpret_cast<float4 *>(sP + (((size_t)KE_NBUF * TC * PS * PW + 3) & ~(size_t)3));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
+        for (int i = tid; i < NKG * 2 * gc; i += KE_TH) {
+            const int kg = i / (2 * gc), o = i - kg * 2 * gc;
+            sC[(size_t)kg * CST + o] = __ldg(src + ((size_t)kg * G8 + q.g0) * 2 + o);
+        }
+    }
+    if (tid < 4) { filled[tid] = 0; drained[tid] = 0; }
+    if (tid == 0) { *claim = 0; *abort_flag = 0; }
+    __syncthreads();
+    if (ntl <= 0) return;
 
-    int cur = -1;
-    // per-request layout: Chat [NKG][CST] float4 | two (1/T, n) tiles [NP+1][TNP]
-    // The emission item of a thread is one k-group (8 wavelengths) of two
-    // neighbouring cells; items run k-group-major over the threads, so the
-    // lanes of a warp share few k-groups (Chat loads are near-broadcasts) and
-    // one 16-byte load fetches (1/T, n) of both cells of a pair.
-    int oTN = 0, TNP = 0, CST = 0, TNB = 0;
-    int ipair = 0, ikg = 0, buf = 0;
-    int64_t pref = -1;  // global tile whose pairs sit (or are landing) in buffer `buf`
-
-    for (int64_t tile = blockIdx.x; tile < B.ntiles; tile += gridDim.x) {
-        int ri = emit_req_of(B, tile, cur < 0 ? 0 : cur);
-        const EmitReq &q = B.req[ri];
-        const DevTables &tb = q.tb;
-        const int G8 = tb.G8, NKG = tb.NKG, K = tb.K, TC = q.TC, NP = TC / 2;
-        const bool rs = (q.mode & EMIT_RESID) != 0;
-        if (ri != cur) {
-            __syncthreads();  // the previous request is done with shared memory
+    if (warp == KE_W) {
+        // ------------------------------------------------------------ copier
+        int expect[KE_NBUF] = {};  // items of the tiles put in each buffer so far
+        for (int i = 0; i < ntl; ++i) {
+            const int b = i % KE_NBUF;
+            if (!warp_wait_geq(&drained[b], expect[b], abort_flag, tb.status, lane)) break;
+            const int64_t c0 = (t0 + i) * TC;
+            const int nc = (int)min((int64_t)TC, q.C - c0);
+            float *dst = sP + (size_t)b * TC * PS * PW;
+            // row c of the buffer <- grains [g0, g1) of the pairs of cell order[c0 + c]
+            const int64_t mycell = lane < nc ? ordered_cell(q, c0 + lane) : 0;
+            for (int c = 0; c < nc; ++c) {
+                const int64_t cell = __shfl_sync(0xffffffffu, mycell, c);
+                for (int g = lane; g < gc; g += 32) {
+                    if (MASS) cp_async4(dst + (size_t)c * PS + g, reinterpret_cast<const float *>(q.prep) + cell * G8 + q.g0 + g);
+                    else cp_async8(dst + ((size_t)c * PS + g) * 2, q.prep + cell * G8 + q.g0 + g);
+                }
+            }
+            cp_async_commit();
             cp_async_wait_all();
-            cur = ri;
-            TNP = (MASS ? 2 : 4) * G8 + 4;
-            CST = 2 * (q.resident ? G8 : q.GC) + 1;
-            TNB = (NP + 1) * TNP;  // floats per (1/T, n) tile buffer
-            oTN = NKG * CST * 16;
-            const bool okit = tid < NP * NKG;
-            ikg = okit ? tid / NP : 0;
-            ipair = okit ? tid - ikg * NP : NP;  // idle threads read the dummy pair row NP
-            for (int b = 0; b < 2; ++b) {
-                float *dummy = reinterpret_cast<float *>(smem_raw + oTN) + (size_t)b * TNB + (size_t)NP * TNP;
-                for (int g = tid; g < G8; g += NT) {
-                    if (MASS) *reinterpret_cast<float2 *>(dummy + 2 * g) = make_float2(PAD_INV_T, PAD_INV_T);
-                    else *reinterpret_cast<float4 *>(dummy + 4 * g) = make_float4(PAD_INV_T, 0.f, PAD_INV_T, 0.f);
-                }
-            }
-            if (q.resident) {
-                const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
-                float4 *dst = reinterpret_cast<float4 *>(smem_raw);
-                for (int i = tid; i < NKG * 2 * G8; i += NT) {
-                    const int kg = i / (2 * G8), o = i - kg * 2 * G8;
-                    dst[(size_t)kg * CST + o] = __ldg(src + i);
-                }
-            }
-            pref = -1;
+            __syncwarp();
+            if (lane == 0) add_release_cta(&filled[b], 1);
+            expect[b] += NKG;
         }
-        float4 *sC = reinterpret_cast<float4 *>(smem_raw);
-        float *sTN0 = reinterpret_cast<float *>(smem_raw + oTN);
-        const int64_t lt = tile - q.tile_begin;
-        const int64_t c0 = lt * TC;
-        const int nc = (int)((q.C - c0) < (int64_t)TC ? (q.C - c0) : (int64_t)TC);
-        __syncthreads();  // previous tile finished with shared memory
-        if (pref != tile) {  // not prefetched (first tile of a request)
-            buf = 0;
-            prefetch_tile<MASS, NT>(q, lt, sTN0, TNP, tid);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        float *sTN = sTN0 + (size_t)buf * TNB;
-        // prefetch the next tile of this request into the other buffer
-        const int64_t nt = tile + gridDim.x;
-        if (nt < B.ntiles && emit_req_of(B, nt, ri) == ri) {
-            prefetch_tile<MASS, NT>(q, nt - q.tile_begin, sTN0 + (size_t)(buf ^ 1) * TNB, TNP, tid);
-            pref = nt;
-        } else {
-            pref = -1;
-        }
-        // ---- emission (two cells x 8 wavelengths per thread)
-        float2 acc[2][4], nax2[4];
-        const float naxl = load_nax(tb, ikg, nax2);
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            acc[0][p] = make_float2(0.f, 0.f);
-            acc[1][p] = make_float2(0.f, 0.f);
-        }
-        const int GC = q.resident ? G8 : q.GC;
-        for (int g0 = 0; g0 < G8; g0 += GC) {
-            const int gn = min(GC, G8 - g0);
-            if (!q.resident) {
-                __syncthreads();
-                const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
-                for (int i = tid; i < NKG * 2 * gn; i += NT) {
-                    const int kg = i / (2 * gn), o = i - kg * 2 * gn;
-                    sC[(size_t)kg * CST + o] = __ldg(src + ((size_t)kg * G8 + g0) * 2 + o);
-                }
-                __syncthreads();
-            }
-            const int goff = q.resident ? g0 : 0;
-            const float *tnp = sTN + (size_t)ipair * TNP + (MASS ? 2 : 4) * g0;
-            const float4 *cp = sC + (size_t)ikg * CST + 2 * goff;
-            emit_item<MASS, MASS ? 2 : 4>(tnp, cp, gn, nax2, naxl, acc[0]);
-            emit_item<MASS, MASS ? 2 : 4>(tnp + (MASS ? 1 : 2), cp, gn, nax2, naxl, acc[1]);
-        }
-        // ---- epilogue: scale, store, residual partials.  An item's 8
-        // wavelengths of a cell are one 32-byte sector of L, written as two
-        // 16-byte stores when the rows allow it.  The 8-term partial
-        // sum_k w_k L_k of an item is accumulated error-free in float-float
-        // (products split by FMA, sums by two-sum).
-        const bool storeL = (q.mode & EMIT_STORE_L) != 0;
+    } else {
+        // ------------------------------------------------------------ emission
+        const bool first = q.g0 == 0, last = q.g1 == G8;
+        const bool rs = (q.mode & EMIT_RESID) != 0, storeL = (q.mode & EMIT_STORE_L) != 0;
         const bool vecL = storeL && ((reinterpret_cast<uintptr_t>(q.L) & 15) == 0) && (q.ld % 4 == 0);
+        for (;;) {
+            int w = 0;
+            if (lane == 0) w = atomicAdd(claim, 1);
+            w = __shfl_sync(0xffffffffu, w, 0);
+            const int i = w / NKG;
+            if (i >= ntl) break;
+            const int ikg = NKG - 1 - (w - i * NKG);
+            const int b = i % KE_NBUF;
+            if (!warp_wait_geq(&filled[b], i / KE_NBUF + 1, abort_flag, tb.status, lane)) break;
+            const int64_t c0 = (t0 + i) * TC;
+            const int nc = (int)min((int64_t)TC, q.C - c0);
+            if (lane < nc) {
+                const int64_t cell = ordered_cell(q, c0 + lane);
+                float2 nax2[4], acc[4];
+                const float naxl = load_nax(tb, ikg, nax2);
+                float2 *ap = q.accp + ((size_t)cell * NKG + ikg) * 4;
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int c = 2 * ipair + r;
-            if (c >= nc) continue;
-            const int64_t cell = ordered_cell(q, c0 + c);
-            const CellInfo ci = q.cell[cell];
-            const int mc = ci.mc;
-            const float ms = MASS ? __int_as_float(ci.ms_bits) : 1.f;  // the cell's mass mantissa
-            float sh = 0.f, sl = 0.f;
-            const int kb = ikg * KQ;
-            float Lv[KQ];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int k = min(kb + 2 * p + h, K - 1);
-                    const float a = h ? acc[r][p].y : acc[r][p].x;
-                    Lv[2 * p + h] = scale2(MASS ? a * ms : a, mc + __ldg(tb.qexp + k));
-                }
-            }
-            if (storeL) {
-                float *row = q.L + cell * q.ld + kb;
-                if (vecL && kb + KQ <= K) {
-                    reinterpret_cast<float4 *>(row)[0] = make_float4(Lv[0], Lv[1], Lv[2], Lv[3]);
-                    reinterpret_cast<float4 *>(row)[1] = make_float4(Lv[4], Lv[5], Lv[6], Lv[7]);
+                for (int p = 0; p < 4; ++p) acc[p] = first ? make_float2(0.f, 0.f) : ap[p];
+                emit_item<MASS, PW>(sP + ((size_t)b * TC + lane) * PS * PW, sC + (size_t)ikg * CST, gc, nax2, naxl, acc);
+                if (last) {
+                    const CellInfo ci = q.cell[cell];
+                    emit_item_out<MASS>(q, cell, ikg, acc, ci.mc, MASS ? __int_as_float(ci.ms_bits) : 1.f, storeL, vecL,
+                                        rs);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < KQ; ++j)
-                        if (kb + j < K) row[j] = Lv[j];
+                    for (int p = 0; p < 4; ++p) ap[p] = acc[p];
                 }
             }
-            if (rs) {
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int k = kb + 2 * p + h;
-                        if (k < K) {
-                            // w_k L_k 2^-(m_c + Ew) = wq_k a: the FP32 accumulator before
-                            // its power-of-two scaling (equal to the stored L unless L is subnormal)
-                            const float a = h ? acc[r][p].y : acc[r][p].x;
-                            const float wk = __ldg(tb.wq + k);
-                            const float pr = wk * a;
-                            ff_add(sh, sl, pr, fmaf(wk, a, -pr));
-                        }
-                    }
-                }
-            }
-            if (rs) q.part[cell * NKG + ikg] = make_float2(sh, sl);
+            __syncwarp();
+            if (lane == 0) add_release_cta(&drained[b], 1);
         }
-        buf ^= 1;
     }
-    cp_async_wait_all();
 }
 
-// Energy-balance residual of every cell of the requests that want it: one
-// thread per cell sums the cell's k-group partials in ascending order, so
-// the order depends only on NKG.
 // Solve and emission of one request in one warp-specialized kernel, for
 // either form of n (general, or the dust-mass form n_g m_c with 1/T-only
 // pairs), with the emission weights resident in shared memory.
@@ -801,6 +758,9 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
     }
 }
 
+// Energy-balance residual of every cell of the requests that want it: one
+// thread per cell sums the cell's k-group partials in ascending order, so
+// the order depends only on NKG.
 __global__ void __launch_bounds__(SOLVE_TH) k_resid(const __grid_constant__ EmitBatch E) {
     const int64_t stride = (int64_t)gridDim.x * SOLVE_TH;
     int ri = 0;
@@ -823,34 +783,26 @@ __global__ void __launch_bounds__(SOLVE_TH) k_resid(const __grid_constant__ Emit
 
 }  // namespace
 
-// Emission geometry of one request: cells per tile, grain chunk, residency
-// of the emission weights and the shared memory they need.
+// Emission geometry of one request in the two-kernel form: 32-cell tiles,
+// KE_NBUF pair buffers and the weights of every k-group for a chunk of gcp
+// grains in shared memory; all grains when they fit, otherwise the largest
+// chunk (a multiple of RG) that does.
+namespace {
+size_t ke_smem(int NKG, int gc, bool mass) {
+    return 64 + (((size_t)KE_NBUF * KE_TC * (gc + 1) * (mass ? 1 : 2) * 4 + 15) & ~(size_t)15) +
+           (size_t)NKG * (2 * gc + 1) * 16;
+}
+}  // namespace
+
 EmitPlan plan_emit(const dust_ctx *ctx, bool emit, bool mass) {
-    const DevTables &tb = ctx->tb;
+    const DevTables &tb = mass ? ctx->tbm : ctx->tb;
     EmitPlan p{};
-    auto fixed_of = [&](int np) { return (size_t)2 * (np + 1) * ((mass ? 2 : 4) * tb.G8 + 4) * 4 + 64; };
-    int NP = std::max(1, std::min(32, NTH / tb.NKG));  // cell pairs per tile
-    p.TC = 2 * NP;
-    p.nth = NTH;
-    if (!emit) { p.GC = tb.G8; p.resident = 0; p.smem = 0; return p; }
-    const size_t budget = 113 * 1024;  // two CTAs per SM
-    const size_t full = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + fixed_of(NP);
-    if (full <= budget) { p.GC = tb.G8; p.resident = 1; p.smem = full; return p; }
-    // streamed weights: one CTA of 2 NTH threads per SM, twice the cells per
-    // tile and the whole shared memory for the grain chunks, so that each
-    // staged chunk serves more cells and fewer barriers are paid per cell
-    p.nth = EMIT_STREAM_NTH;
-    const size_t budget2 = ctx->smem_optin ? ctx->smem_optin - 1024 : budget;
-    NP = std::max(1, std::min(32, p.nth / tb.NKG));
-    while (NP > 1 && fixed_of(NP) + (size_t)tb.NKG * (2 * RG + 1) * 16 > budget2) --NP;  // room for a chunk
-    p.TC = 2 * NP;
-    const size_t fixed = fixed_of(NP);
-    const size_t avail = budget2 > fixed ? budget2 - fixed : 0;
-    int gc = (int)((avail / ((size_t)tb.NKG * 16) - 1) / 2) / RG * RG;
-    gc = std::max(RG, std::min(gc, tb.G8));
-    p.GC = gc;
-    p.resident = 0;
-    p.smem = (size_t)tb.NKG * (2 * gc + 1) * 16 + fixed;
+    p.TC = KE_TC;
+    p.gcp = tb.G8;
+    if (!emit) { p.smem = 0; return p; }
+    const size_t budget = (ctx->smem_optin ? ctx->smem_optin : 99 * 1024) - 1024;
+    while (p.gcp > RG && ke_smem(tb.NKG, p.gcp, mass) > budget) p.gcp -= RG;
+    p.smem = ke_smem(tb.NKG, p.gcp, mass);
     return p;
 }
 
@@ -865,9 +817,11 @@ inline size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 size_t scratch_bytes(const dust_ctx *ctx, int64_t C, bool emit) {
     size_t b = al16((size_t)C * ctx->tb.Gs * 4);
-    if (emit)
+    if (emit) {
         b += al16((size_t)C * ctx->tb.G8 * 8) + (size_t)C * sizeof(CellInfo) + al16((size_t)C * ctx->tb.NKG * 8) +
              al16((size_t)C * 4) + al16((size_t)C * 2) + (size_t)2 * NBK * 4;
+        if (plan_emit(ctx, true, false).gcp < ctx->tb.G8) b += (size_t)C * ctx->tb.NKG * 32;
+    }
     return b;
 }
 
@@ -887,6 +841,8 @@ ScratchView scratch_view(const dust_ctx *ctx, int64_t C, void *base) {
     v.bkt = reinterpret_cast<uint16_t *>(p);
     p += al16((size_t)C * 2);
     v.hist = reinterpret_cast<unsigned *>(p);
+    p += (size_t)2 * NBK * 4;
+    v.accp = plan_emit(ctx, true, false).gcp < ctx->tb.G8 ? reinterpret_cast<float2 *>(p) : nullptr;
     return v;
 }
 
@@ -907,10 +863,13 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
     r.cell = sv.cell;
     r.part = sv.part;
     r.order = nullptr;
+    r.accp = sv.accp;
     r.TC = p.TC;
-    r.GC = p.GC;
-    r.resident = p.resident;
-    r.nth = p.nth;
+    r.g0 = 0;
+    r.g1 = p.gcp;  // the first pass; launch_emit_batch adds the others
+    r.gcp = p.gcp;
+    r.unit_begin = 0;
+    r.tpu = 1;
     r.smem = (uint32_t)p.smem;
     r.mode = ((L || resid) ? EMIT_ON : 0) | (resid ? EMIT_RESID : 0) | (L ? EMIT_STORE_L : 0) |
              ((mass && (L || resid)) ? EMIT_MASS : 0);
@@ -918,7 +877,7 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
 
 // Numbers the cells and emission tiles of a filled batch; launches the solve
 // over every request, then the emission over the requests that want it.
-int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, cudaEvent_t between,
+int launch_emit_batch(EmitBatch &B, int num_sms, cudaStream_t st, cudaEvent_t between,
                       bool solved, int *nlaunch) {
     int nl = 0;
     int64_t cells = 0;
@@ -957,57 +916,86 @@ int launch_emit_batch(EmitBatch &B, size_t smem, int num_sms, cudaStream_t st, c
         ++nl;
     }
     if (between) DUST_CUDA_TRY(cudaEventRecord(between, st));
-    // emission work lists: the requests that want L or resid, in order, one
-    // list (and launch) per form of the grain numbers and CTA size
+    // emission work lists: the requests that want L or resid, one entry per
+    // grain pass, in pass order; one list per form of the grain numbers,
+    // split at MAXREQ entries.  Tiles per work unit: about two units per SM
+    // over the list, at least one tile.
     for (int form = 0; form < 2; ++form) {
-        for (int nt : {NTH, EMIT_STREAM_NTH}) {
-            EmitBatch E;
-            E.nreq = 0;
+        const bool mass = form == 1;
+        EmitBatch E;
+        E.nreq = 0;
+        auto flush = [&]() -> int {
+            if (E.nreq == 0) return DUST_OK;
             int64_t tiles = 0;
-            size_t lsmem = 0;
-            for (int i = 0; i < B.nreq; ++i) {
-                if (!(B.req[i].mode & EMIT_ON) || ((B.req[i].mode & EMIT_MASS) != 0) != (form == 1) ||
-                    B.req[i].nth != nt)
-                    continue;
-                EmitReq &r = E.req[E.nreq++];
-                r = B.req[i];
-                r.tile_begin = tiles;
-                tiles += (r.C + r.TC - 1) / r.TC;
-                lsmem = std::max(lsmem, (size_t)r.smem);
+            size_t smem = 0;
+            for (int k = 0; k < E.nreq; ++k) {
+                tiles += (E.req[k].C + KE_TC - 1) / KE_TC;
+                smem = std::max(smem, (size_t)E.req[k].smem);
+            }
+            const int64_t tpu = std::max<int64_t>(1, (tiles + 2 * num_sms - 1) / (2 * num_sms));
+            int64_t units = 0;
+            for (int k = 0; k < E.nreq; ++k) {
+                E.req[k].unit_begin = units;
+                E.req[k].tpu = tpu;
+                units += ((E.req[k].C + KE_TC - 1) / KE_TC + tpu - 1) / tpu;
             }
             E.ntiles = tiles;
-            E.ncells = 0;
-            bool resid = false;
-            for (int i = 0; i < E.nreq; ++i) {  // cells of the emission list, numbered afresh
-                E.req[i].cell_begin = E.ncells;
-                E.ncells += E.req[i].C;
-                resid = resid || (E.req[i].mode & EMIT_RESID);
-            }
-            if (tiles == 0) continue;
-            const void *kern = form ? (nt == NTH ? reinterpret_cast<const void *>(k_emit<true, NTH>)
-                                                 : reinterpret_cast<const void *>(k_emit<true, EMIT_STREAM_NTH>))
-                                    : (nt == NTH ? reinterpret_cast<const void *>(k_emit<false, NTH>)
-                                                 : reinterpret_cast<const void *>(k_emit<false, EMIT_STREAM_NTH>));
-            DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
-            int per_sm = 0;
-            DUST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, lsmem));
-            per_sm = std::max(per_sm, 1);
-            const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)num_sms * per_sm);
-            if (form) {
-                if (nt == NTH) k_emit<true, NTH><<<grid, NTH, lsmem, st>>>(E);
-                else k_emit<true, EMIT_STREAM_NTH><<<grid, EMIT_STREAM_NTH, lsmem, st>>>(E);
-            } else {
-                if (nt == NTH) k_emit<false, NTH><<<grid, NTH, lsmem, st>>>(E);
-                else k_emit<false, EMIT_STREAM_NTH><<<grid, EMIT_STREAM_NTH, lsmem, st>>>(E);
-            }
+            const void *kern = mass ? reinterpret_cast<const void *>(k_emit<true>) : reinterpret_cast<const void *>(k_emit<false>);
+            DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            if (mass) k_emit<true><<<(unsigned)units, KE_TH, smem, st>>>(E);
+            else k_emit<false><<<(unsigned)units, KE_TH, smem, st>>>(E);
             DUST_CUDA_TRY(cudaGetLastError());
             ++nl;
-            if (resid) {
-                const int64_t rgrid = std::min<int64_t>((E.ncells + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
-                k_resid<<<(unsigned)rgrid, SOLVE_TH, 0, st>>>(E);
-                DUST_CUDA_TRY(cudaGetLastError());
-                ++nl;
+            E.nreq = 0;
+            return DUST_OK;
+        };
+        // pass pi of every request in one list; a pass reads the sums the
+        // previous one wrote, so passes are separate launches
+        for (int i = 0; i < B.nreq; ++i) {
+            const EmitReq &r = B.req[i];
+            if ((r.mode & EMIT_ON) && r.gcp < r.tb.G8 && !r.accp)
+                return set_error(DUST_EINVAL, "request %d needs grain passes but has no buffer for their sums", i);
+        }
+        for (int pi = 0;; ++pi) {
+            bool any = false;
+            for (int i = 0; i < B.nreq; ++i) {
+                const EmitReq &r = B.req[i];
+                if (!(r.mode & EMIT_ON) || ((r.mode & EMIT_MASS) != 0) != mass) continue;
+                const int g0 = pi * r.gcp;
+                if (g0 >= r.tb.G8) continue;
+                any = true;
+                if (E.nreq == MAXREQ) {
+                    int rc = flush();
+                    if (rc != DUST_OK) return rc;
+                }
+                EmitReq &e = E.req[E.nreq++];
+                e = r;
+                e.g0 = g0;
+                e.g1 = std::min(r.tb.G8, g0 + r.gcp);
             }
+            int rc = flush();
+            if (rc != DUST_OK) return rc;
+            if (!any) break;
+        }
+    }
+    // residual fold over the requests that want it (after every pass)
+    {
+        EmitBatch R;
+        R.nreq = 0;
+        R.ncells = 0;
+        R.ntiles = 0;
+        for (int i = 0; i < B.nreq; ++i) {
+            if (!(B.req[i].mode & EMIT_RESID)) continue;
+            EmitReq &e = R.req[R.nreq++];
+            e = B.req[i];
+            e.cell_begin = R.ncells;
+            R.ncells += e.C;
+        }
+        if (R.ncells > 0) {
+            const int64_t rgrid = std::min<int64_t>((R.ncells + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
+            k_resid<<<(unsigned)rgrid, SOLVE_TH, 0, st>>>(R);
+            DUST_CUDA_TRY(cudaGetLastError());
+            ++nl;
         }
     }
     if (nlaunch) *nlaunch = nl;
@@ -1082,7 +1070,7 @@ int launch_solve_emit(const dust_ctx *ctx, int64_t C, const ScratchView &sv, con
     EmitBatch B;
     B.nreq = 1;
     fill_emit_req(ctx, p, C, sv, n, T, L, ld, resid, flags, B.req[0], false);
-    return launch_emit_batch(B, p.smem, ctx->num_sms, st);
+    return launch_emit_batch(B, ctx->num_sms, st);
 }
 
 }  // namespace dust
