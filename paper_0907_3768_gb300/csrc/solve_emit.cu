@@ -599,9 +599,11 @@ __global__ void __launch_bounds__(KE_TH, 1) k_emit(const __grid_constant__ EmitB
                 float2 *ap = q.accp + ((size_t)cell * NKG + ikg) * 4;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) acc[p] = first ? make_float2(0.f, 0.f) : ap[p];
+                // the cell record is read now, so that its latency hides behind the sums
+                CellInfo ci{};
+                if (last) ci = q.cell[cell];
                 emit_item<MASS, PW>(sP + ((size_t)b * TC + lane) * PS * PW, sC + (size_t)ikg * CST, gc, nax2, naxl, acc);
                 if (last) {
-                    const CellInfo ci = q.cell[cell];
                     emit_item_out<MASS>(q, cell, ikg, acc, ci.mc, MASS ? __int_as_float(ci.ms_bits) : 1.f, storeL, vecL,
                                         rs);
                 } else {
