@@ -30,10 +30,54 @@ METRIC = "grain-T solves/s & SED cells/s, mixed vs FP32 at stated err, 1 GB300; 
 UNIT = "grain-T solves/s"
 CONFIG_ID = 1
 WORKLOAD = "2^18 cells x 200 wavelengths (0.09-1000 um) x 96 grains (3 species x 32 sizes), P_g(T) table 4096 pts"
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the step's dominant
-# kernel on this workload, from one `ncu --set full` capture of that launch
-# (None until captured); to be retaken whenever that kernel changes
-DOMINANT_TRAFFIC_BYTES = 206.069504e6 + 337.327616e6
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch,
+# recorded from the capture in the named profile summary, with a hash of the
+# kernel's sources at capture time: a run reports the figure only while the
+# sources still hash the same, and null (with the reason) once they changed.
+KERNEL_SOURCES = {
+    "k_solve_emit": ["solve_emit.cu", "solve_core.cuh", "dust_internal.cuh", "mbar.cuh"],
+    "k_emit": ["solve_emit.cu", "solve_core.cuh", "dust_internal.cuh", "mbar.cuh"],
+    "k_fluct": ["fluct.cu", "solve_core.cuh", "dust_internal.cuh"],
+}
+RECORDED_TRAFFIC = {
+    # kernel: (bytes per launch, profile summary, sources sha256[:16])
+    "k_solve_emit": (None, "profiles/k_solve_emit_2e18cells_K200_G96.md", None),
+    "k_fluct": (None, "profiles/k_fluct_2e14cells_K200_G36_M128.md", None),
+}
+
+
+def _measured_hbm_peak():
+    """HBM copy bandwidth (GB/s) measured on this machine's GPUs, else the profiling fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return 6800.0, "fallback 6.8 TB/s (no measured peak found)"
+
+
+HBM_PEAK, HBM_PEAK_SOURCE = _measured_hbm_peak()
+
+
+def kernel_sources_sha(kernel):
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_0907_3768_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """(bytes or None, note) for the kernel's recorded ncu traffic."""
+    nbytes, prof, sha = RECORDED_TRAFFIC[kernel]
+    now = kernel_sources_sha(kernel)
+    if nbytes is None or sha is None:
+        return None, f"not captured for the current sources (sha {now})"
+    if sha != now:
+        return None, f"sources changed since the capture in {prof} (sha {sha}, now {now})"
+    return nbytes, f"ncu capture in {prof} (sources sha {sha})"
 
 
 def parse():
@@ -282,6 +326,7 @@ def run_ours(args):
     ms_emit = res[main]["prof"][2]
     solve_in_emit = res[main]["prof"][1] < 0.02 * ms_emit
     terms = C * G * K
+    traffic_b, traffic_note = recorded_traffic("k_solve_emit" if solve_in_emit else "k_emit")
     achieved = terms / (ms_emit * 1e-3) / 1e9
     peak = ex2_rate / 1e9
     roofline = {"bound": "alu",
@@ -290,8 +335,9 @@ def run_ours(args):
                 "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "G Planck terms/s",
                 "frac": round(achieved / peak, 4),
                 "peak_source": "measured MUFU ex2.approx issue rate (dust_diag_throughput), 1 ex2 per term",
-                "traffic": DOMINANT_TRAFFIC_BYTES if (C, K, G) == (1 << 18, 200, 96) and world == 1 else None,
+                "traffic": traffic_b if (C, K, G) == (1 << 18, 200, 96) and world == 1 else None,
                 "traffic_unit": "bytes per launch (ncu DRAM read + write)",
+                "traffic_source": traffic_note,
                 "algorithmic_bytes": C * (4 * ((G + 15) // 16 * 16) + 4 * G + 4 * G + G + 16 + 4 * K + 8 * ((K + 7) // 8))
                 if solve_in_emit else C * (8 * ((G + 7) // 8 * 8) + 16 + 4 * K + 8 * ((K + 7) // 8)),
                 "ms_per_launch": round(ms_emit, 4),
@@ -314,7 +360,9 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": aggregate_rate(C * G, world, ms_main * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_main, 5),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"{main} GEMM (16-bit hi/lo split products, f32 accumulate), f32 solve and emission"
+        if main != "fp32" else "f32",
         "data": "synthetic (seeded generators: 2-temperature stellar field x U, toy grain model, MRN sizes)",
         "config": {"workload": WORKLOAD, "precision": main, "cells_per_gpu": C, "K": K, "G": G,
                    "l2": "inputs larger than L2 (J 210 MB, L 210 MB per step)",
@@ -381,10 +429,6 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-# k_fluct DRAM traffic of a 2^14-cell launch at 200 wavelengths, 36 grains, 128 levels
-# (ncu dram__bytes_read.sum + dram__bytes_write.sum: 17.55 MB + 1 KB)
-FLUCT_TRAFFIC_2E14_CELLS = 17.553920e6 + 1.024e3
-
 
 def fluctuating(ctx, wl, J, n, stream, args, world, ex2_rate, oracle_sample):
     """Temperature distributions of the workload's 0.5-10 nm grains (36 of
@@ -424,6 +468,7 @@ def fluctuating(ctx, wl, J, n, stream, args, world, ex2_rate, oracle_sample):
     launches = (_lib_launches(ctx) - l0) / steps
     assert ctx.check() == 0
     terms = C * Gf * (M - 1) * K
+    fl_traffic, fl_note = recorded_traffic("k_fluct")
     r = {"workload": f"{C} cells x {K} wavelengths; {Gf} fluctuating grains of 0.5-10 nm (Einstein enthalpy) "
                      f"x {M} levels; inputs resident in HBM",
          "method": "per (cell, grain): level grid from the equilibrium T, photon-bin heating rates by two prefix "
@@ -434,10 +479,8 @@ def fluctuating(ctx, wl, J, n, stream, args, world, ex2_rate, oracle_sample):
                       "achieved": round(terms / (ms * 1e-3) / 1e9, 1), "peak": round(ex2_rate / 1e9, 1),
                       "frac": round(terms / (ms * 1e-3) / ex2_rate, 4),
                       "peak_source": "measured MUFU ex2.approx rate (dust_diag_throughput)",
-                      "traffic": None,
-                      "traffic_2e14_cells": FLUCT_TRAFFIC_2E14_CELLS if M == 128 and K == 200 else None,
-                      "traffic_note": "full-size launch not captured; ncu DRAM read + write of the first 2^14 cells "
-                                      "(its L writes stay in L2), not scaled: the tables are read once per launch",
+                      "traffic": fl_traffic if M == 128 and K == 200 and fl_traffic is not None else None,
+                      "traffic_source": fl_note,
                       "algorithmic_bytes": C * (2 * K + Gf) * 4}}
     if oracle_sample:
         from oracle import fluct as ofl
@@ -663,7 +706,8 @@ def run_large(args, dev, local, ex2_rate):
                                     "frac": round(C * G * K / (ms_b * 1e-3) / ex2_rate, 4)}
         gbytes = (C * K * 4 + C * ((G + 15) // 16 * 16) * 4) / 1e9
         r["roofline_absorb"] = {"bound": "hbm", "unit": "GB/s", "achieved": round(gbytes / (ms_a * 1e-3), 1),
-                                "peak": 6684.8, "frac": round(gbytes / (ms_a * 1e-3) / 6684.8, 4),
+                                "peak": HBM_PEAK, "frac": round(gbytes / (ms_a * 1e-3) / HBM_PEAK, 4),
+                                "peak_source": HBM_PEAK_SOURCE,
                                 "tensor_TFLOPs_executed": round((3 if prec != "fp32" else 1) * 2 * C * G * K /
                                                                 (ms_a * 1e-3) / 1e12, 1)}
         out[prec] = r

@@ -190,19 +190,24 @@ int dust_solve_host(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, 
  * implicit device synchronisation, memory-capped embeddings.  Same arguments,
  * layouts, ownership and errors as dust_solve with the context's current
  * precision; the caller still provides every input and output buffer.  The
- * scratch (absorbed powers, then the solve's per-grain and per-cell results
- * and the residual's partial sums for the emission: 4 Gs + 8 G8 + 16 + 8 NKG
- * bytes per cell, Gs = G rounded up to 16, G8 to 8, NKG = K / 8 rounded up)
- * lives in one fixed 64 MiB array in the library's device data, which every
- * GPU that loads the library holds until the process exits, so n_cells may
- * not exceed dust_noalloc_max_cells(ctx) (49056 cells for 96 grains and 200
- * wavelengths): larger batches get DUST_EINVAL and must be split.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, no allocation); make that
- * first call before any stream capture.  All calls share the array: calls
- * whose work overlaps on the GPU (different streams, or different contexts on
- * one device) race on it and must be serialised by the caller.  Nothing is
- * left to clear between calls (every scratch value a call reads, it writes
- * first). */
+ * scratch (absorbed powers, then the solve's per-grain and per-cell results,
+ * the residual's partial sums and the emission order: 4 Gs + 8 G8 + 16 +
+ * 8 NKG + 6 bytes per cell and 8 KiB of class counts, Gs = G rounded up to
+ * 16, G8 to 8, NKG = K / 8 rounded up; 32 NKG more per cell for contexts
+ * whose emission weights do not fit in shared memory at once) lives in one
+ * fixed 64 MiB array in the library's device data, which every GPU that
+ * loads the library holds until the process exits, so n_cells may not
+ * exceed dust_noalloc_max_cells(ctx) (48836 cells for 96 grains and 200
+ * wavelengths): larger batches get DUST_EINVAL and must be split.  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, no allocation) and keeps it for the life of the
+ * process: make that first call before any stream capture, and do not reset
+ * the device (cudaDeviceReset reloads the module; a reset device is not
+ * supported).  All calls share the array: calls whose work overlaps on the
+ * GPU (different streams, or different contexts on one device) race on it
+ * and must be serialised by the caller.  Nothing is left to clear between
+ * calls (every scratch value a call reads, it writes first).  Its kernel
+ * launches count in dust_ctx_launch_count. */
 int dust_solve_noalloc(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n,
                        float *T, float *L, double *resid, uint8_t *flags, void *stream);
 

@@ -286,7 +286,7 @@ int launch_gemm_simt(const dust_ctx *ctx, int64_t C, const float *J, int64_t ld,
 int launch_gemm_tc(const dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld,
                    float *S, cudaStream_t st);
 int launch_solve_emit(const dust_ctx *ctx, int64_t C, const ScratchView &sv, const float *n, float *T,
-                      float *L, int64_t ld, double *resid, uint8_t *flags, cudaStream_t st);
+                      float *L, int64_t ld, double *resid, uint8_t *flags, cudaStream_t st, int *nlaunch = nullptr);
 EmitPlan plan_emit(const dust_ctx *ctx, bool emit, bool mass);
 // Scratch bytes of a request of C cells and its layout at `base`.
 size_t scratch_bytes(const dust_ctx *ctx, int64_t C, bool emit);

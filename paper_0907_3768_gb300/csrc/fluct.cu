@@ -563,7 +563,6 @@ extern "C" int dust_ctx_set_fluctuating(dust_ctx *ctx, int Gf, const int *grains
 extern "C" int dust_solve_fluct(dust_ctx *ctx, int64_t n_cells, const float *J, int64_t ld, const float *n,
                                 float *L, float *P, float *dE, void *stream) {
     if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
-    if (!ctx->fl_mem) return set_error(DUST_EINVAL, "no fluctuating grains: call dust_ctx_set_fluctuating");
     if (n_cells < 0) return set_error(DUST_EINVAL, "n_cells < 0");
     if (ld < ctx->K) return set_error(DUST_EINVAL, "ld=%lld < K=%d", (long long)ld, ctx->K);
     if (n_cells == 0) return DUST_OK;
@@ -573,11 +572,14 @@ extern "C" int dust_solve_fluct(dust_ctx *ctx, int64_t n_cells, const float *J, 
         const int r = check_device_ptr(ctx, p);
         if (r != DUST_OK) return r;
     }
+    // the grain set (M, Gf and the tables) is read under the context's lock, in one
+    // snapshot, so that a concurrent dust_ctx_set_fluctuating cannot replace it in between
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->fl_mem) return set_error(DUST_EINVAL, "no fluctuating grains: call dust_ctx_set_fluctuating");
     const int K = ctx->K, M = ctx->fl_M, Gf = ctx->fl_Gf;
     // one problem slot of shared memory per (cell, grain) in flight
     if (sizeof(float) * (((K + 3) & ~3) + fl_warp_floats(K, M)) > (ctx->smem_optin ? ctx->smem_optin : 232448))
         return set_error(DUST_EINVAL, "K=%d, M=%d need more shared memory than one CTA has", K, M);
-    std::lock_guard<std::mutex> lk(ctx->mu);
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return set_error(DUST_ECUDA, "cudaGetDevice failed");
     if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess)

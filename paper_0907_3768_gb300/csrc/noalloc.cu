@@ -11,6 +11,7 @@
 
 #include <mutex>
 
+
 namespace {
 
 // 64 MiB of scratch, resident on every device that loads the library.
@@ -23,7 +24,9 @@ float *g_addr[MAX_DEVICES] = {};  // device address of the array, per device
 
 // Device address of the scratch array on `device` (which must be current).
 // Taken once per device with cudaGetSymbolAddress: in host code the array's
-// name is only a host-side stand-in, not a device address.
+// name is only a host-side stand-in, not a device address.  The address is
+// kept for the life of the process, so a device reset (which reloads the
+// module) is not supported.
 int scratch_address(int device, float **out) {
     if (device < 0 || device >= MAX_DEVICES)
         return dust::set_error(DUST_EINVAL, "device %d beyond the scratch table", device);
@@ -31,9 +34,11 @@ int scratch_address(int device, float **out) {
     if (!g_addr[device]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
             return dust::set_error(DUST_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
                                    cudaGetErrorString(e));
+        }
         g_addr[device] = static_cast<float *>(p);
     }
     *out = g_addr[device];
@@ -71,7 +76,6 @@ extern "C" int dust_solve_noalloc(dust_ctx *ctx, int64_t n_cells, const float *J
                                   float *T, float *L, double *resid, uint8_t *flags, void *stream) {
     using namespace dust;
     if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
-    const int precision = ctx->precision;
     if (n_cells < 0) return set_error(DUST_EINVAL, "n_cells < 0");
     if (ld < ctx->K) return set_error(DUST_EINVAL, "ld=%lld < K=%d", (long long)ld, ctx->K);
     if (n_cells == 0) return DUST_OK;
@@ -84,8 +88,6 @@ extern "C" int dust_solve_noalloc(dust_ctx *ctx, int64_t n_cells, const float *J
                          "for this context): split the batch",
                          (long long)n_cells, scratch_bytes(ctx, n_cells, true), NOALLOC_SCRATCH_BYTES, max_cells);
     if (!J || !n || !T) return set_error(DUST_EINVAL, "J, n and T must be non-NULL");
-    if (precision != DUST_PREC_FP32 && (ld % 4 != 0 || ((uintptr_t)J & 15) != 0))
-        return set_error(DUST_EINVAL, "tensor-core precisions need ld %% 4 == 0 and a 16-byte aligned J");
     int rc;
     if ((rc = check_ptr(J, ctx->device, "J")) || (rc = check_ptr(n, ctx->device, "n")) ||
         (rc = check_ptr(T, ctx->device, "T")) || (L && (rc = check_ptr(L, ctx->device, "L"))) ||
@@ -93,6 +95,10 @@ extern "C" int dust_solve_noalloc(dust_ctx *ctx, int64_t n_cells, const float *J
         (flags && (rc = check_ptr(flags, ctx->device, "flags"))))
         return rc;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    // the precision is read under the lock: the kernel choice and its checks use one value
+    const int precision = ctx->precision;
+    if (precision != DUST_PREC_FP32 && (ld % 4 != 0 || ((uintptr_t)J & 15) != 0))
+        return set_error(DUST_EINVAL, "tensor-core precisions need ld %% 4 == 0 and a 16-byte aligned J");
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return set_error(DUST_ECUDA, "cudaGetDevice failed");
     if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess)
@@ -107,7 +113,12 @@ extern "C" int dust_solve_noalloc(dust_ctx *ctx, int64_t n_cells, const float *J
         const ScratchView sv = scratch_view(ctx, n_cells, S);
         rc = precision == DUST_PREC_FP32 ? launch_gemm_simt(ctx, n_cells, J, ld, sv.S, st)
                                          : launch_gemm_tc(ctx, precision, n_cells, J, ld, sv.S, st);
-        if (rc == DUST_OK) rc = launch_solve_emit(ctx, n_cells, sv, n, T, L, ld, resid, flags, st);
+        if (rc == DUST_OK) {
+            ctx->launches += 1;
+            int nl = 0;
+            rc = launch_solve_emit(ctx, n_cells, sv, n, T, L, ld, resid, flags, st, &nl);
+            ctx->launches += (uint64_t)nl;
+        }
     }
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     return rc;

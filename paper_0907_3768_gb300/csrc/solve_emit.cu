@@ -1066,13 +1066,14 @@ int launch_solve_emit_fused(const EmitReq &req, int TC, size_t smem, int num_sms
 }
 
 int launch_solve_emit(const dust_ctx *ctx, int64_t C, const ScratchView &sv, const float *n, float *T, float *L,
-                      int64_t ld, double *resid, uint8_t *flags, cudaStream_t st) {
+                      int64_t ld, double *resid, uint8_t *flags, cudaStream_t st, int *nlaunch) {
+    if (nlaunch) *nlaunch = 0;
     if (C <= 0) return DUST_OK;
     const EmitPlan p = plan_emit(ctx, L || resid, false);
     EmitBatch B;
     B.nreq = 1;
     fill_emit_req(ctx, p, C, sv, n, T, L, ld, resid, flags, B.req[0], false);
-    return launch_emit_batch(B, ctx->num_sms, st);
+    return launch_emit_batch(B, ctx->num_sms, st, nullptr, false, nlaunch);
 }
 
 }  // namespace dust
