@@ -757,7 +757,7 @@ def run_serving(args, dev, local):
         att = torch.where(op[:, None], torch.exp(-(tau[:, None] * ext[None, :])), torch.ones_like(ext)[None, :])
         Jb[:, :K] = (U[:, None] * shape[None, :] * att).float()
         del att
-        grids[(K, G)] = dict(J=Jb[:, :K], n=(rho[:, None] * n0[None, :]).float().contiguous(), C=C,
+        grids[(K, G)] = dict(J=Jb[:, :K], n=(rho[:, None] * n0[None, :]).float().contiguous(), C=C, wl=wl,
                              mixed=Context.from_workload(wl, precision="bf16x3", device=local),
                              fp32=Context.from_workload(wl, precision="fp32", device=local))
     torch.cuda.synchronize()
@@ -798,23 +798,38 @@ def run_serving(args, dev, local):
     res["rate_hz"] = rate
     res["load"] = args.serve_load
 
+    # the first request of every (K, G) grid is kept for the error against the oracle
+    keep = {}
+    for i, r in enumerate(reqs):
+        keep.setdefault((r["K"], r["G"]), i)
+    keep = set(keep.values())
+
     # Poisson stream through the server
+    lat_srv = np.zeros(len(reqs))
+    kept = {}
     with Server(budget, max_inflight=24, device=local) as srv:
         pend, lag = {}, []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(len(reqs)):
             while time.perf_counter() - t0 < arrivals[i]:
-                for t in [t for t in pend if srv.poll(t)[0] in ("done", "cancelled")]:
-                    del pend[t]
+                for t in list(pend):
+                    state, ms = srv.poll(t)
+                    if state in ("done", "cancelled"):
+                        lat_srv[pend[t][0]] = ms
+                        del pend[t]
                 time.sleep(0.0002)
             lag.append(time.perf_counter() - t0 - arrivals[i])
             g, J, n = inputs(i)
             t, out = g["mixed"].submit(srv, J, n)
-            pend[t] = (J, n, out)
+            pend[t] = (i, J, n, out)
+            if i in keep:
+                kept[i] = (g, J, n, out)
         for t in list(pend):
-            if srv.poll(t)[0] not in ("done", "cancelled"):
-                srv.wait(t, 600000.0)
+            state, ms = srv.poll(t)
+            if state not in ("done", "cancelled"):
+                ms = srv.wait(t, 600000.0)
+            lat_srv[pend[t][0]] = ms
         span = time.perf_counter() - t0
         st = srv.stats()
     res["mixed_server"] = {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
@@ -822,7 +837,10 @@ def run_serving(args, dev, local):
                            "cells_per_s": total_cells / span, "solves_per_s": total_solves / span,
                            "rounds": st["rounds"], "completed": st["completed"],
                            "client_lag_p99_ms": float(np.percentile(lag, 99) * 1e3),
-                           "latency": "submit to completion, server clock"}
+                           "latency": "submit to completion, server clock",
+                           "by_cells_decade": _by_decade(reqs, lat_srv)}
+    res["err_vs_oracle"] = _serving_errors(kept)
+    del kept
 
     # the same stream, one request at a time, FP32
     lat = []
@@ -840,11 +858,63 @@ def run_serving(args, dev, local):
     res["fp32_one_at_a_time"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                                  "max_ms": float(max(lat)), "span_s": span, "requests_per_s": len(reqs) / span,
                                  "solves_per_s": total_solves / span,
-                                 "latency": "arrival to completion (includes queueing behind earlier requests)"}
+                                 "latency": "arrival to completion (includes queueing behind earlier requests)",
+                                 "by_cells_decade": _by_decade(reqs, np.array(lat))}
     for g in grids.values():
         g["mixed"].close()
         g["fp32"].close()
     return res
+
+
+def _by_decade(reqs, lat_ms):
+    """p50 / p99 latency (ms) of the requests in each decade of cell count."""
+    import numpy as np
+
+    cells = np.array([r["n_cells"] for r in reqs])
+    out = {}
+    for lo in (1e3, 1e4, 1e5):
+        m = (cells >= lo) & (cells < lo * 10)
+        if m.any():
+            out[f"{int(lo):d}-{int(lo * 10):d} cells"] = {"requests": int(m.sum()),
+                                                        "p50_ms": float(np.percentile(lat_ms[m], 50)),
+                                                        "p99_ms": float(np.percentile(lat_ms[m], 99))}
+    return out
+
+
+def _serving_errors(kept, ncells=16):
+    """T and L of sampled cells of the kept requests (one per grid) against the oracle."""
+    import numpy as np
+
+    import oracle
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from metrics import l_err, t_err
+
+    worst = {"T_max": 0.0, "L_max": 0.0, "flags_equal": True, "requests": 0, "cells": 0}
+    for i, (g, J, n, out) in sorted(kept.items()):
+        wl = g["wl"]
+        C = J.shape[0]
+        cells = np.unique(np.linspace(0, C - 1, min(ncells, C)).astype(np.int64))
+        idx = torch_index(cells, J.device)
+        Jh = J[idx].double().cpu().numpy()
+        nh = n[idx].double().cpu().numpy()
+        ref = oracle.run(wl.lam, wl.w, wl.C_abs, Jh, nh, wl.T_min, wl.T_max)
+        T = out["T"][idx].cpu().numpy()
+        L = out["L"][idx].cpu().numpy()[:, :wl.K]
+        te = t_err(T, ref["T"], ref["flags"])
+        worst["T_max"] = max(worst["T_max"], float(te.max()) if te.size else 0.0)
+        worst["L_max"] = max(worst["L_max"], float(l_err(L, ref["L"]).max()))
+        worst["flags_equal"] = worst["flags_equal"] and bool((out["flags"][idx].cpu().numpy() == ref["flags"]).all())
+        worst["requests"] += 1
+        worst["cells"] += len(cells)
+    worst["sample"] = f"{ncells} cells of the first request of each (K, G) grid, BF16x3 server outputs"
+    return worst
+
+
+def torch_index(cells, device):
+    import torch
+
+    return torch.from_numpy(cells).to(device)
 
 
 # ------------------------------------------------------------------ reference arm

@@ -236,11 +236,15 @@ int dust_ctx_profile_read(dust_ctx *ctx, double *ms_absorb, double *ms_solve, do
  * requests in FIFO order (later ones may pass one that does not fit yet)
  * while the summed device footprint of admitted requests (J, n, T, L, resid,
  * flags and the scratch the solve needs) stays within `hbm_budget_bytes` and
- * at most `max_inflight` are active; it then runs them in rounds, each round
- * a fair-share chunk of every active request through one launch per kernel,
- * with two rounds in flight.  Requests arriving while the GPU is busy join
- * the next round.  A request's results are bitwise those of dust_solve on
- * the same context with the context's precision at submit time.  The paper
+ * at most `max_inflight` are active; it then runs them in rounds of work
+ * sized by priority, with two rounds in flight: active requests are
+ * ranked by remaining Planck terms discounted by their wait (shortest first,
+ * large ones not starved); small ones go whole into batched rounds (one
+ * launch per kernel for up to 32 of them), large ones run alone a chunk at a
+ * time through dust_solve's path.  Requests arriving while the GPU is busy
+ * join a round as soon as one retires.  A request's results are bitwise
+ * those of dust_solve on the same context with the context's precision at
+ * submit time.  The paper
  * processes one grid per call (Section 5); serving has no counterpart there.
  *
  * dust_server_create: the server allocates `hbm_budget_bytes` (>= 1 MiB) of
@@ -278,6 +282,14 @@ int dust_serve_poll(dust_server *srv, uint64_t ticket, int *state, double *laten
 int dust_serve_wait(dust_server *srv, uint64_t ticket, double timeout_ms, double *latency_ms);
 int dust_serve_cancel(dust_server *srv, uint64_t ticket);
 int dust_server_stats(dust_server *srv, dust_serve_stats *out);
+/* The round policy (defaults 1e9, 5e9, 1e10, 20): requests with at most
+ * small_terms Planck terms (cells x K x G) left go whole into batched rounds
+ * of up to batch_terms; larger ones run alone in chunks of about chunk_terms
+ * (at least 4096 cells); the ranking divides remaining terms by
+ * 1 + wait / age_ms.  Applies from the next round.  DUST_EINVAL for a NULL
+ * server or values that are not finite, small_terms < 0, or the others <= 0. */
+int dust_server_set_policy(dust_server *srv, double small_terms, double batch_terms, double chunk_terms,
+                           double age_ms);
 int dust_server_reset_stats(dust_server *srv);
 void dust_server_destroy(dust_server *srv);
 

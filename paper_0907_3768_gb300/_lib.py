@@ -59,6 +59,7 @@ _SIGS = {
     "dust_serve_wait": (_i, [_p, ctypes.c_uint64, _d, _p]),
     "dust_serve_cancel": (_i, [_p, ctypes.c_uint64]),
     "dust_server_stats": (_i, [_p, _p]),
+    "dust_server_set_policy": (_i, [_p, _d, _d, _d, _d]),
     "dust_server_reset_stats": (_i, [_p]),
     "dust_server_destroy": (None, [_p]),
     "dust_last_error": (ctypes.c_char_p, []),
@@ -228,6 +229,11 @@ def dust_server_stats(srv):
     s = ServeStats()
     check(lib().dust_server_stats(srv, ctypes.byref(s)))
     return s.as_dict()
+
+
+def dust_server_set_policy(srv, small_terms, batch_terms, chunk_terms, age_ms):
+    return check(lib().dust_server_set_policy(srv, float(small_terms), float(batch_terms), float(chunk_terms),
+                                              float(age_ms)))
 
 
 def dust_server_reset_stats(srv):

@@ -292,6 +292,10 @@ class Server:
     def stats(self):
         return _lib.dust_server_stats(self.handle)
 
+    def set_policy(self, small_terms=1e9, batch_terms=5e9, chunk_terms=1e10, age_ms=20.0):
+        """Round sizes and the aging of the shortest-work-first ranking (see include/dust.h)."""
+        _lib.dust_server_set_policy(self.handle, small_terms, batch_terms, chunk_terms, age_ms)
+
     def reset_stats(self):
         _lib.dust_server_reset_stats(self.handle)
 

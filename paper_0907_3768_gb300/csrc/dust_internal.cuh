@@ -336,6 +336,13 @@ int launch_solve_emit_fused(const EmitReq &req, int TC, size_t smem, int num_sms
 // Grow the context's scratch to hold `cells` cells (synchronises `st` first).
 int ensure_scratch(dust_ctx *ctx, int64_t cells, cudaStream_t st);
 
+// The whole path on device buffers over an explicit scratch view (a
+// request's, or a slice of one: order, classes and counts may be NULL, and
+// the cells are then emitted in ascending order); nlaunch counts the kernels,
+// ev (optional, four events) marks absorption / solve / emission boundaries.
+int solve_view(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, const float *n, float *T,
+               float *L, double *resid, uint8_t *flags, const ScratchView &sv, cudaStream_t st, bool mass,
+               int *nlaunch, cudaEvent_t *ev = nullptr);
 // The whole path on device buffers with scratch of scratch_bytes(ctx, C, true)
 // bytes at `scratch`.
 int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld,

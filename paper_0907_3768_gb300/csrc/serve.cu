@@ -5,18 +5,24 @@
 // order (a later request may pass one that does not fit yet) while the sum of
 // the device footprints of admitted requests stays within the HBM budget and
 // at most `max_inflight` are active; each admitted request gets its scratch
-// (absorbed powers) from a first-fit arena carved out of one allocation.
-// Work proceeds in rounds: a round takes a chunk of cells from every active
-// request (a fair share of a fixed amount of work, at least one tile) and
-// runs all chunks through the batched kernels in one launch per kernel
-// (absorption GEMM per precision, then solve + emission).  Two rounds are kept
-// in flight, so requests that arrive while the GPU is busy join the next
-// round and their work overlaps with the tail of earlier requests.  A cell's
-// arithmetic does not depend on its chunk or its batch, so a request's
-// results are bitwise those of dust_solve on the same context.
+// from a first-fit arena carved out of one allocation.  Work proceeds in
+// rounds, two in flight, so requests that arrive while the GPU is busy join a
+// round as soon as one retires and their work overlaps with the tail of
+// earlier ones.  Rounds are sized by work, shortest remaining first: active
+// requests are ranked by their remaining Planck terms discounted by how long
+// they have waited (so that large requests are not starved).  A small first
+// request (little work left) makes a batched round: it and the next small
+// requests, whole, up to a work budget and 32 parts, through one launch per
+// kernel (absorption GEMM per precision and orientation, the cell ordering,
+// the batched solve, the emission in work units, the residual).  A large one
+// runs alone, a chunk of cells per round, through dust_solve's own path (the
+// fused solve + emission where it applies).  A cell's arithmetic does not
+// depend on its chunk, its batch or its place in the emission order, so a
+// request's results are bitwise those of dust_solve on the same context.
 #include "dust_internal.cuh"
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -97,8 +103,12 @@ struct Part {
 
 struct Round {
     cudaEvent_t ev = nullptr;
+    int slot = 0;  // its part of the server's class-count workspace
     std::vector<Part> parts;
 };
+
+// Rounds in flight at once, each with its own class counts for the parts' cell order.
+constexpr int NSLOT = 2;
 
 }  // namespace
 
@@ -121,8 +131,13 @@ struct dust_server {
     std::thread th;
     bool stop = false;
     uint64_t next_ticket = 1;
-    size_t rr = 0;                  // round-robin start
-    double round_terms = 5.0e9;     // Planck terms per round (~1 ms of emission)
+    unsigned *hist_ws = nullptr;    // [NSLOT][MAXREQ][2 NBK] class counts of the rounds' parts
+    bool slot_busy[NSLOT] = {};
+    // scheduling: shortest remaining work first, the remaining work of a request
+    // discounted by 1 + wait / age_ms so that large requests are not starved;
+    // requests of at most small_terms Planck terms go whole into batched rounds of
+    // up to batch_terms, larger ones run alone in chunks of about chunk_terms
+    double small_terms = 1.0e9, batch_terms = 5.0e9, chunk_terms = 1.0e10, age_ms = 20.0;
     // statistics
     std::vector<double> lat_ms;
     int64_t submitted = 0, completed = 0, cancelled = 0, failed = 0, cells_done = 0, rounds = 0, launches = 0;
@@ -188,35 +203,53 @@ void admit(dust_server *s) {
     }
 }
 
-// Build one round: a fair share of round_terms for each active request.
+// Build one round.  Active requests are ranked by remaining Planck terms
+// discounted by their wait, (C - next) K G / (1 + wait / age_ms), smallest
+// first.  If the first is small (at most small_terms left), the round takes
+// it and the next small ones whole, up to batch_terms and MAXREQ parts, for
+// the batched kernels; otherwise it takes a chunk of about chunk_terms of the
+// first alone (a multiple of 128 cells, at least 4096), for dust_solve's path.
 std::vector<Part> build_round(dust_server *s) {
     std::vector<Part> parts;
-    std::vector<ServeReq *> cand;
+    std::vector<std::pair<double, ServeReq *>> cand;
+    const double t = now_ms();
+    auto terms = [](const ServeReq *r) { return (double)(r->C - r->next) * r->ctx->K * r->ctx->G; };
     for (ServeReq *r : s->active)
-        if (r->state == RS_ACTIVE && r->next < r->C) cand.push_back(r);
+        if (r->state == RS_ACTIVE && r->next < r->C)
+            cand.push_back({terms(r) / (1.0 + (t - r->t_submit) / s->age_ms), r});
     if (cand.empty()) return parts;
-    const size_t n = cand.size();
-    const double share = s->round_terms / (double)std::min<size_t>(n, MAXREQ);
-    for (size_t i = 0; i < n && parts.size() < (size_t)MAXREQ; ++i) {
-        ServeReq *r = cand[(s->rr + i) % n];
-        const double per_cell = (double)r->ctx->K * r->ctx->G;
-        int64_t cn = (int64_t)(share / per_cell);
-        cn = std::max<int64_t>(cn, 4096);
-        cn = (cn + 127) / 128 * 128;
-        cn = std::min<int64_t>(cn, r->C - r->next);
-        parts.push_back({r, r->next, cn});
-        r->next += cn;
-        r->inflight_parts++;
+    std::stable_sort(cand.begin(), cand.end(),
+                     [](const std::pair<double, ServeReq *> &a, const std::pair<double, ServeReq *> &b) { return a.first < b.first; });
+    ServeReq *top = cand[0].second;
+    if (terms(top) <= s->small_terms) {
+        double sum = 0.0;
+        for (const auto &c : cand) {
+            ServeReq *r = c.second;
+            const double w = terms(r);
+            if (w > s->small_terms || (!parts.empty() && sum + w > s->batch_terms)) continue;
+            parts.push_back({r, r->next, r->C - r->next});
+            r->next = r->C;
+            r->inflight_parts++;
+            sum += w;
+            if (parts.size() == (size_t)MAXREQ) break;
+        }
+        return parts;
     }
-    s->rr = (s->rr + 1) % std::max<size_t>(n, 1);
+    const double per_cell = (double)top->ctx->K * top->ctx->G;
+    int64_t cn = (int64_t)(s->chunk_terms / per_cell);
+    cn = std::max<int64_t>(cn, 4096);
+    cn = (cn + 127) / 128 * 128;
+    cn = std::min<int64_t>(cn, top->C - top->next);
+    parts.push_back({top, top->next, cn});
+    top->next += cn;
+    top->inflight_parts++;
     return parts;
 }
 
 // Scratch of one part: rows c0.. of its request's S, (1/T, n) pairs, cell
-// records, residual partials and grain-pass sums.  Parts are emitted in
-// ascending cell order (no class ordering), so order, classes and counts stay
-// unset.
-ScratchView part_view(const Part &p) {
+// records, residual partials, grain-pass sums, emission order and classes,
+// and the round slot's class counts for part index k.
+ScratchView part_view(const dust_server *s, const Part &p, int slot, int k) {
     const ScratchView v = scratch_view(p.r->ctx, p.r->C, p.r->S);
     const DevTables &tb = p.r->ctx->tb;
     ScratchView w{};
@@ -225,10 +258,14 @@ ScratchView part_view(const Part &p) {
     w.cell = v.cell + p.c0;
     w.part = v.part + p.c0 * tb.NKG;
     w.accp = v.accp ? v.accp + p.c0 * tb.NKG * 4 : nullptr;
+    w.order = v.order + p.c0;
+    w.bkt = v.bkt + p.c0;
+    w.hist = s->hist_ws + ((size_t)slot * MAXREQ + k) * 2 * NBK;
     return w;
 }
 
-int launch_round(dust_server *s, const std::vector<Part> &parts) {
+int launch_round(dust_server *s, const Round &rd) {
+    const std::vector<Part> &parts = rd.parts;
     // a request's first round waits (on the device) for the work its
     // producer had queued before submitting
     for (const Part &p : parts) {
@@ -239,15 +276,28 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
             r->ready_waited = true;
         }
     }
+    if (parts.size() == 1) {
+        // one chunk of one request: dust_solve's own path over its cells
+        const Part &p = parts[0];
+        ServeReq *r = p.r;
+        const int G = r->ctx->G;
+        int nl = 0;
+        const int rc = solve_view(r->ctx, r->precision, p.cn, r->J + p.c0 * r->ld, r->ld, r->n + p.c0 * G,
+                                  r->T + p.c0 * G, r->L ? r->L + p.c0 * r->ld : nullptr, r->resid ? r->resid + p.c0 : nullptr,
+                                  r->flags ? r->flags + p.c0 * G : nullptr, part_view(s, p, rd.slot, 0), s->st, false, &nl);
+        s->launches += (uint64_t)nl;
+        return rc;
+    }
     // absorption GEMMs, one launch per precision
     for (int prec = DUST_PREC_FP32; prec <= DUST_PREC_FP16X3; ++prec) {
         if (prec == DUST_PREC_FP32) {
             SimtBatch B;
             B.nreq = 0;
-            for (const Part &p : parts) {
+            for (size_t k = 0; k < parts.size(); ++k) {
+                const Part &p = parts[k];
                 if (p.r->precision != prec) continue;
                 ServeReq *r = p.r;
-                make_simt_req(r->ctx, p.cn, r->J + p.c0 * r->ld, r->ld, part_view(p).S, B.req[B.nreq++]);
+                make_simt_req(r->ctx, p.cn, r->J + p.c0 * r->ld, r->ld, part_view(s, p, rd.slot, (int)k).S, B.req[B.nreq++]);
             }
             if (B.nreq) {
                 int rc = launch_simt_batch(B, s->st);
@@ -262,11 +312,12 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
                 B.nreq = 0;
                 B.status = nullptr;
                 B.orient = orient;
-                for (const Part &p : parts) {
+                for (size_t k = 0; k < parts.size(); ++k) {
+                    const Part &p = parts[k];
                     if (p.r->precision != prec || tc_orient(p.r->ctx) != orient) continue;
                     ServeReq *r = p.r;
                     if (!B.status) B.status = r->ctx->tb.status;
-                    int rc = make_tc_req(r->ctx, prec, p.cn, r->J + p.c0 * r->ld, r->ld, part_view(p).S,
+                    int rc = make_tc_req(r->ctx, prec, p.cn, r->J + p.c0 * r->ld, r->ld, part_view(s, p, rd.slot, (int)k).S,
                                          B.req[B.nreq], B.tm[B.nreq], orient);
                     if (rc != DUST_OK) return rc;
                     B.nreq++;
@@ -281,19 +332,38 @@ int launch_round(dust_server *s, const std::vector<Part> &parts) {
             }
         }
     }
-    // solve + emission over every chunk of the round
+    // emission order of every part that emits (classes of the reference grain's absorbed power)
     EmitBatch E;
     E.nreq = 0;
-    for (const Part &p : parts) {
+    OrderBatch ob;
+    ob.nreq = 0;
+    for (size_t k = 0; k < parts.size(); ++k) {
+        const Part &p = parts[k];
         ServeReq *r = p.r;
         dust_ctx *ctx = r->ctx;
         const int G = ctx->G;
+        const ScratchView v = part_view(s, p, rd.slot, (int)k);
         const EmitPlan pl = plan_emit(ctx, r->L || r->resid, false);
-        fill_emit_req(ctx, pl, p.cn, part_view(p), r->n + p.c0 * G, r->T + p.c0 * G,
-                      r->L ? r->L + p.c0 * r->ld : nullptr, r->ld, r->resid ? r->resid + p.c0 : nullptr,
-                      r->flags ? r->flags + p.c0 * G : nullptr, E.req[E.nreq++], false);
+        EmitReq &e = E.req[E.nreq++];
+        fill_emit_req(ctx, pl, p.cn, v, r->n + p.c0 * G, r->T + p.c0 * G, r->L ? r->L + p.c0 * r->ld : nullptr, r->ld,
+                      r->resid ? r->resid + p.c0 : nullptr, r->flags ? r->flags + p.c0 * G : nullptr, e, false);
+        if (r->L || r->resid) {
+            OrderReq &o = ob.req[ob.nreq++];
+            o.key = v.S + order_ref_grain(G);
+            o.kstride = ctx->tb.Gs;
+            o.C = p.cn;
+            o.bkt = v.bkt;
+            o.hist = v.hist;
+            o.order = v.order;
+            e.order = v.order;
+        }
     }
     int nl = 0;
+    if (ob.nreq) {
+        int rc = launch_order(ob, s->st, &nl);
+        if (rc != DUST_OK) return rc;
+        s->launches += (uint64_t)nl;
+    }
     int rc = launch_emit_batch(E, s->num_sms, s->st, nullptr, false, &nl);
     if (rc != DUST_OK) return rc;
     s->launches += (uint64_t)nl;
@@ -317,6 +387,7 @@ void retire_round(dust_server *s, Round &rd, int status) {
         }
     }
     s->ev_pool.push_back(rd.ev);
+    s->slot_busy[rd.slot] = false;
     s->cv_done.notify_all();
 }
 
@@ -331,14 +402,16 @@ void scheduler(dust_server *s) {
             retire_round(s, rd, e == cudaSuccess ? DUST_OK : DUST_ECUDA);
         }
         admit(s);
-        if (s->inflight.size() < 2) {
+        if (s->inflight.size() < (size_t)NSLOT) {
             std::vector<Part> parts = build_round(s);
             if (!parts.empty()) {
                 Round rd;
                 if (!s->ev_pool.empty()) { rd.ev = s->ev_pool.back(); s->ev_pool.pop_back(); }
                 else cudaEventCreateWithFlags(&rd.ev, cudaEventDisableTiming);
                 rd.parts = std::move(parts);
-                int rc = launch_round(s, rd.parts);
+                while (s->slot_busy[rd.slot]) ++rd.slot;  // a free slot exists: fewer than NSLOT in flight
+                s->slot_busy[rd.slot] = true;
+                int rc = launch_round(s, rd);
                 if (rc == DUST_OK && cudaEventRecord(rd.ev, s->st) == cudaSuccess) {
                     s->rounds++;
                     s->inflight.push_back(std::move(rd));
@@ -396,9 +469,11 @@ int dust_server_create(dust_server **out, size_t hbm_budget_bytes, int max_infli
     cudaError_t e = cudaGetDeviceProperties(&prop, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->arena_mem, hbm_budget_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&s->hist_ws, sizeof(unsigned) * NSLOT * MAXREQ * 2 * NBK);
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
         if (s->st) cudaStreamDestroy(s->st);
+        if (s->arena_mem) cudaFree(s->arena_mem);
         delete s;
         return set_error(e == cudaErrorMemoryAllocation ? DUST_ENOMEM : DUST_ECUDA, "server setup failed: %s",
                          cudaGetErrorString(e));
@@ -589,6 +664,19 @@ int dust_server_stats(dust_server *s, dust_serve_stats *out) {
     return DUST_OK;
 }
 
+int dust_server_set_policy(dust_server *s, double small_terms, double batch_terms, double chunk_terms, double age_ms) {
+    if (!s) return set_error(DUST_EINVAL, "server is NULL");
+    if (!(small_terms >= 0.0) || !(batch_terms > 0.0) || !(chunk_terms > 0.0) || !(age_ms > 0.0) ||
+        !std::isfinite(small_terms) || !std::isfinite(batch_terms) || !std::isfinite(chunk_terms) || !std::isfinite(age_ms))
+        return set_error(DUST_EINVAL, "policy values must be finite, small_terms >= 0 and the others > 0");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->small_terms = small_terms;
+    s->batch_terms = batch_terms;
+    s->chunk_terms = chunk_terms;
+    s->age_ms = age_ms;
+    return DUST_OK;
+}
+
 int dust_server_reset_stats(dust_server *s) {
     if (!s) return set_error(DUST_EINVAL, "server is NULL");
     std::lock_guard<std::mutex> lk(s->mu);
@@ -620,6 +708,7 @@ void dust_server_destroy(dust_server *s) {
         if (kv.second->ready) cudaEventDestroy(kv.second->ready);
     cudaStreamDestroy(s->st);
     cudaFree(s->arena_mem);
+    cudaFree(s->hist_ws);
     cudaSetDevice(prev);
     for (auto &kv : s->by_ticket) delete kv.second;
     delete s;

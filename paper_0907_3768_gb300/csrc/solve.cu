@@ -88,15 +88,13 @@ cudaEvent_t prof_event(dust_ctx *ctx) {
 }
 }  // namespace
 
-int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, const float *n,
-                 float *T, float *L, double *resid, uint8_t *flags, void *scratch, cudaStream_t st, bool mass) {
+int solve_view(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, const float *n, float *T,
+               float *L, double *resid, uint8_t *flags, const ScratchView &sv, cudaStream_t st, bool mass,
+               int *nlaunch, cudaEvent_t *ev) {
+    int nl_total = 0;
+    if (nlaunch) *nlaunch = 0;
     if (C == 0) return DUST_OK;
-    const ScratchView sv = scratch_view(ctx, C, scratch);
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    if (ctx->prof_on)
-        for (int i = 0; i < 4; ++i) ev[i] = prof_event(ctx);
-    const bool prof = ev[0] && ev[1] && ev[2] && ev[3];
-    if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[0], st));
+    if (ev && ev[0]) DUST_CUDA_TRY(cudaEventRecord(ev[0], st));
     const EmitPlan p = plan_emit(ctx, L || resid, mass);
     EmitBatch B;
     B.nreq = 1;
@@ -119,10 +117,10 @@ int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_
         rc = precision == DUST_PREC_FP32 ? launch_gemm_simt(ctx, C, J, ld, sv.S, st)
                                          : launch_gemm_tc(ctx, precision, C, J, ld, sv.S, st);
     }
-    if (rc == DUST_OK) ctx->launches += 1;
+    if (rc == DUST_OK) nl_total += 1;
     int ftc = 0;
     const size_t fsmem = !fused && ctx->fused_emit ? plan_solve_emit(ctx, L || resid, mass, &ftc) : 0;
-    if (rc == DUST_OK && (L || resid)) {
+    if (rc == DUST_OK && (L || resid) && sv.order && sv.bkt && sv.hist) {
         // emission order: cells classed by the absorbed power of the reference
         // grain (S), or by its inverse temperature where S stayed in tensor memory
         const int gref = order_ref_grain(ctx->G);
@@ -143,22 +141,37 @@ int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_
         o.order = sv.order;
         int nl = 0;
         rc = launch_order(ob, st, &nl);
-        ctx->launches += (uint64_t)nl;
+        nl_total += nl;
         B.req[0].order = sv.order;
     }
     if (rc == DUST_OK) {
-        if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[1], st));
+        if (ev && ev[1]) DUST_CUDA_TRY(cudaEventRecord(ev[1], st));
         int nl = 0;
         if (fsmem) {
             // the solve runs inside the emission kernel: its time is reported with the emission's
-            if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[2], st));
+            if (ev && ev[2]) DUST_CUDA_TRY(cudaEventRecord(ev[2], st));
             rc = launch_solve_emit_fused(B.req[0], ftc, fsmem, ctx->num_sms, st, &nl);
         } else {
-            rc = launch_emit_batch(B, ctx->num_sms, st, prof ? ev[2] : nullptr, fused, &nl);
+            rc = launch_emit_batch(B, ctx->num_sms, st, ev ? ev[2] : nullptr, fused, &nl);
         }
-        ctx->launches += (uint64_t)nl;
-        if (prof) DUST_CUDA_TRY(cudaEventRecord(ev[3], st));
+        nl_total += nl;
+        if (ev && ev[3]) DUST_CUDA_TRY(cudaEventRecord(ev[3], st));
     }
+    if (nlaunch) *nlaunch = nl_total;
+    return rc;
+}
+
+int solve_device(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t ld, const float *n,
+                 float *T, float *L, double *resid, uint8_t *flags, void *scratch, cudaStream_t st, bool mass) {
+    if (C == 0) return DUST_OK;
+    const ScratchView sv = scratch_view(ctx, C, scratch);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (ctx->prof_on)
+        for (int i = 0; i < 4; ++i) ev[i] = prof_event(ctx);
+    const bool prof = ev[0] && ev[1] && ev[2] && ev[3];
+    int nl = 0;
+    const int rc = solve_view(ctx, precision, C, J, ld, n, T, L, resid, flags, sv, st, mass, &nl, prof ? ev : nullptr);
+    ctx->launches += (uint64_t)nl;
     for (int i = 0; i < 4; ++i) {
         if (!ev[i]) continue;
         if (prof && rc == DUST_OK) ctx->prof_marks.push_back(ev[i]);

@@ -163,3 +163,95 @@ def test_submit_waits_for_the_producer_stream():
         torch.cuda.synchronize()
         for k in ("T", "L", "resid", "flags"):
             assert torch.equal(out[k], ref[k]), k
+
+
+TOL = {"fp32": (1e-5, 1e-4), "bf16x3": (1e-3, 5e-3), "fp16x3": (1e-3, 5e-3)}
+
+
+def _grid_mix():
+    """Every request shape of the serving stream: K in {100, 200, 350, 500} x G in
+    {48, 96, 240} (K = 500 with the large grid and its 10 % near-opaque cells), the
+    three precisions in turn, seeded cell counts."""
+    from paper_0907_3768_gb300 import Context
+
+    rng = np.random.default_rng(23)
+    precs = ("bf16x3", "fp32", "fp16x3")
+    out = []
+    for i, (K, G) in enumerate([(K, G) for K in (100, 200, 350, 500) for G in (48, 96, 240)]):
+        C = int(np.exp(rng.uniform(np.log(500), np.log(30000))))
+        wl = _request_data(K, G, C, snapshot=7 + i)
+        ctx = Context.from_workload(wl, precision=precs[i % 3])
+        out.append((wl, ctx, precs[i % 3]))
+    return out
+
+
+def _check_against_oracle(wl, prec, out, ncells=64):
+    """T, L, the residual and the flags of sampled cells against the FP64 oracle."""
+    import oracle
+    from metrics import assert_flags_match, l_err, t_err
+
+    C = wl.J.shape[0]
+    cells = np.unique(np.linspace(0, C - 1, min(ncells, C)).astype(np.int64))
+    ref = oracle.run(wl.lam, wl.w, wl.C_abs, wl.J[cells], wl.n[cells], wl.T_min, wl.T_max)
+    T = out["T"].cpu().numpy()[cells]
+    L = out["L"].cpu().numpy()[cells, :wl.K]
+    tT, tL = TOL[prec]
+    assert t_err(T, ref["T"], ref["flags"]).max() <= tT, f"{prec} K={wl.K} G={wl.G}"
+    assert l_err(L, ref["L"]).max() <= tL, f"{prec} K={wl.K} G={wl.G}"
+    assert_flags_match(out["flags"].cpu().numpy()[cells], {"flags": ref["flags"], "A": ref["A"]}, wl)
+    ok = (ref["flags"] == 0).all(axis=1)
+    assert np.abs(out["resid"].cpu().numpy()[cells][ok]).max(initial=0.0) <= (2e-5 if prec == "fp32" else 2e-4)
+
+
+@pytest.mark.parametrize("policy", ["default", "small rounds"])
+def test_serving_matches_the_oracle(policy):
+    """Every request of the mix and of the full grid of serving shapes, served
+    together, against the FP64 oracle on sampled cells: T and L within the
+    precision's tolerance, flags as the oracle's, residuals small.  The small
+    policy forces multi-part batched rounds and requests chunked over several
+    rounds at these sizes."""
+    from paper_0907_3768_gb300 import Server
+
+    grid = _grid_mix()
+    _, mix = _mix()
+    with Server(hbm_budget_bytes=8 << 30, max_inflight=32) as srv:
+        if policy != "default":
+            srv.set_policy(small_terms=2e7, batch_terms=1e8, chunk_terms=3e8, age_ms=5.0)
+        inputs = [(_padded(wl.J), torch.from_numpy(wl.n).cuda()) for wl, _, _ in grid]  # alive until served
+        subs = [(wl, prec, ctx.submit(srv, J, n)) for (wl, ctx, prec), (J, n) in zip(grid, inputs)]
+        tix = [ctx.submit(srv, J, n) for ctx, J, n in mix]
+        for _, _, (t, _) in subs:
+            srv.wait(t, 120000.0)
+        for t, _ in tix:
+            srv.wait(t, 120000.0)
+        st = srv.stats()
+    assert st["failed"] == 0 and st["completed"] == len(subs) + len(tix)
+    for wl, prec, (_, out) in subs:
+        _check_against_oracle(wl, prec, out)
+    for _, ctx, _ in grid:
+        assert ctx.check() == 0
+        ctx.close()
+
+
+def test_served_mix_matches_the_oracle():
+    """The alone-vs-mix requests (four grids, three grain sets, both GEMM
+    orientations, three precisions) served together, against the oracle."""
+    from paper_0907_3768_gb300 import Server
+
+    rng = np.random.default_rng(11)
+    shapes = [(100, 48, "bf16x3"), (350, 96, "fp32"), (500, 240, "fp16x3"), (200, 96, "bf16x3"),
+              (100, 240, "bf16x3"), (200, 48, "fp16x3")]
+    ctxs, reqs = _mix()
+    wls = []
+    for i in range(10):  # the same draws as _mix
+        K, G, prec = shapes[i % len(shapes)]
+        C = int(np.exp(rng.uniform(np.log(300), np.log(40000))))
+        wls.append((_request_data(K, G, C, snapshot=i % 5), prec))
+    with Server(hbm_budget_bytes=8 << 30, max_inflight=6) as srv:
+        tickets = [ctx.submit(srv, J, n) for ctx, J, n in reqs]
+        for t, _ in tickets:
+            srv.wait(t, 60000.0)
+    for (wl, prec), (_, out) in zip(wls, tickets):
+        _check_against_oracle(wl, prec, out)
+    for c in ctxs.values():
+        c.close()
