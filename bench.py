@@ -40,8 +40,10 @@ KERNEL_SOURCES = {
     "k_fluct": ["fluct.cu", "solve_core.cuh", "dust_internal.cuh"],
 }
 RECORDED_TRAFFIC = {
-    # kernel: (bytes per launch, profile summary, sources sha256[:16])
-    "k_solve_emit": (None, "profiles/k_solve_emit_2e18cells_K200_G96.md", None),
+    # kernel: (bytes per launch on the bench's workload, profile summary, sources sha256[:16])
+    "k_solve_emit": (220.822784e6 + 352.343296e6, "profiles/k_solve_emit_2e18cells_K200_G96.md", "b731616fd0709c21"),
+    "k_emit": (220.439040e6 + 218.785024e6, "profiles/k_emit_2e18cells_K200_G96.md", "b731616fd0709c21"),
+    # captured at 2^14 cells only, where the L writes stay in L2: not proportional to the 2^18-cell launch
     "k_fluct": (None, "profiles/k_fluct_2e14cells_K200_G36_M128.md", None),
 }
 
@@ -99,6 +101,12 @@ def parse():
     ap.add_argument("--no-fused", action="store_true", help="skip the fused absorption + solve kernel")
     ap.add_argument("--no-fluct", action="store_true", help="skip the thermally fluctuating grains")
     ap.add_argument("--fluct-levels", type=int, default=128)
+    ap.add_argument("--profile-case", choices=["main", "main-two-kernel", "large", "fluct"], default=None,
+                    help="no measurement: run --steps solves of one case for a profiler to capture "
+                         "(main: 2^18 x 200 x 96 BF16x3, default kernels; main-two-kernel: the same with the solve "
+                         "and the emission as two kernels; large: --large-cells x 500 x 240; fluct: "
+                         "--profile-cells x 200 x 36 fluctuating grains on 128 levels)")
+    ap.add_argument("--profile-cells", type=int, default=1 << 14)
     ap.add_argument("--large-cells", type=int, default=1 << 20,
                     help="cells of the K=500, G=240 solve (the full case is 2^20; fewer for profiling captures)")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -421,6 +429,15 @@ def run_ours(args):
         torch.cuda.empty_cache()
     if not args.no_serving:
         line["serving"] = run_serving(args, dev, local)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the error against the FP64 oracle of every workload configuration the line covers
+        byc = {"0 tiny: 1024 cells x 64 wavelengths x 16 grains, all cells": tiny_errors(local, dev),
+               "1-2 main: 2^18 cells x 200 x 96, first cells (as cpu_baseline)": line.get("err_vs_oracle")}
+        if "large" in line:
+            byc["3 large: 2^20 cells x 500 x 240, 10% near-opaque"] = line["large"].get("err_vs_oracle")
+        if "serving" in line:
+            byc["4 serving: Poisson stream, BF16x3 server"] = line["serving"].get("err_vs_oracle")
+        line["err_by_config"] = byc
     if rank == 0:
         print(json.dumps(line), flush=True)
     for c in ctxs.values():
@@ -623,6 +640,38 @@ def _oracle_sample(seconds, cfg_id=CONFIG_ID, seed=None):
     return wl, ref, dt, oracle.max_threads()
 
 
+def tiny_errors(local, dev):
+    """The 1024-cell, 64-wavelength, 16-grain case in every precision against the oracle, in full."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    from paper_0907_3768_gb300 import Context, padded_rows
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from metrics import l_err, t_err
+
+    wl = synth.make_workload(0)
+    ref = oracle.run_workload(wl)
+    J = padded_rows(torch.from_numpy(wl.J).to(dev))
+    n = torch.from_numpy(wl.n).to(dev)
+    errs = {"cells": len(wl.cells)}
+    for prec in ("fp32", "bf16x3", "fp16x3"):
+        with Context.from_workload(wl, precision=prec, device=local) as ctx:
+            o = ctx.solve(J, n)
+            torch.cuda.synchronize()
+            assert ctx.check() == 0
+            T, L = o["T"].cpu().numpy(), o["L"].cpu().numpy()[:, :wl.K]
+            fl, rs = o["flags"].cpu().numpy(), o["resid"].cpu().numpy()
+        eT, eL = t_err(T, ref["T"], ref["flags"]), l_err(L, ref["L"])
+        ok = (ref["flags"] == 0).all(axis=1)
+        errs[prec] = {"T_max": float(eT.max()), "T_p99": float(np.percentile(eT, 99)), "L_max": float(eL.max()),
+                      "L_p99": float(np.percentile(eL, 99)), "resid_max": float(np.abs(rs[ok]).max(initial=0.0)),
+                      "flags_equal": bool((fl == ref["flags"]).all())}
+    return errs
+
+
 def cpu_baseline(args, wl_full, res):
     import numpy as np
 
@@ -674,6 +723,12 @@ def run_large(args, dev, local, ex2_rate):
     stream = torch.cuda.current_stream(dev)
     out = {"workload": f"{C} cells x 500 wavelengths (0.05-2000 um) x 240 grains, 10% near-opaque cells"}
     steps = max(3, min(args.steps, 10))
+    # error sample: every (C // 128)-th cell and the first 32 near-opaque cells
+    from synth.workloads import _cell_draws
+
+    opaque = np.nonzero(_cell_draws(synth.CONFIGS[3], full, synth.CONFIGS[3]["seed"])[2][:C])[0][:32]
+    sample = np.unique(np.concatenate([np.arange(0, C, max(1, C // 128)), opaque]))
+    kept = {}
     for prec in ("bf16x3", "fp32"):
         ctx = Context.from_workload(synth.make_workload(3, cells=[0]), precision=prec, device=local)
         r = {}
@@ -696,6 +751,9 @@ def run_large(args, dev, local, ex2_rate):
             r[mode] = {"ms_step": round(ms, 4), "ms_absorb": round(a / cnt, 4), "ms_solve": round(b / cnt, 4),
                        "ms_emit": round(c / cnt, 4),
                        "solves_per_s": C * G / (ms * 1e-3), "sed_cells_per_s": C / (ms * 1e-3) if wantL else None}
+            if wantL:
+                idx = torch.from_numpy(sample).to(dev)
+                kept[prec] = {k: o[k][idx].cpu().numpy() for k in ("T", "L", "flags", "resid")}
             del o
         assert ctx.check() == 0
         ctx.close()
@@ -711,6 +769,26 @@ def run_large(args, dev, local, ex2_rate):
                                 "tensor_TFLOPs_executed": round((3 if prec != "fp32" else 1) * 2 * C * G * K /
                                                                 (ms_a * 1e-3) / 1e12, 1)}
         out[prec] = r
+    # error against the oracle on the sample
+    import oracle
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from metrics import l_err, t_err
+
+    ws = synth.make_workload(3, cells=sample)
+    t0 = time.perf_counter()
+    ref = oracle.run_workload(ws)
+    dt = time.perf_counter() - t0
+    errs = {}
+    for prec, k in kept.items():
+        eT = t_err(k["T"], ref["T"], ref["flags"])
+        eL = l_err(k["L"][:, :K], ref["L"])
+        ok = (ref["flags"] == 0).all(axis=1)
+        errs[prec] = {"T_max": float(eT.max()), "T_p99": float(np.percentile(eT, 99)), "L_max": float(eL.max()),
+                      "L_p99": float(np.percentile(eL, 99)), "resid_max": float(np.abs(k["resid"][ok]).max(initial=0.0)),
+                      "flags_equal": bool((k["flags"] == ref["flags"]).all())}
+    out["err_vs_oracle"] = dict(errs, sample=f"{len(sample)} cells: every {max(1, C // 128)}-th and the first "
+                                              f"{len(opaque)} near-opaque ones; oracle {dt:.1f} s")
     return out
 
 
@@ -954,9 +1032,49 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """Run one case's solves with nothing else on the GPU, for a profiler's launch filter."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_0907_3768_gb300 import Context, padded_rows
+    from synth.workloads import heat_capacity_params
+
+    dev = torch.device("cuda", 0)
+    if args.profile_case in ("main", "main-two-kernel"):
+        wl = synth.make_workload(CONFIG_ID)
+    elif args.profile_case == "large":
+        wl = synth.make_workload(3, cells=np.arange(min(args.large_cells, synth.CONFIGS[3]["n_cells"])))
+    else:
+        wl = synth.make_workload(CONFIG_ID, cells=np.arange(args.profile_cells))
+    J = padded_rows(torch.from_numpy(wl.J).to(dev))
+    n = torch.from_numpy(wl.n).to(dev)
+    with Context.from_workload(wl, precision="bf16x3") as ctx:
+        if args.profile_case == "fluct":
+            g = synth.fluctuating_selection(wl.a_of_g)
+            N, th = heat_capacity_params(synth.CONFIGS[CONFIG_ID]["species"], wl.sp_of_g, wl.a_of_g)
+            ctx.set_fluctuating(g, N[g], th[g], 128)
+            nf = n[:, torch.from_numpy(g).to(dev)].contiguous()
+            out = ctx.solve_fluct(J, nf, want_dE=False)
+            for _ in range(args.steps):
+                ctx.solve_fluct(J, nf, want_dE=False, out=out)
+        else:
+            ctx.set_fused_emit(args.profile_case != "main-two-kernel")
+            out = ctx.solve(J, n)
+            for _ in range(args.steps):
+                ctx.solve(J, n, out=out)
+        torch.cuda.synchronize()
+        assert ctx.check() == 0
+    print(json.dumps({"profile_case": args.profile_case, "cells": len(wl.cells), "K": wl.K, "G": wl.G,
+                      "solves": args.steps + 1}))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_case:
+        profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -98,19 +98,22 @@ __device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[
             f4[i] = __ldg(tb.fw + (size_t)g[i] * (tb.NT - 1) + j[i]);
             tn[i] = __ldg(tb.Tnode + j[i]);
         }
-        // two Newton steps on the Hermite cubic q(tau) = t(u_j + tau h2) - t_j = y - t_j
-        // from the inverse-table guess; a step leaving the bracket bisects instead
+        // Newton on the Hermite cubic q(tau) = t(u_j + tau h2) - t_j = y - t_j from
+        // the inverse-table guess.  The guess is a cubic Hermite interpolant of the
+        // exact inverse, so one step lands within FP32 rounding of the root; a step
+        // that leaves the bracket bisects instead, and only then is a second taken
         const float r = y[i] - f4[i].x, d = f4[i].z - f4[i].x, m0 = f4[i].y, m1 = f4[i].w;
         const float c2 = 3.f * d - 2.f * m0 - m1, c3 = m0 + m1 - 2.f * d;
         float lo = 0.f, hi = 1.f, t = tau[i];
-#pragma unroll
         for (int it = 0; it < 2; ++it) {
             const float q = t * (m0 + t * (c2 + t * c3)) - r;
             const float dq = m0 + t * (2.f * c2 + 3.f * t * c3);
             lo = q < 0.f ? t : lo;
             hi = q < 0.f ? hi : t;
             const float nt = t - q * rcp_approx(dq);
-            t = (nt >= lo && nt <= hi) ? nt : 0.5f * (lo + hi);
+            const bool inside = nt >= lo && nt <= hi;
+            t = inside ? nt : 0.5f * (lo + hi);
+            if (inside) break;
         }
         // T = T_j 2^(tau h2), 2^x by its Taylor series (|x| <= h2, error < 1e-12)
         const float x = t * tb.h2;
