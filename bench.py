@@ -43,8 +43,8 @@ RECORDED_TRAFFIC = {
     # kernel: (bytes per launch on the bench's workload, profile summary, sources sha256[:16])
     "k_solve_emit": (220.822784e6 + 352.343296e6, "profiles/k_solve_emit_2e18cells_K200_G96.md", "b731616fd0709c21"),
     "k_emit": (220.439040e6 + 218.785024e6, "profiles/k_emit_2e18cells_K200_G96.md", "b731616fd0709c21"),
-    # captured at 2^14 cells only, where the L writes stay in L2: not proportional to the 2^18-cell launch
-    "k_fluct": (None, "profiles/k_fluct_2e14cells_K200_G36_M128.md", None),
+    # the full-size launch, DRAM counters only (one ncu pass; the 2^14-cell --set full capture is in the same file)
+    "k_fluct": (258.2208e6 + 176.340992e6, "profiles/k_fluct_2e14cells_K200_G36_M128.md", "224fa4910248abc6"),
 }
 
 
