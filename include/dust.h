@@ -87,9 +87,12 @@ enum dust_flag {
  * The context copies every input (the caller may free them on return), keeps
  * all tables resident in device memory, and owns a scratch buffer for the
  * absorbed powers that dust_solve grows on demand.  The P_g(T) table, its
- * slope and an inverse table are built on the device in FP64 (replacing the
- * per-iteration quadrature of the paper's Newton kernel, Section 4.3, by the
- * table lookup its production code uses, Section 6).
+ * slope and an inverse table (the roots of the table at n_table uniform steps
+ * of log2 P, with the table's cubic on each interval between them) are built
+ * on the device in FP64, replacing the per-iteration quadrature of the
+ * paper's Newton kernel (Section 4.3) by the table lookup its production code
+ * uses (Section 6); a solve is one lookup and one Newton step.  Also fails
+ * with DUST_EINVAL when P_g(T) is not strictly increasing in FP64.
  * Also fails with DUST_EINVAL when h c / (lambda_max k_B T_max) < 1e-3 (the
  * emission kernel's rational accumulation needs 1 - exp(-x) >= 1e-3).
  * Synchronous; returns DUST_OK and *out, or an error and *out = NULL. */

@@ -5,12 +5,21 @@
 //   P_g(T)  = sum_k W[g,k] B_k(T),   W[g,k] = w_k C_abs[g,k]      (FP64)
 //   t_g(u)  = log2(P_g(2^u) / P_g(T_min)),  u = log2 T  on NT uniform nodes
 //   s_g(u)  = d log P / d log T = sum W B x / (1 - e^-x) / P
-// stored as FP32 Hermite intervals; the inverse u(t) on NI uniform nodes of t
-// seeds the device Newton iteration.  The paper solved Eq. 7 by Newton with a
-// quadrature per iteration (Section 4.3) and notes that production runs
-// interpolate a temperature table instead (Section 6); here the table is
-// built once per context in FP64 and every solve is a table lookup plus a
-// Newton step on its Hermite interpolant.
+// stored as FP32 Hermite intervals (the fluctuating-grain cooling rates read
+// them).  The solve reads the inverse: the roots u_m of t(u) = m dy on NI
+// uniform nodes of t (FP64 Newton on the forward interpolant), one record per
+// interval [u_m, u_m+1]: the forward cubic Hermite of t(u) on that interval,
+// in tau = (u - u_m) / du and in units of dy, has end values 0 and 1 and end
+// slopes a0 = t'(u_m) du / dy and a1 = t'(u_m+1) du / dy, and the record is
+// (2^u_m, du, a0 - 1, a1 - 1).  A cell's y = log2(A / P_g(T_min)) selects
+// its interval (m = floor(y / dy)) and Newton on that cubic gives tau, so one
+// table load gives both the bracket and the Newton model; over one interval
+// t(u) is nearly straight (a0, a1 within a few 1e-3 of 1 on the workloads),
+// so the step from tau = ty lands within FP32 rounding.  The paper solved
+// Eq. 7 by Newton with a quadrature per iteration (Section 4.3) and notes that
+// production runs interpolate a temperature table instead (Section 6); here
+// the table is built once per context in FP64 and every solve is one table
+// lookup and one Newton step on its interpolant.
 //
 // Scaled operands:
 //   W32[g,k]  = W[g,k] / P_g(T_min) * 2^-f_g  (max_k W32 in (1/2, 1]), so that
@@ -155,19 +164,22 @@ __global__ void k_inverse(int G, int NT, int NI, double log2Tmin, double h2, con
     idu[i] = h2 / dp;
 }
 
-__global__ void k_inv32(int G, int NI, double dy_unused, const double *iu, const double *idu,
-                        const GrainParam *gp, float4 *inv) {
+// Newton records of the inverse-table intervals (see the top of this file).
+// flag: 1 where an interval is wider than 1/8 in log2 T (coarse tables:
+// 2^(tau du) then takes ex2 instead of the short series), 2 where the
+// interval is empty or its slopes are not finite.
+__global__ void k_ivrec(int G, int NT, int NI, const double *lp, const double *iu, const double *idu,
+                        float4 *ivr, int *flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= G * (NI - 1)) return;
     int g = i / (NI - 1), m = i % (NI - 1);
     size_t b = (size_t)g * NI + m;
-    double dy = (double)gp[g].tmax / (NI - 1);
-    inv[i] = make_float4((float)iu[b], (float)(idu[b] * dy), (float)iu[b + 1], (float)(idu[b + 1] * dy));
-}
-
-__global__ void k_tnode(int NT, double log2Tmin, double h2, float *Tnode) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < NT) Tnode[j] = (float)exp2(log2Tmin + j * h2);
+    const double dy = (lp[(size_t)g * NT + NT - 1] - lp[(size_t)g * NT]) / (NI - 1);
+    const double du = iu[b + 1] - iu[b];
+    const double a0 = du / (idu[b] * dy), a1 = du / (idu[b + 1] * dy);
+    ivr[i] = make_float4((float)exp2(iu[b]), (float)du, (float)(a0 - 1.0), (float)(a1 - 1.0));
+    if (!(du > 0.0 && isfinite(a0) && isfinite(a1))) atomicMax(flag, 2);
+    else if (du > 0.125) atomicMax(flag, 1);
 }
 
 // W32 [Gs][Kw] (zero padded) and the 16-bit hi/lo operand images of the
@@ -284,8 +296,7 @@ int build_context(dust_ctx *ctx, const double *lambda, const double *w, const do
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     size_t o_fw = take(sizeof(float4) * (size_t)G * (NT - 1));
-    size_t o_inv = take(sizeof(float4) * (size_t)G * (NI - 1));
-    size_t o_Tn = take(sizeof(float) * NT);
+    size_t o_ivr = take(sizeof(float4) * (size_t)G * (NI - 1));
     size_t o_gp = take(sizeof(GrainParam) * G);
     size_t o_gs = take(sizeof(double) * G);
     size_t o_P0 = take(sizeof(double) * G);
@@ -306,8 +317,7 @@ int build_context(dust_ctx *ctx, const double *lambda, const double *w, const do
     tb.log2Tmin = (float)log2Tmin; tb.h2 = (float)h2;
     tb.Tmin = (float)ctx->Tmin; tb.Tmax = (float)ctx->Tmax;
     tb.fw = (const float4 *)(base + o_fw);
-    tb.inv = (const float4 *)(base + o_inv);
-    tb.Tnode = (const float *)(base + o_Tn);
+    tb.ivr = (const float4 *)(base + o_ivr);
     tb.gp = (const GrainParam *)(base + o_gp);
     tb.gscale = (const double *)(base + o_gs);
     tb.P0 = (const double *)(base + o_P0);
@@ -367,10 +377,13 @@ int build_context(dust_ctx *ctx, const double *lambda, const double *w, const do
                                                 (float4 *)(base + o_fw));
     k_inverse<<<blocks((size_t)G * NI), B>>>(G, NT, NI, log2Tmin, h2, (double *)t_lp.p,
                                              (double *)t_sl.p, (double *)t_iu.p, (double *)t_idu.p);
-    k_inv32<<<blocks((size_t)G * (NI - 1)), B>>>(G, NI, 0.0, (double *)t_iu.p, (double *)t_idu.p,
-                                                 (const GrainParam *)(base + o_gp),
-                                                 (float4 *)(base + o_inv));
-    k_tnode<<<blocks(NT), B>>>(NT, log2Tmin, h2, (float *)(base + o_Tn));
+    DUST_CUDA_TRY(cudaMemset(t_bad.p, 0, sizeof(int)));
+    k_ivrec<<<blocks((size_t)G * (NI - 1)), B>>>(G, NT, NI, (double *)t_lp.p, (double *)t_iu.p,
+                                                 (double *)t_idu.p, (float4 *)(base + o_ivr), (int *)t_bad.p);
+    DUST_CUDA_TRY(cudaGetLastError());
+    DUST_CUDA_TRY(cudaMemcpy(&bad, t_bad.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad == 2) return set_error(DUST_EINVAL, "P_g(T) is not strictly increasing over [T_min, T_max] in FP64");
+    tb.wide = bad == 1;
     k_w32<<<blocks((size_t)Gs * Kw), B>>>(K, G, Gs, Kw, W_d, (double *)(base + o_P0),
                                           (const GrainParam *)(base + o_gp), ctx->W32,
                                           ctx->Wimg[0], ctx->Wimg[1]);

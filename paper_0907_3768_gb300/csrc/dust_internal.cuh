@@ -45,8 +45,9 @@ struct DevTables {
     float log2Tmin, h2;       // u_j = log2Tmin + j h2 (u = log2 T)
     float Tmin, Tmax;
     const float4 *fw;         // [G][NT-1] (t_j, s_j h2, t_j+1, s_j+1 h2), t = log2(P/P0)
-    const float4 *inv;        // [G][NI-1] (u_m, u'_m dy, u_m+1, u'_m+1 dy)
-    const float *Tnode;       // [NT] 2^u_j
+    const float4 *ivr;        // [G][NI-1] Newton records of the inverse-table intervals
+                              //     (2^u_m, du = u_m+1 - u_m, d0, d1), see context.cu
+    int wide;                 // some du > 1/8: 2^(tau du) by ex2 instead of its series
     const GrainParam *gp;     // [G]
     const double *gscale;     // [G] A = S * gscale (= P0 2^f)
     const double *P0;         // [G] P_g(T_min)

@@ -51,7 +51,7 @@ __device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[
                                             const float4 (&gq)[NB], float (&T)[NB], int (&fl)[NB]) {
     float y[NB], ty[NB];
     int m[NB];
-    float4 iv[NB];
+    float4 rv[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         // log2 s = e + log2 m with the exponent split off exactly and m in
@@ -69,45 +69,26 @@ __device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[
         ty[i] = fminf(fy - (float)m[i], 1.f);
     }
 #pragma unroll
-    for (int i = 0; i < NB; ++i) iv[i] = __ldg(tb.inv + (size_t)g[i] * (tb.NI - 1) + m[i]);
-    int j[NB];
-    float tau[NB], tn[NB];
-    float4 f4[NB];
-    const float inv_h2 = 1.f / tb.h2;
+    for (int i = 0; i < NB; ++i) rv[i] = __ldg(tb.ivr + (size_t)g[i] * (tb.NI - 1) + m[i]);
+    // 2^x = sum_n (x ln 2)^n / n!, five terms: |x| <= 1/8 leaves < 6e-10 (tables
+    // with a wider interval take ex2)
+    const float L1 = 0.69314718056f, L2 = 0.24022650695f, L3 = 0.05550410866f, L4 = 0.00961812911f,
+                L5 = 0.00133335581f;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const float ug = hermite(iv[i].x, iv[i].y, iv[i].z, iv[i].w, ty[i]);
-        const float fj = (ug - tb.log2Tmin) * inv_h2;
-        j[i] = min(max((int)floorf(fj), 0), tb.NT - 2);
-        tau[i] = fminf(fmaxf(fj - (float)j[i], 0.f), 1.f);
-    }
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-        f4[i] = __ldg(tb.fw + (size_t)g[i] * (tb.NT - 1) + j[i]);
-        tn[i] = __ldg(tb.Tnode + j[i]);
-    }
-    const float L1 = 0.69314718056f, L2 = 0.24022650695f, L3 = 0.05550410866f;  // (ln 2)^k / k!
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-        // bracketing interval t_j <= y <= t_j+1 (the guess is right unless y
-        // sits within rounding of a node)
-        for (int a = 0; a < 4; ++a) {
-            if (y[i] < f4[i].x && j[i] > 0) { --j[i]; tau[i] = 1.f; }
-            else if (y[i] > f4[i].z && j[i] < tb.NT - 2) { ++j[i]; tau[i] = 0.f; }
-            else break;
-            f4[i] = __ldg(tb.fw + (size_t)g[i] * (tb.NT - 1) + j[i]);
-            tn[i] = __ldg(tb.Tnode + j[i]);
-        }
-        // Newton on the Hermite cubic q(tau) = t(u_j + tau h2) - t_j = y - t_j from
-        // the inverse-table guess.  The guess is a cubic Hermite interpolant of the
-        // exact inverse, so one step lands within FP32 rounding of the root; a step
-        // that leaves the bracket bisects instead, and only then is a second taken
-        const float r = y[i] - f4[i].x, d = f4[i].z - f4[i].x, m0 = f4[i].y, m1 = f4[i].w;
-        const float c2 = 3.f * d - 2.f * m0 - m1, c3 = m0 + m1 - 2.f * d;
-        float lo = 0.f, hi = 1.f, t = tau[i];
+        // Newton on the interval's forward cubic, in units of the interval:
+        // p(tau) = tau + tau (d0 + tau (c2 + tau c3)) = ty, p(0) = 0, p(1) = 1,
+        // p'(0) = 1 + d0, p'(1) = 1 + d1, from tau = ty (the straight line
+        // through the ends).  The bracket [0, 1] holds the root; a step that
+        // leaves the current bracket bisects instead, and only then is a
+        // second taken.  The first residual, p(ty) - ty, is the small cubic
+        // term alone, so it carries no cancellation.
+        const float d0 = rv[i].z, d1 = rv[i].w;
+        const float c2 = -2.f * d0 - d1, c3 = d0 + d1;
+        float lo = 0.f, hi = 1.f, t = ty[i];
         for (int it = 0; it < 2; ++it) {
-            const float q = t * (m0 + t * (c2 + t * c3)) - r;
-            const float dq = m0 + t * (2.f * c2 + 3.f * t * c3);
+            const float q = (t - ty[i]) + t * (d0 + t * (c2 + t * c3));
+            const float dq = 1.f + d0 + t * (2.f * c2 + 3.f * t * c3);
             lo = q < 0.f ? t : lo;
             hi = q < 0.f ? hi : t;
             const float nt = t - q * rcp_approx(dq);
@@ -115,9 +96,10 @@ __device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[
             t = inside ? nt : 0.5f * (lo + hi);
             if (inside) break;
         }
-        // T = T_j 2^(tau h2), 2^x by its Taylor series (|x| <= h2, error < 1e-12)
-        const float x = t * tb.h2;
-        const float Tv = tn[i] * fmaf(x, fmaf(x, fmaf(x, L3, L2), L1), 1.f);
+        // T = 2^u_m 2^(tau du)
+        const float x = t * rv[i].y;
+        const float Tv = rv[i].x * (tb.wide ? ex2_approx(x)
+                                            : fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, L5, L4), L3), L2), L1), 1.f));
         T[i] = fl[i] == DUST_FLAG_OK ? Tv
              : fl[i] == DUST_FLAG_LOW ? tb.Tmin
              : fl[i] == DUST_FLAG_HIGH ? tb.Tmax : __int_as_float(0x7fc00000);

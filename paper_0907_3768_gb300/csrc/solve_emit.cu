@@ -8,10 +8,11 @@
 // dependent table lookups, so it wants parallelism, not shared memory):
 //   the exponent m_c of max_g n[c,g] (n enters the emission as n 2^-m_c) and,
 //   per grain, the root of Eq. 7 from the scaled absorbed power S
-//   (A / P_g(T_min) = S 2^f_g): a guess from the inverse table u(t), then
-//   Newton on the FP32 Hermite interpolant of
-//   t_g(u) = log2(P_g(2^u) / P_g(T_min)) inside the bracketing table interval
-//   (bisection when a step leaves it).  The paper's kernel 3 iterated Newton
+//   (A / P_g(T_min) = S 2^f_g): y = log2 S + f_g selects the interval of
+//   the inverse table that brackets the root, and one Newton step on that
+//   interval's cubic Hermite of t_g(u) = log2(P_g(2^u) / P_g(T_min)) gives
+//   u = log2 T (bisection when a step leaves the bracket); one table load
+//   per grain.  The paper's kernel 3 iterated Newton
 //   with a fresh quadrature per step (Section 4.3); the device table removes
 //   those exponentials.  Writes T, flags and, when the emission follows, the
 //   pairs (1/T, n 2^-m_c) and a per-cell record (m_c, absorbed power).
