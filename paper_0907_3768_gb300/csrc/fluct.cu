@@ -310,53 +310,60 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
         }
         __syncwarp(hmask);
         // 5. forward cut-flux recursion from P_0 = 1: step j adds P_j's flux
-        //    to every level above j, then reads P_{j+1} off its owner lane
+        //    to every level above j, then reads P_{j+1} off its owner lane.
+        //    Level 0 sits in lane 0's first register as acc = 1 with factor 1
+        //    (its flux terms are the zero pad), so that every level's P is
+        //    acc mul 2^ei in the current frame and a frame change rescales
+        //    them all at once; the distribution is read off the registers
+        //    at the end.
+        if (hl == 0) { acc[0] = 1.f; mul[0] = 1.f; mulx[0] = 1.f; ei[0] = 0; }
         float pj = 1.f;
-        if (hl == 0) LT[0].y = 1.f;
         const float *ph = phi + hl;
         // (registers below R0 hold levels at or below j: their updates add 0)
-#define FL_STEP(J, RS, R0)                                                                    \
+#define FL_STEP(J, RS, R0, OWN)                                                               \
     {                                                                                         \
         const int j_ = (J);                                                                   \
         _Pragma("unroll") for (int r = (R0); r < MR; ++r) acc[r] = fmaf(ph[LW * r - j_], pj, acc[r]); \
-        const int own = (j_ + 1) % LW;                                                        \
-        const float cand = acc[RS] * mulx[RS];                                                \
-        const float v = __shfl_sync(hmask, cand < 0x1p64f ? cand : -1.f, own, LW);            \
-        if (v >= 0.f) {                                                                       \
+        const float v = __shfl_sync(hmask, acc[RS] * mulx[RS], (OWN), LW);                     \
+        if (v < 0x1p64f) {                                                                    \
             pj = v;                                                                           \
         } else { /* exact path: rescale the frame, or an exponent out of float range */       \
-            const float raw = __shfl_sync(hmask, acc[RS] * mul[RS], own, LW);                 \
-            const int E = __shfl_sync(hmask, ei[RS], own, LW);                                \
+            const float raw = __shfl_sync(hmask, acc[RS] * mul[RS], (OWN), LW);               \
+            const int E = __shfl_sync(hmask, ei[RS], (OWN), LW);                              \
             const int ve = (raw > 0.f && raw < INFINITY) ? ilogbf(raw) : -1000;               \
             if (ve + E > 64) {                                                                \
                 const int sh = ve + E;                                                        \
-                __syncwarp(hmask);                                                            \
                 _Pragma("unroll") for (int r = 0; r < MR; ++r) acc[r] = ldexpf(acc[r], -sh);  \
-                for (int i = hl; i <= j_; i += LW) LT[i].y = ldexpf(LT[i].y, -sh);            \
                 pj = ldexpf(raw, -ve);                                                        \
             } else {                                                                          \
                 pj = ldexpf(raw, E);                                                          \
             }                                                                                 \
         }                                                                                     \
-        if (hl == own) LT[j_ + 1].y = pj;                                                     \
     }
 #pragma unroll
         for (int r0 = 0; r0 < MR; ++r0) {
             // levels LW r0 + 1 .. LW r0 + LW - 1 (this register of lanes 1..LW-1)
-            for (int jj = 0; jj < LW - 1; ++jj) FL_STEP(LW * r0 + jj, r0, r0)
+#pragma unroll 2
+            for (int jj = 0; jj < LW - 1; ++jj) FL_STEP(LW * r0 + jj, r0, r0, jj + 1)
             // level LW (r0 + 1) (the next register of lane 0)
-            if (r0 + 1 < MR) FL_STEP(LW * r0 + LW - 1, r0 + 1 < MR ? r0 + 1 : r0, r0 + 1)
+            if (r0 + 1 < MR) FL_STEP(LW * r0 + LW - 1, r0 + 1 < MR ? r0 + 1 : r0, r0 + 1, 0)
         }
 #undef FL_STEP
-        __syncwarp(hmask);
-        // normalisation
-        float z = 0.f;
-        for (int j = hl; j < M; j += LW) z += LT[j].y;
+        // the distribution in the final frame, normalised
+        float pv[MR], z = 0.f;
+#pragma unroll
+        for (int r = 0; r < MR; ++r) {
+            const float fast = acc[r] * mulx[r];
+            pv[r] = fast < 0x1p64f ? fast : ldexpf(acc[r] * mul[r], ei[r]);
+            z += pv[r];
+        }
 #pragma unroll
         for (int o = LW / 2; o; o >>= 1) z += __shfl_xor_sync(hmask, z, o);
         const float iz = 1.f / z;
-        for (int j = hl; j < M; j += LW) {
-            const float p = LT[j].y * iz;
+#pragma unroll
+        for (int r = 0; r < MR; ++r) {
+            const int j = hl + LW * r;
+            const float p = pv[r] * iz;
             LT[j].y = p;
             if (P) P[((size_t)c * fd.Gf + q) * M + j] = p;
         }
