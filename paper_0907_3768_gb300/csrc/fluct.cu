@@ -85,20 +85,20 @@ __host__ __device__ constexpr size_t fl_warp_floats(int K, int M) {
 // One level's term for two wavelengths, folded into the group's fraction
 // (sum of p t/(1-t) = N/D), kept as Nn = -N and D:
 //   Nn -= t (p D + Nn),  D -= t D,
-// five packed operations with -t formed once.  The first level of a group
-// starts from Nn = -p t, D = 1 - t.
+// four packed operations (the sign of t is an operand modifier).  The first
+// level of a group starts from Nn = -p t, D = 1 - t.
 __device__ __forceinline__ void fl_term(float2 nax, float iT, float p, float2 &Nn, float2 &D) {
     const float2 a = __fmul2_rn(nax, make_float2(iT, iT));
-    const float2 tn = __fmul2_rn(make_float2(ex2_approx(a.x), ex2_approx(a.y)), make_float2(-1.f, -1.f));
+    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
     const float2 e = __ffma2_rn(make_float2(p, p), D, Nn);
-    Nn = __ffma2_rn(tn, e, Nn);
-    D = __ffma2_rn(tn, D, D);
+    Nn = __ffma2_rn(make_float2(-t.x, -t.y), e, Nn);
+    D = __ffma2_rn(make_float2(-t.x, -t.y), D, D);
 }
 __device__ __forceinline__ void fl_first(float2 nax, float iT, float p, float2 &Nn, float2 &D) {
     const float2 a = __fmul2_rn(nax, make_float2(iT, iT));
-    const float2 tn = __fmul2_rn(make_float2(ex2_approx(a.x), ex2_approx(a.y)), make_float2(-1.f, -1.f));
-    Nn = __fmul2_rn(make_float2(p, p), tn);
-    D = __ffma2_rn(tn, make_float2(1.f, 1.f), make_float2(1.f, 1.f));
+    const float2 t = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+    Nn = __fmul2_rn(make_float2(-p, -p), t);
+    D = __ffma2_rn(make_float2(-t.x, -t.y), make_float2(1.f, 1.f), make_float2(1.f, 1.f));
 }
 
 // One CTA per cell; its problem slots take the fluctuating grains in turn.
@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
     const unsigned hmask = LW == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
     const int64_t c = blockIdx.x;
     if (c >= C) return;
+    const float inv_h2 = 1.f / tb.h2;
     const int Kp4 = (K + 3) & ~3;
     float *Jc = sm;
     float *base = sm + Kp4 + (size_t)slot * fl_warp_floats(K, M);
@@ -260,13 +261,15 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
         __syncwarp(hmask);
         // sigma: Phi 2^-sigma <= 1 (the total rate bounds every Phi(m))
         const int sigma = (carry_h > 0.f && carry_h < INFINITY) ? ilogbf(carry_h) + 1 : 0;
-        for (int m = hl; m < M; m += LW) {
-            int lo = 0, hi = K;  // x is non-increasing: count of x_k >= m
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (x[mid] >= (float)m) lo = mid + 1; else hi = mid;
-            }
-            kb[m] = lo;
+        // kb(m) = #{k : x_k >= m}.  x is non-increasing, so kb = k + 1 on
+        // floor(x_k+1) < m <= floor(x_k), kb = K on m <= floor(x_K-1) and 0
+        // above floor(x_0): every wavelength fills its own range of m
+        for (int m = hl; m < M; m += LW) kb[m] = 0;
+        __syncwarp(hmask);
+        for (int k = hl; k < K; k += LW) {
+            const int hi = (int)fminf(floorf(x[k]), (float)(M - 1));
+            const int lo = k + 1 < K ? (int)fminf(floorf(x[k + 1]), (float)M) + 1 : 0;
+            for (int m = lo; m <= hi; ++m) kb[m] = k + 1;
         }
         __syncwarp(hmask);
         for (int m = hl; m < M; m += LW) {
@@ -293,10 +296,14 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
                 LT[0].x = PAD_INV_T;  // level 0 (T = 0) emits nothing: every t is 0
                 continue;
             }
-            const float T = gr.theta / log1pf(gr.ctil / ((float)f * dEt));
-            LT[f].x = 1.f / T;
-            const float u = log2f(fminf(fmaxf(T, tb.Tmin), tb.Tmax));
-            const float fj = (u - tb.log2Tmin) / tb.h2;
+            const float T = gr.theta * rcp_approx(log1pf(gr.ctil / ((float)f * dEt)));
+            LT[f].x = rcp_approx(T);
+            // log2 of T clamped into the table: exponent split off exactly,
+            // lg2.approx of the mantissa in [1/2, 1)
+            const int tbits = __float_as_int(fminf(fmaxf(T, tb.Tmin), tb.Tmax));
+            const float u = (float)(((tbits >> 23) & 0xff) - 126) +
+                            lg2_approx(__int_as_float((tbits & 0x007fffff) | 0x3f000000));
+            const float fj = (u - tb.log2Tmin) * inv_h2;
             const int j0 = min(max((int)floorf(fj), 0), tb.NT - 2);
             const float tau = fminf(fmaxf(fj - (float)j0, 0.f), 1.f);
             const float4 f4 = __ldg(tb.fw + (size_t)g * (tb.NT - 1) + j0);
@@ -304,7 +311,7 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
             const float e = gr.fprime + (float)sigma - t;
             const float fe = floorf(e);
             ei[r] = (int)fe;
-            mul[r] = dEt * exp2f(e - fe);
+            mul[r] = dEt * ex2_approx(e - fe);  // e - fe in [0, 1)
             const float mx = ldexpf(mul[r], ei[r]);
             mulx[r] = (mx >= 1.17549435e-38f && mx < INFINITY) ? mx : __int_as_float(0x7fc00000);
         }
