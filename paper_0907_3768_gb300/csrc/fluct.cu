@@ -230,29 +230,35 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
         const float Etop = fminf(2.f * (Eeq + 1.f), gr.Etop);
         const float dEt = Etop / (float)(M - 1);
         const float idE = 1.f / dEt;
-        // 3. photon landings and prefix sums over wavelength
-        float carry_h = 0.f, carry_f = 0.f;
-        for (int k0 = 0; k0 < K; k0 += LW) {
-            const int k = k0 + hl;
-            float h = 0.f, hf = 0.f;
-            if (k < K) {
-                const float xk = __ldg(fd.epst + k) * idE;
-                x[k] = xk;
-                h = Jc[k] * __ldg(fd.Rhat + (size_t)q * K + k);
-                hf = h * (xk - floorf(xk));
-            }
-            float ih = h, ihf = hf;
+        const float cidE = gr.ctil * idE;  // level f: ctil / E_f = cidE / f
+        // 3. photon landings and prefix sums over wavelength: each lane
+        //    sums its own run of consecutive wavelengths (exclusive sums in
+        //    place), one scan of the run totals across the lanes, then each
+        //    run is offset
+        const int KL = (K + LW - 1) / LW;
+        const int kbeg = min(hl * KL, K), kend = min(kbeg + KL, K);
+        float th = 0.f, tf = 0.f;
+        for (int k = kbeg; k < kend; ++k) {
+            const float xk = __ldg(fd.epst + k) * idE;
+            x[k] = xk;
+            const float h = Jc[k] * __ldg(fd.Rhat + (size_t)q * K + k);
+            Sh[k] = th;
+            Sf[k] = tf;
+            th += h;
+            tf = fmaf(h, xk - floorf(xk), tf);
+        }
+        float oh = th, of = tf;
 #pragma unroll
-            for (int o = 1; o < LW; o <<= 1) {
-                const float a = __shfl_up_sync(hmask, ih, o, LW), b = __shfl_up_sync(hmask, ihf, o, LW);
-                if (hl >= o) { ih += a; ihf += b; }
-            }
-            if (k < K) {
-                Sh[k] = carry_h + (ih - h);
-                Sf[k] = carry_f + (ihf - hf);
-            }
-            carry_h += __shfl_sync(hmask, ih, LW - 1, LW);
-            carry_f += __shfl_sync(hmask, ihf, LW - 1, LW);
+        for (int o = 1; o < LW; o <<= 1) {
+            const float a = __shfl_up_sync(hmask, oh, o, LW), b = __shfl_up_sync(hmask, of, o, LW);
+            if (hl >= o) { oh += a; of += b; }
+        }
+        const float carry_h = __shfl_sync(hmask, oh, LW - 1, LW), carry_f = __shfl_sync(hmask, of, LW - 1, LW);
+        oh -= th;
+        of -= tf;
+        for (int k = kbeg; k < kend; ++k) {
+            Sh[k] += oh;
+            Sf[k] += of;
         }
         if (hl == 0) {
             Sh[K] = carry_h;
@@ -296,7 +302,7 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
                 LT[0].x = PAD_INV_T;  // level 0 (T = 0) emits nothing: every t is 0
                 continue;
             }
-            const float T = gr.theta * rcp_approx(log1pf(gr.ctil / ((float)f * dEt)));
+            const float T = gr.theta * rcp_approx(log1pf(cidE * rcp_approx((float)f)));
             LT[f].x = rcp_approx(T);
             // log2 of T clamped into the table: exponent split off exactly,
             // lg2.approx of the mantissa in [1/2, 1)
@@ -312,7 +318,10 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
             const float fe = floorf(e);
             ei[r] = (int)fe;
             mul[r] = dEt * ex2_approx(e - fe);  // e - fe in [0, 1)
-            const float mx = ldexpf(mul[r], ei[r]);
+            // mul 2^ei where that is a normal float (the scale is 0 outside
+            // the exponent range, so the test below fails there as well)
+            const float sc = (ei[r] >= -126 && ei[r] <= 127) ? __int_as_float((ei[r] + 127) << 23) : 0.f;
+            const float mx = mul[r] * sc;
             mulx[r] = (mx >= 1.17549435e-38f && mx < INFINITY) ? mx : __int_as_float(0x7fc00000);
         }
         __syncwarp(hmask);
