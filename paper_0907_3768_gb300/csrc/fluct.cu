@@ -319,10 +319,14 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
             ei[r] = (int)fe;
             mul[r] = dEt * ex2_approx(e - fe);  // e - fe in [0, 1)
             // mul 2^ei where that is a normal float (the scale is 0 outside
-            // the exponent range, so the test below fails there as well)
+            // the exponent range, so the test below fails there as well);
+            // below the normal range the rounded (subnormal or zero) value:
+            // such a level's P is below 2^-126 of the frame's, whatever its
+            // last bits; above it NaN, for the exact path
             const float sc = (ei[r] >= -126 && ei[r] <= 127) ? __int_as_float((ei[r] + 127) << 23) : 0.f;
             const float mx = mul[r] * sc;
-            mulx[r] = (mx >= 1.17549435e-38f && mx < INFINITY) ? mx : __int_as_float(0x7fc00000);
+            mulx[r] = (mx >= 1.17549435e-38f && mx < INFINITY) ? mx
+                    : ei[r] < 0 ? ldexpf(mul[r], ei[r]) : __int_as_float(0x7fc00000);
         }
         __syncwarp(hmask);
         // 5. forward cut-flux recursion from P_0 = 1: step j adds P_j's flux
@@ -356,14 +360,51 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
             }                                                                                 \
         }                                                                                     \
     }
+        // Fast form of a step: no test, only a flag (a branch per step
+        // measured 12 % of the kernel); a block of LW steps whose flag fails
+        // (a value past 2^100, or a level whose factor is not a normal float)
+        // is taken again from its saved state with the tested step.  Every P
+        // of a block that passes is below 2^100, so no register can pass
+        // 2^109 (at most M <= 512 terms P phi with phi <= 1), and after each
+        // block the frame is moved to the newest level when that is above
+        // 2^32.
+#define FL_FAST(J, RS, R0, OWN)                                                               \
+    {                                                                                         \
+        const int j_ = (J);                                                                   \
+        _Pragma("unroll") for (int r = (R0); r < MR; ++r) acc[r] = fmaf(ph[LW * r - j_], pj, acc[r]); \
+        pj = __shfl_sync(hmask, acc[RS] * mulx[RS], (OWN), LW);                                \
+        ok &= pj < 0x1p100f;                                                                  \
+    }
 #pragma unroll
         for (int r0 = 0; r0 < MR; ++r0) {
-            // levels LW r0 + 1 .. LW r0 + LW - 1 (this register of lanes 1..LW-1)
+            // block: levels LW r0 + 1 .. LW r0 + LW - 1 (this register of
+            // lanes 1..LW-1), then level LW (r0 + 1) (the next register of
+            // lane 0).  Saved state: the registers in the lanes' own LT[.].y
+            // (free until the distribution is written), and pj.
+#pragma unroll
+            for (int r = 0; r < MR; ++r) LT[hl + LW * r].y = acc[r];
+            const float pj0 = pj;
+            bool ok = true;
 #pragma unroll 2
-            for (int jj = 0; jj < LW - 1; ++jj) FL_STEP(LW * r0 + jj, r0, r0, jj + 1)
-            // level LW (r0 + 1) (the next register of lane 0)
-            if (r0 + 1 < MR) FL_STEP(LW * r0 + LW - 1, r0 + 1 < MR ? r0 + 1 : r0, r0 + 1, 0)
+            for (int jj = 0; jj < LW - 1; ++jj) FL_FAST(LW * r0 + jj, r0, r0, jj + 1)
+            if (r0 + 1 < MR) FL_FAST(LW * r0 + LW - 1, r0 + 1 < MR ? r0 + 1 : r0, r0 + 1, 0)
+            if (!ok) {  // the same on every lane of the problem (pj is broadcast)
+#pragma unroll
+                for (int r = 0; r < MR; ++r) acc[r] = LT[hl + LW * r].y;
+                pj = pj0;
+                for (int jj = 0; jj < LW - 1; ++jj) FL_STEP(LW * r0 + jj, r0, r0, jj + 1)
+                if (r0 + 1 < MR) FL_STEP(LW * r0 + LW - 1, r0 + 1 < MR ? r0 + 1 : r0, r0 + 1, 0)
+            } else {
+                const int e = ((__float_as_int(pj) >> 23) & 0xff) - 127;  // pj normal, < 2^100
+                if (e > 32) {
+                    const float sc = __int_as_float((127 - e) << 23);
+#pragma unroll
+                    for (int r = 0; r < MR; ++r) acc[r] *= sc;
+                    pj *= sc;
+                }
+            }
         }
+#undef FL_FAST
 #undef FL_STEP
         // the distribution in the final frame, normalised
         float pv[MR], z = 0.f;
