@@ -131,16 +131,18 @@ __device__ void herm(double t0, double m0, double t1, double m1, double tau, dou
 }
 
 // Inverse table nodes: u(t_m) and du/dt at t_m = m dy, by bisection-guarded
-// Newton on the FP64 Hermite interpolant of t(u).
+// Newton on the FP64 Hermite interpolant of t(u).  dy = 1 / invdy of the
+// grain's FP32 constant exactly, so that the device's y invdy puts node m at
+// m (the last node, at most a rounding past t_max, is taken at t_max).
 __global__ void k_inverse(int G, int NT, int NI, double log2Tmin, double h2, const double *lp,
-                          const double *sl, double *iu, double *idu) {
+                          const double *sl, const GrainParam *gp, double *iu, double *idu) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= G * NI) return;
     int g = i / NI, m = i % NI;
     const double *l = lp + (size_t)g * NT;
     const double *s = sl + (size_t)g * NT;
     double tmax = l[NT - 1] - l[0];
-    double y = (m == NI - 1) ? tmax : m * (tmax / (NI - 1));
+    double y = fmin(m / (double)gp[g].invdy, tmax);
     int lo = 0, hi = NT - 1;  // find j with t_j <= y <= t_j+1
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
@@ -168,13 +170,13 @@ __global__ void k_inverse(int G, int NT, int NI, double log2Tmin, double h2, con
 // flag: 1 where an interval is wider than 1/8 in log2 T (coarse tables:
 // 2^(tau du) then takes ex2 instead of the short series), 2 where the
 // interval is empty or its slopes are not finite.
-__global__ void k_ivrec(int G, int NT, int NI, const double *lp, const double *iu, const double *idu,
+__global__ void k_ivrec(int G, int NI, const GrainParam *gp, const double *iu, const double *idu,
                         float4 *ivr, int *flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= G * (NI - 1)) return;
     int g = i / (NI - 1), m = i % (NI - 1);
     size_t b = (size_t)g * NI + m;
-    const double dy = (lp[(size_t)g * NT + NT - 1] - lp[(size_t)g * NT]) / (NI - 1);
+    const double dy = 1.0 / (double)gp[g].invdy;
     const double du = iu[b + 1] - iu[b];
     const double a0 = du / (idu[b] * dy), a1 = du / (idu[b + 1] * dy);
     ivr[i] = make_float4((float)exp2(iu[b]), (float)du, (float)(a0 - 1.0), (float)(a1 - 1.0));
@@ -375,10 +377,11 @@ int build_context(dust_ctx *ctx, const double *lambda, const double *w, const do
     }
     k_fw32<<<blocks((size_t)G * (NT - 1)), B>>>(G, NT, h2, (double *)t_lp.p, (double *)t_sl.p,
                                                 (float4 *)(base + o_fw));
-    k_inverse<<<blocks((size_t)G * NI), B>>>(G, NT, NI, log2Tmin, h2, (double *)t_lp.p,
-                                             (double *)t_sl.p, (double *)t_iu.p, (double *)t_idu.p);
+    k_inverse<<<blocks((size_t)G * NI), B>>>(G, NT, NI, log2Tmin, h2, (double *)t_lp.p, (double *)t_sl.p,
+                                             (const GrainParam *)(base + o_gp), (double *)t_iu.p,
+                                             (double *)t_idu.p);
     DUST_CUDA_TRY(cudaMemset(t_bad.p, 0, sizeof(int)));
-    k_ivrec<<<blocks((size_t)G * (NI - 1)), B>>>(G, NT, NI, (double *)t_lp.p, (double *)t_iu.p,
+    k_ivrec<<<blocks((size_t)G * (NI - 1)), B>>>(G, NI, (const GrainParam *)(base + o_gp), (double *)t_iu.p,
                                                  (double *)t_idu.p, (float4 *)(base + o_ivr), (int *)t_bad.p);
     DUST_CUDA_TRY(cudaGetLastError());
     DUST_CUDA_TRY(cudaMemcpy(&bad, t_bad.p, sizeof(int), cudaMemcpyDeviceToHost));

@@ -54,19 +54,23 @@ __device__ __forceinline__ void solve_batch(const DevTables &tb, const int (&g)[
     float4 rv[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        // log2 s = e + log2 m with the exponent split off exactly and m in
-        // [1/2, 1), where lg2.approx is good to ~2^-22 absolute; the
-        // temperature error this causes is below 1e-7
+        // y = log2 s + f_g = Y0 + ly: the integer Y0 (s's exponent plus f_g,
+        // exact) and ly = log2 of the mantissa in [1/2, 1), where lg2.approx
+        // is good to ~2^-22 absolute
         const int bits = __float_as_int(s[i]);
-        const float mant = __int_as_float((bits & 0x007fffff) | 0x3f000000);
-        y[i] = (s[i] > 0.f) ? (float)(((bits >> 23) & 0xff) - 126) + lg2_approx(mant) + gq[i].x : -INFINITY;
+        const bool pos = s[i] > 0.f;  // false for 0, negatives and NaN
+        const float Y0 = pos ? (float)(((bits >> 23) & 0xff) - 126) + gq[i].x : 0.f;
+        const float ly = pos ? lg2_approx(__int_as_float((bits & 0x007fffff) | 0x3f000000)) : 0.f;
+        y[i] = pos ? Y0 + ly : -INFINITY;
         const bool bad = !(s[i] >= 0.f) || isinf(s[i]);
         fl[i] = bad ? DUST_FLAG_INVALID : (y[i] < 0.f ? DUST_FLAG_LOW : (y[i] > gq[i].y ? DUST_FLAG_HIGH : DUST_FLAG_OK));
-        const float yc = fminf(fmaxf(y[i], 0.f), gq[i].y);  // NaN -> 0
-        y[i] = yc;
-        const float fy = yc * gq[i].z;
-        m[i] = min((int)fy, tb.NI - 2);
-        ty[i] = fminf(fy - (float)m[i], 1.f);
+        // interval coordinate y invdy (node m at m): the product of the
+        // integer part is split exactly (ah + al) and the interval offset
+        // formed from the parts, so that it keeps ~2^-24 of an interval
+        // instead of ~2^-24 of y invdy (a few thousand)
+        const float ah = Y0 * gq[i].z, al = fmaf(Y0, gq[i].z, -ah), b = ly * gq[i].z;
+        m[i] = min(max((int)floorf(ah + b), 0), tb.NI - 2);
+        ty[i] = fminf(fmaxf(((ah - (float)m[i]) + b) + al, 0.f), 1.f);
     }
 #pragma unroll
     for (int i = 0; i < NB; ++i) rv[i] = __ldg(tb.ivr + (size_t)g[i] * (tb.NI - 1) + m[i]);
