@@ -120,6 +120,26 @@ def test_ragged_cell_counts(prec, C):
     _compare(out, ref, prec, wl)
 
 
+@pytest.mark.parametrize("n_table,tol_L", [(64, 1e-3), (256, 1e-4)])
+def test_coarse_tables(n_table, tol_L):
+    """Small tables.  At n_table = 64 the inverse-table intervals of the tiny
+    configuration span up to 0.18 in log2 T (more than 1/8), so 2^(tau du)
+    takes ex2 instead of its five-term series; in FP64 the cubic there is
+    good to 3e-6 in T (1e-8 at 256), so the FP32 T tolerance holds and L,
+    whose Wien terms scale T's error by up to ~90, gets 1e-3."""
+    from paper_0907_3768_gb300 import Context
+
+    wl = synth.make_workload(0)
+    ref = oracle.run_workload(wl)
+    with Context(wl.lam, wl.w, wl.C_abs, wl.T_min, wl.T_max, n_table, "fp32") as ctx:
+        assert ctx.info()["n_table"] == n_table
+        out = _run(ctx, wl.J, wl.n, precision="fp32")
+    assert_flags_match(out["flags"], ref, wl)
+    eT = t_err(out["T"], ref["T"], ref["flags"])
+    assert eT.max(initial=0.0) <= 1e-5, f"T err {eT.max():.3g}"
+    assert l_err(out["L"], ref["L"]).max() <= tol_L
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_odd_shapes(prec):
     """G not a multiple of 16, K not a multiple of 8 or of the 32-wavelength chunk."""
