@@ -618,6 +618,20 @@ __global__ void __launch_bounds__(KE_TH, 1) k_emit(const __grid_constant__ EmitB
     }
 }
 
+// Residual of one cell (Eq. 6 against Eqs. 8-10, see residual()) from its
+// k-group partials, summed in ascending order, and its cell record.
+__device__ __forceinline__ void cell_resid(const EmitReq &q, int64_t cell) {
+    const int NKG = q.tb.NKG;
+    const float2 *pp = q.part + cell * NKG;
+    float h = 0.f, l = 0.f;
+    for (int kg = 0; kg < NKG; ++kg) {
+        const float2 v = pp[kg];
+        ff_add(h, l, v.x, v.y);
+    }
+    const CellInfo ci = q.cell[cell];
+    q.resid[cell] = (double)residual(h, l, ci.ah, ci.al, q.tb);
+}
+
 // Solve and emission of one request in one warp-specialized kernel, for
 // either form of n (general, or the dust-mass form n_g m_c with 1/T-only
 // pairs), with the emission weights resident in shared memory.
@@ -697,6 +711,7 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
     if (warp >= FE_W) {
         // ------------------------------------------------------------ solvers
         const int sw = warp - FE_W;
+        const bool rs = (q.mode & EMIT_RESID) != 0;
         int it = 0;
         int64_t tile = fse_tile(0, ntiles);
         float s0[NB], n0[NB];
@@ -709,6 +724,12 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
             // a warp with no slot in the previous tile (a ragged one) prefetched nothing
             if (sw < nc && pf != tile) load_pass<NB>(q, ordered_cell(q, tile * TC + sw), 0, lane, s0, n0);
             if (!(ok = mbar_wait(&empty[b], ph ^ 1, abort_flag, tb.status))) break;
+            // the buffer's previous tile (it - FSE_NBUF) is fully emitted: one
+            // solver warp, in turn, folds its cells' residuals (lane = cell)
+            if (rs && it >= FSE_NBUF && sw == it % FS_W) {
+                const int64_t i = fse_tile(it - FSE_NBUF, ntiles) * TC + lane;
+                if (i < q.C) cell_resid(q, ordered_cell(q, i));
+            }
             for (int cl = sw; cl < nc; cl += FS_W) {
                 const int64_t cell = ordered_cell(q, tile * TC + cl);
                 // next cell of this warp: in this tile, else its first in the next tile
@@ -728,6 +749,13 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
             __syncwarp();
             if (lane == 0) mbar_arrive(&full[b]);
         }
+        // the residuals of the last FSE_NBUF tiles, once their emission is done
+        if (rs && ok && sw == 0)
+            for (int j = max(0, it - FSE_NBUF); j < it; ++j) {
+                if (!mbar_wait(&empty[j % FSE_NBUF], (uint32_t)((j / FSE_NBUF) & 1), abort_flag, tb.status)) break;
+                const int64_t i = fse_tile(j, ntiles) * TC + lane;
+                if (i < q.C) cell_resid(q, ordered_cell(q, i));
+            }
     } else {
         // ------------------------------------------------------------ emission
         if (warp >= NKG * (FSE_NBUF - 1) - 1) return;  // see the phase argument above
@@ -763,7 +791,8 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
 
 // Energy-balance residual of every cell of the requests that want it: one
 // thread per cell sums the cell's k-group partials in ascending order, so
-// the order depends only on NKG.
+// the order depends only on NKG (cell_resid; the warp-specialized kernel
+// folds its own cells with the same function).
 __global__ void __launch_bounds__(SOLVE_TH) k_resid(const __grid_constant__ EmitBatch E) {
     const int64_t stride = (int64_t)gridDim.x * SOLVE_TH;
     int ri = 0;
@@ -771,16 +800,7 @@ __global__ void __launch_bounds__(SOLVE_TH) k_resid(const __grid_constant__ Emit
         while (ri + 1 < E.nreq && u >= E.req[ri + 1].cell_begin) ++ri;
         const EmitReq &q = E.req[ri];
         if (!(q.mode & EMIT_RESID)) continue;
-        const int NKG = q.tb.NKG;
-        const int64_t cell = u - q.cell_begin;
-        const float2 *pp = q.part + cell * NKG;
-        float h = 0.f, l = 0.f;
-        for (int kg = 0; kg < NKG; ++kg) {
-            const float2 v = pp[kg];
-            ff_add(h, l, v.x, v.y);
-        }
-        const CellInfo ci = q.cell[cell];
-        q.resid[cell] = (double)residual(h, l, ci.ah, ci.al, q.tb);
+        cell_resid(q, u - q.cell_begin);
     }
 }
 
@@ -1056,13 +1076,7 @@ int launch_solve_emit_fused(const EmitReq &req, int TC, size_t smem, int num_sms
     const unsigned grid = (unsigned)std::min<int64_t>(E.ntiles, num_sms);
     int rc = mass ? launch_fse<true>(r, nb, grid, smem, st) : launch_fse<false>(r, nb, grid, smem, st);
     if (rc != DUST_OK) return rc;
-    if (nlaunch) *nlaunch = 1;
-    if (r.mode & EMIT_RESID) {
-        const int64_t rgrid = std::min<int64_t>((r.C + SOLVE_TH - 1) / SOLVE_TH, (int64_t)num_sms * 16);
-        k_resid<<<(unsigned)rgrid, SOLVE_TH, 0, st>>>(E);
-        DUST_CUDA_TRY(cudaGetLastError());
-        if (nlaunch) *nlaunch = 2;
-    }
+    if (nlaunch) *nlaunch = 1;  // the residual fold runs inside the kernel
     return DUST_OK;
 }
 
