@@ -41,8 +41,8 @@ KERNEL_SOURCES = {
 }
 RECORDED_TRAFFIC = {
     # kernel: (bytes per launch on the bench's workload, profile summary, sources sha256[:16])
-    "k_solve_emit": (218.488576e6 + 351.847424e6, "profiles/k_solve_emit_2e18cells_K200_G96.md", "ff72a021d946068a"),
-    "k_emit": (220.361216e6 + 218.373376e6, "profiles/k_emit_2e18cells_K200_G96.md", "ff72a021d946068a"),
+    "k_solve_emit": (234.664448e6 + 358.100224e6, "profiles/k_solve_emit_2e18cells_K200_G96.md", "d579eea9fbbab15f"),
+    "k_emit": (220.435456e6 + 218.797056e6, "profiles/k_emit_2e18cells_K200_G96.md", "d579eea9fbbab15f"),
     # the full-size launch, DRAM counters only (one ncu pass; the 2^14-cell --set full capture is in the same file)
     "k_fluct": (256.108544e6 + 175.599872e6, "profiles/k_fluct_2e14cells_K200_G36_M128.md", "30e5b68ef1b8bba7"),
 }
@@ -351,16 +351,20 @@ def run_ours(args):
     achieved = terms / (ms_emit * 1e-3) / 1e9
     peak = ex2_rate / 1e9
     roofline = {"bound": "alu",
-                "kernel": ("k_solve_emit (temperature solve + emission, warp-specialized) + k_resid" if solve_in_emit
-                           else "k_emit (emission) + k_resid"),
+                "kernel": ("k_solve_emit (temperature solve + emission + residual fold, warp-specialized)"
+                           if solve_in_emit else "k_emit (emission) + k_resid"),
                 "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "G Planck terms/s",
                 "frac": round(achieved / peak, 4),
                 "peak_source": "measured MUFU ex2.approx issue rate (dust_diag_throughput), 1 ex2 per term",
                 "traffic": traffic_b if (C, K, G) == (1 << 18, 200, 96) and world == 1 else None,
                 "traffic_unit": "bytes per launch (ncu DRAM read + write)",
                 "traffic_source": traffic_note,
-                "algorithmic_bytes": C * (4 * ((G + 15) // 16 * 16) + 4 * G + 4 * G + G + 16 + 4 * K + 8 * ((K + 7) // 8))
-                if solve_in_emit else C * (8 * ((G + 7) // 8 * 8) + 16 + 4 * K + 8 * ((K + 7) // 8)),
+                # per cell, fused: S, n and the order index in; T, flags, L and the residual out; the cell
+                # record and the k-group partials once (written, then read back by the fold).  Two-kernel
+                # emission: pairs, record and order index in; L and the partials out
+                "algorithmic_bytes": C * (4 * ((G + 15) // 16 * 16) + 4 * G + 4 + 4 * G + G + 4 * K + 8 + 16
+                                          + 8 * ((K + 7) // 8))
+                if solve_in_emit else C * (8 * ((G + 7) // 8 * 8) + 16 + 4 + 4 * K + 8 * ((K + 7) // 8)),
                 "ms_per_launch": round(ms_emit, 4),
                 "fma_pipe_peak_Gflop_lanes": round(fma_rate / 1e9, 1)}
     if solve_in_emit:
