@@ -236,8 +236,9 @@ def test_cell_results_independent_of_batch(prec):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_host_entry_point_matches_device(prec):
-    """Host buffers through the copy-in / compute / copy-out pipeline: 5 chunks
-    over 3 buffer sets (a ragged last one), called twice in a row."""
+    """Host buffers through the copy-in / compute / copy-out pipeline: six
+    chunks of growing size over 3 buffer sets (a ragged last one), called
+    twice in a row."""
     from paper_0907_3768_gb300 import Context
 
     wl = synth.make_workload(1, cells=np.arange(40001))  # K = 200: rows already 16-byte multiples
