@@ -315,9 +315,10 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
 // emission over those that want L or resid; `between` (optional) is recorded
 // on `st` between the two kernels.
 // With solved = true the temperatures, pairs and cell records are already
-// there (fused absorption + solve) and only the emission runs.
+// there (fused absorption + solve) and only the emission runs; with pass0 > 0
+// the grain passes before pass0 are done too (their sums carried in accp).
 int launch_emit_batch(EmitBatch &B, int num_sms, cudaStream_t st, cudaEvent_t between = nullptr,
-                      bool solved = false, int *nlaunch = nullptr);
+                      bool solved = false, int *nlaunch = nullptr, int pass0 = 0);
 
 // Orders the cells of every request of the batch by the class of its key
 // (three launches: zero the counts, classify, scatter).  Cells of one class
@@ -328,9 +329,9 @@ int launch_order(OrderBatch &B, cudaStream_t st, int *nlaunch);
 inline int order_ref_grain(int G) { return G / 2; }
 
 // Warp-specialized solve + emission over one request: the plan (its tile of
-// TC cells and shared memory, 0 where it does not apply) and the launch (the
-// kernel, then the residual fold when the request wants it).
-size_t plan_solve_emit(const dust_ctx *ctx, bool emit, bool mass, int *TC);
+// TC cells, the grains [0, gc) it emits, and shared memory; 0 where it does
+// not apply) and the launch (for req.g1 = gc < G8 the first grain pass only).
+size_t plan_solve_emit(const dust_ctx *ctx, bool emit, bool mass, int *TC, int *gc);
 int launch_solve_emit_fused(const EmitReq &req, int TC, size_t smem, int num_sms, cudaStream_t st,
                             int *nlaunch = nullptr);
 

@@ -118,8 +118,9 @@ int solve_view(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t 
                                          : launch_gemm_tc(ctx, precision, C, J, ld, sv.S, st);
     }
     if (rc == DUST_OK) nl_total += 1;
-    int ftc = 0;
-    const size_t fsmem = !fused && ctx->fused_emit ? plan_solve_emit(ctx, L || resid, mass, &ftc) : 0;
+    int ftc = 0, fgc = 0;
+    const size_t fsmem = !fused && ctx->fused_emit ? plan_solve_emit(ctx, L || resid, mass, &ftc, &fgc) : 0;
+    if (fsmem && fgc != p.gcp) return set_error(DUST_EINVAL, "internal: grain passes of the two emission forms differ");
     if (rc == DUST_OK && (L || resid) && sv.order && sv.bkt && sv.hist) {
         // emission order: cells classed by the absorbed power of the reference
         // grain (S), or by its inverse temperature where S stayed in tensor memory
@@ -148,9 +149,15 @@ int solve_view(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t 
         if (ev && ev[1]) DUST_CUDA_TRY(cudaEventRecord(ev[1], st));
         int nl = 0;
         if (fsmem) {
-            // the solve runs inside the emission kernel: its time is reported with the emission's
+            // the solve runs inside the emission kernel: its time is reported with the emission's;
+            // where the grains come in passes the kernel emits the first and k_emit the others
             if (ev && ev[2]) DUST_CUDA_TRY(cudaEventRecord(ev[2], st));
             rc = launch_solve_emit_fused(B.req[0], ftc, fsmem, ctx->num_sms, st, &nl);
+            if (rc == DUST_OK && fgc < (mass ? ctx->tbm : ctx->tb).G8) {
+                nl_total += nl;
+                nl = 0;
+                rc = launch_emit_batch(B, ctx->num_sms, st, nullptr, true, &nl, 1);
+            }
         } else {
             rc = launch_emit_batch(B, ctx->num_sms, st, ev ? ev[2] : nullptr, fused, &nl);
         }

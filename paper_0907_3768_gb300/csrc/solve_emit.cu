@@ -95,16 +95,18 @@ __device__ __forceinline__ void load_pass(const EmitReq &q, int64_t cell, int gb
 // the roots, T and flags to global memory, and (emission) the pairs
 // (1/T, n 2^-m_c) and the cell record: to the request's scratch (q.prep
 // [C][G8], float2 or, in the dust-mass form, 1/T only; q.cell), or with SMEM
-// to `spairs` (G8 float2, or G8 floats in the dust-mass form) and `srec` in
-// shared memory as well as the record to q.cell.  s0 / n0: this cell's first
-// pass, loaded.
+// to `spairs` (its first gsm grains, float2 or floats in the dust-mass form)
+// and `srec` in shared memory as well as the record to q.cell, and with
+// also_glb the pairs of every grain to q.prep too.  s0 / n0: this cell's
+// first pass, loaded.
 // MF: the form of n when the caller knows it (0 general, 1 dust-mass), -1 to
 // read it from the request; EMIT: the emission is known to follow (the fused
 // kernel, whose launch has NB = ceil(G8 / 32), so a cell is one pass when
 // NB < NB_MAX).
 template <int NB, bool SMEM, bool TONLY = false, int MF = -1, bool EMIT = false>
 __device__ __forceinline__ void solve_cell(const EmitReq &q, int64_t cell, int lane, const float (&s0)[NB],
-                                           const float (&n0)[NB], float2 *spairs, CellInfo *srec) {
+                                           const float (&n0)[NB], float2 *spairs, CellInfo *srec,
+                                           int gsm = 1 << 30, bool also_glb = false) {
     const DevTables &tb = q.tb;
     const int G = tb.G, G8 = tb.G8;
     const bool emit = EMIT || (!TONLY && (q.mode & EMIT_ON) != 0), rs = (q.mode & EMIT_RESID) != 0;
@@ -159,13 +161,13 @@ __device__ __forceinline__ void solve_cell(const EmitReq &q, int64_t cell, int l
                 if (!TONLY) grain_out(tb, g, Tv[i], fl[i], s[i], nv[i], mc, mass, rs, invT, nn, ah, al);
             }
             if (emit) {
-                if (SMEM) {
+                if (SMEM && g < gsm) {
                     if (mass) reinterpret_cast<float *>(spairs)[g] = invT;
                     else spairs[g] = make_float2(invT, nn);
-                } else if (mass) {
-                    reinterpret_cast<float *>(q.prep)[cell * G8 + g] = invT;
-                } else {
-                    q.prep[cell * G8 + g] = make_float2(invT, nn);
+                }
+                if (!SMEM || also_glb) {
+                    if (mass) reinterpret_cast<float *>(q.prep)[cell * G8 + g] = invT;
+                    else q.prep[cell * G8 + g] = make_float2(invT, nn);
                 }
             }
         }
@@ -678,10 +680,14 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevTables &tb = q.tb;
     const int G8 = tb.G8, NKG = tb.NKG;
+    // the grains of this launch, [0, gc): all of them, or the first grain pass
+    // of a request whose weights do not fit (the later passes follow in k_emit)
+    const int gc = q.g1 - q.g0;
+    const bool whole = gc == G8;
     constexpr int TC = FSE_TC;
-    const int CST = 2 * G8 + 1;
+    const int CST = 2 * gc + 1;
     // odd row stride of a pair tile (in float2, or floats for 1/T alone): a warp's cells fall in distinct banks
-    const int PS = G8 + 1;
+    const int PS = gc + 1;
     constexpr int PW = MASS ? 1 : 2;  // floats per pair
     float4 *sC = reinterpret_cast<float4 *>(smem_raw);                          // [NKG][CST]
     float *sP = reinterpret_cast<float *>(sC + (size_t)NKG * CST);             // [FSE_NBUF][TC][PS][PW]
@@ -695,9 +701,9 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
 
     {
         const float4 *src = reinterpret_cast<const float4 *>(tb.Chat);
-        for (int i = tid; i < NKG * 2 * G8; i += FSE_TH) {
-            const int kg = i / (2 * G8), o = i - kg * 2 * G8;
-            sC[(size_t)kg * CST + o] = __ldg(src + i);
+        for (int i = tid; i < NKG * 2 * gc; i += FSE_TH) {
+            const int kg = i / (2 * gc), o = i - kg * 2 * gc;
+            sC[(size_t)kg * CST + o] = __ldg(src + ((size_t)kg * G8 + q.g0) * 2 + o);
         }
     }
     if (tid == 0) {
@@ -711,7 +717,7 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
     if (warp >= FE_W) {
         // ------------------------------------------------------------ solvers
         const int sw = warp - FE_W;
-        const bool rs = (q.mode & EMIT_RESID) != 0;
+        const bool rs = (q.mode & EMIT_RESID) != 0 && whole;  // else the fold follows the last pass
         int it = 0;
         int64_t tile = fse_tile(0, ntiles);
         float s0[NB], n0[NB];
@@ -742,7 +748,7 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
                 pf = more ? tn : -1;
                 solve_cell<NB, true, false, MASS ? 1 : 0, true>(q, cell, lane, s0, n0,
                                                                 reinterpret_cast<float2 *>(sP + ((size_t)b * TC + cl) * PS * PW),
-                                                                sI + b * TC + cl);
+                                                                sI + b * TC + cl, gc, !whole);
 #pragma unroll
                 for (int i = 0; i < NB; ++i) { s0[i] = s1[i]; n0[i] = n1[i]; }
             }
@@ -778,10 +784,18 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
                 const float naxl = load_nax(tb, ikg, nax2);
 #pragma unroll
                 for (int p = 0; p < 4; ++p) acc[p] = make_float2(0.f, 0.f);
-                emit_item<MASS, PW>(sP + ((size_t)b * TC + lane) * PS * PW, sC + (size_t)ikg * CST, G8, nax2, naxl, acc);
-                const CellInfo ci = sI[b * TC + lane];
-                emit_item_out<MASS>(q, ordered_cell(q, tile * TC + lane), ikg, acc, ci.mc,
-                                    MASS ? __int_as_float(ci.ms_bits) : 1.f, storeL, vecL, rs);
+                emit_item<MASS, PW>(sP + ((size_t)b * TC + lane) * PS * PW, sC + (size_t)ikg * CST, gc, nax2, naxl, acc);
+                const int64_t cell = ordered_cell(q, tile * TC + lane);
+                if (whole) {
+                    const CellInfo ci = sI[b * TC + lane];
+                    emit_item_out<MASS>(q, cell, ikg, acc, ci.mc, MASS ? __int_as_float(ci.ms_bits) : 1.f, storeL,
+                                        vecL, rs);
+                } else {
+                    // the first pass's sums, carried to the next (k_emit's layout)
+                    float2 *ap = q.accp + ((size_t)cell * NKG + ikg) * 4;
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) ap[p] = acc[p];
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[b]);
@@ -901,7 +915,7 @@ void fill_emit_req(const dust_ctx *ctx, const EmitPlan &p, int64_t C, const Scra
 // Numbers the cells and emission tiles of a filled batch; launches the solve
 // over every request, then the emission over the requests that want it.
 int launch_emit_batch(EmitBatch &B, int num_sms, cudaStream_t st, cudaEvent_t between,
-                      bool solved, int *nlaunch) {
+                      bool solved, int *nlaunch, int pass0) {
     int nl = 0;
     int64_t cells = 0;
     for (int i = 0; i < B.nreq; ++i) {
@@ -979,7 +993,7 @@ int launch_emit_batch(EmitBatch &B, int num_sms, cudaStream_t st, cudaEvent_t be
             if ((r.mode & EMIT_ON) && r.gcp < r.tb.G8 && !r.accp)
                 return set_error(DUST_EINVAL, "request %d needs grain passes but has no buffer for their sums", i);
         }
-        for (int pi = 0;; ++pi) {
+        for (int pi = pass0;; ++pi) {
             bool any = false;
             for (int i = 0; i < B.nreq; ++i) {
                 const EmitReq &r = B.req[i];
@@ -1025,18 +1039,32 @@ int launch_emit_batch(EmitBatch &B, int num_sms, cudaStream_t st, cudaEvent_t be
     return DUST_OK;
 }
 
-// Tile and shared memory of the warp-specialized solve + emission kernel for
-// the context, or 0 where it does not apply: no emission, or emission
-// weights that do not fit beside the pair tiles with room left for L1 (the
-// solve's table lookups live there).
-size_t plan_solve_emit(const dust_ctx *ctx, bool emit, bool mass, int *TC) {
+// Tile, grains and shared memory of the warp-specialized solve + emission
+// kernel for the context, or 0 where it does not apply (no emission).  All
+// grains when their weights fit beside the pair tiles with room left for L1
+// (the solve's table lookups live there); else, where the two-kernel form
+// takes the grains in passes, the first of those passes (its grain chunk,
+// the same as k_emit's) with the rest of shared memory, the later passes
+// then following in k_emit.  0 where neither fits.
+size_t plan_solve_emit(const dust_ctx *ctx, bool emit, bool mass, int *TC, int *gc) {
     if (!emit || (mass && !ctx->mass_ready)) return 0;
     const DevTables &tb = mass ? ctx->tbm : ctx->tb;
     const int tc = FSE_TC;
-    const size_t smem = (size_t)tb.NKG * (2 * tb.G8 + 1) * 16 + (((size_t)FSE_NBUF * tc * (tb.G8 + 1) * (mass ? 4 : 8) + 15) & ~(size_t)15) +
-                        (size_t)FSE_NBUF * tc * sizeof(CellInfo) + 2 * FSE_NBUF * sizeof(uint64_t) + 16;
-    if (smem > 160 * 1024) return 0;
+    auto bytes = [&](int g) {
+        return (size_t)tb.NKG * (2 * g + 1) * 16 + (((size_t)FSE_NBUF * tc * (g + 1) * (mass ? 4 : 8) + 15) & ~(size_t)15) +
+               (size_t)FSE_NBUF * tc * sizeof(CellInfo) + 2 * FSE_NBUF * sizeof(uint64_t) + 16;
+    };
+    int g = tb.G8;
+    size_t smem = bytes(g);
+    if (smem > 160 * 1024) {
+        g = plan_emit(ctx, true, mass).gcp;
+        if (g >= tb.G8) return 0;
+        smem = bytes(g);
+        const size_t optin = ctx->smem_optin ? ctx->smem_optin : 99 * 1024;
+        if (smem > optin - 1024) return 0;
+    }
     *TC = tc;
+    *gc = g;
     return smem;
 }
 
