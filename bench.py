@@ -776,6 +776,8 @@ def run_large(args, dev, local, ex2_rate):
         ctx.close()
         ms_a, ms_b = r["full"]["ms_absorb"], r["full"]["ms_emit"]
         r["roofline_emit"] = {"bound": "alu", "unit": "G Planck terms/s",
+                              "kernels": "k_solve_emit (temperature solve + first grain pass) + k_emit (later passes)"
+                                         " + k_resid" if r["full"]["ms_solve"] < 0.02 * ms_b else "k_emit + k_resid",
                                     "achieved": round(C * G * K / (ms_b * 1e-3) / 1e9, 1),
                                     "peak": round(ex2_rate / 1e9, 1),
                                     "frac": round(C * G * K / (ms_b * 1e-3) / ex2_rate, 4)}
