@@ -675,15 +675,16 @@ __device__ __forceinline__ int64_t fse_tile(int64_t it, int64_t ntiles) {
     return it < nb ? blockIdx.x + j * gridDim.x : ntiles;
 }
 
-template <int NB, bool MASS>
+template <int NB, bool MASS, bool PASS>
 __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant__ EmitReq q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevTables &tb = q.tb;
     const int G8 = tb.G8, NKG = tb.NKG;
-    // the grains of this launch, [0, gc): all of them, or the first grain pass
-    // of a request whose weights do not fit (the later passes follow in k_emit)
-    const int gc = q.g1 - q.g0;
-    const bool whole = gc == G8;
+    // the grains of this launch, [0, gc): all of them, or (PASS) the first
+    // grain pass of a request whose weights do not fit (the later passes
+    // follow in k_emit)
+    const int gc = PASS ? q.g1 - q.g0 : G8;
+    constexpr bool whole = !PASS;
     constexpr int TC = FSE_TC;
     const int CST = 2 * gc + 1;
     // odd row stride of a pair tile (in float2, or floats for 1/T alone): a warp's cells fall in distinct banks
@@ -748,7 +749,7 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
                 pf = more ? tn : -1;
                 solve_cell<NB, true, false, MASS ? 1 : 0, true>(q, cell, lane, s0, n0,
                                                                 reinterpret_cast<float2 *>(sP + ((size_t)b * TC + cl) * PS * PW),
-                                                                sI + b * TC + cl, gc, !whole);
+                                                                sI + b * TC + cl, PASS ? gc : 1 << 30, PASS);
 #pragma unroll
                 for (int i = 0; i < NB; ++i) { s0[i] = s1[i]; n0[i] = n1[i]; }
             }
@@ -786,7 +787,7 @@ __global__ void __launch_bounds__(FSE_TH, 1) k_solve_emit(const __grid_constant_
                 for (int p = 0; p < 4; ++p) acc[p] = make_float2(0.f, 0.f);
                 emit_item<MASS, PW>(sP + ((size_t)b * TC + lane) * PS * PW, sC + (size_t)ikg * CST, gc, nax2, naxl, acc);
                 const int64_t cell = ordered_cell(q, tile * TC + lane);
-                if (whole) {
+                if constexpr (whole) {
                     const CellInfo ci = sI[b * TC + lane];
                     emit_item_out<MASS>(q, cell, ikg, acc, ci.mc, MASS ? __int_as_float(ci.ms_bits) : 1.f, storeL,
                                         vecL, rs);
@@ -1069,18 +1070,18 @@ size_t plan_solve_emit(const dust_ctx *ctx, bool emit, bool mass, int *TC, int *
 }
 
 // The fused kernel over one request (general form), then the residual fold.
-template <bool MASS>
+template <bool MASS, bool PASS>
 int launch_fse(const EmitReq &r, int nb, unsigned grid, size_t smem, cudaStream_t st) {
-    const void *kern = nb == 1 ? reinterpret_cast<const void *>(k_solve_emit<1, MASS>)
-                     : nb == 2 ? reinterpret_cast<const void *>(k_solve_emit<2, MASS>)
-                     : nb == 3 ? reinterpret_cast<const void *>(k_solve_emit<3, MASS>)
-                               : reinterpret_cast<const void *>(k_solve_emit<4, MASS>);
+    const void *kern = nb == 1 ? reinterpret_cast<const void *>(k_solve_emit<1, MASS, PASS>)
+                     : nb == 2 ? reinterpret_cast<const void *>(k_solve_emit<2, MASS, PASS>)
+                     : nb == 3 ? reinterpret_cast<const void *>(k_solve_emit<3, MASS, PASS>)
+                               : reinterpret_cast<const void *>(k_solve_emit<4, MASS, PASS>);
     DUST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     switch (nb) {
-        case 1: k_solve_emit<1, MASS><<<grid, FSE_TH, smem, st>>>(r); break;
-        case 2: k_solve_emit<2, MASS><<<grid, FSE_TH, smem, st>>>(r); break;
-        case 3: k_solve_emit<3, MASS><<<grid, FSE_TH, smem, st>>>(r); break;
-        default: k_solve_emit<4, MASS><<<grid, FSE_TH, smem, st>>>(r); break;
+        case 1: k_solve_emit<1, MASS, PASS><<<grid, FSE_TH, smem, st>>>(r); break;
+        case 2: k_solve_emit<2, MASS, PASS><<<grid, FSE_TH, smem, st>>>(r); break;
+        case 3: k_solve_emit<3, MASS, PASS><<<grid, FSE_TH, smem, st>>>(r); break;
+        default: k_solve_emit<4, MASS, PASS><<<grid, FSE_TH, smem, st>>>(r); break;
     }
     DUST_CUDA_TRY(cudaGetLastError());
     return DUST_OK;
@@ -1102,7 +1103,9 @@ int launch_solve_emit_fused(const EmitReq &req, int TC, size_t smem, int num_sms
     const int nb = std::min(NB_MAX, (r.tb.G8 + 31) / 32);
     const bool mass = (r.mode & EMIT_MASS) != 0;
     const unsigned grid = (unsigned)std::min<int64_t>(E.ntiles, num_sms);
-    int rc = mass ? launch_fse<true>(r, nb, grid, smem, st) : launch_fse<false>(r, nb, grid, smem, st);
+    const bool pass = r.g1 - r.g0 < r.tb.G8;  // the first of several grain passes
+    int rc = mass ? (pass ? launch_fse<true, true>(r, nb, grid, smem, st) : launch_fse<true, false>(r, nb, grid, smem, st))
+                  : (pass ? launch_fse<false, true>(r, nb, grid, smem, st) : launch_fse<false, false>(r, nb, grid, smem, st));
     if (rc != DUST_OK) return rc;
     if (nlaunch) *nlaunch = 1;  // the residual fold runs inside the kernel
     return DUST_OK;
