@@ -41,8 +41,8 @@ KERNEL_SOURCES = {
 }
 RECORDED_TRAFFIC = {
     # kernel: (bytes per launch on the bench's workload, profile summary, sources sha256[:16])
-    "k_solve_emit": (234.664448e6 + 358.100224e6, "profiles/k_solve_emit_2e18cells_K200_G96.md", "d579eea9fbbab15f"),
-    "k_emit": (220.435456e6 + 218.797056e6, "profiles/k_emit_2e18cells_K200_G96.md", "d579eea9fbbab15f"),
+    "k_solve_emit": (234.917888e6 + 358.397696e6, "profiles/k_solve_emit_2e18cells_K200_G96.md", "8870be16607616af"),
+    "k_emit": (220.424192e6 + 218.604288e6, "profiles/k_emit_2e18cells_K200_G96.md", "8870be16607616af"),
     # the full-size launch, DRAM counters only (one ncu pass; the 2^14-cell --set full capture is in the same file)
     "k_fluct": (256.108544e6 + 175.599872e6, "profiles/k_fluct_2e14cells_K200_G36_M128.md", "30e5b68ef1b8bba7"),
 }
