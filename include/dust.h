@@ -120,12 +120,14 @@ int dust_ctx_set_fused(dust_ctx *ctx, int fused);
 
 /* Kernel layout of the temperature solve and the emission (Eqs. 7-10) in
  * later dust_solve calls: fused != 0 runs them as one warp-specialized kernel
- * where it applies (L or resid wanted, and the emission weights fitting in
- * shared memory beside three tiles of (1/T, n) pairs; other calls keep the
- * two kernels), in dust_solve and dust_solve_mass alike.  Its solver warps solve the next
- * tile of cells into shared memory while its emission warps emit the current
- * one.  T, flags, L and resid are bitwise the same either way.  On by
- * default; ignored when dust_ctx_set_fused is on.  Takes the context's lock; returns DUST_OK, or
+ * where it applies (L or resid wanted), in dust_solve and dust_solve_mass
+ * alike.  Its solver warps solve the next tile of cells into shared memory
+ * while its emission warps emit the current one.  Where the emission weights
+ * do not fit in shared memory beside three tiles of (1/T, n) pairs, the
+ * emission runs in grain passes: the fused kernel solves every grain and
+ * emits the first pass, a second kernel the others.  T, flags, L and resid
+ * are bitwise the same either way.  On by default; ignored when
+ * dust_ctx_set_fused is on.  Takes the context's lock; returns DUST_OK, or
  * DUST_EINVAL for a NULL context. */
 int dust_ctx_set_fused_emit(dust_ctx *ctx, int fused);
 
