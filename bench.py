@@ -382,6 +382,22 @@ def run_ours(args):
             "achieved": round(terms / (prof_2[2] * 1e-3) / 1e9, 2), "frac": round(terms / (prof_2[2] * 1e-3) / ex2_rate, 4),
             "step_ms": round(ms_2, 5), "ms_solve": round(prof_2[1], 5), "bitwise_equal": bool(same2)}
 
+    # ablation of the split's third product: J split, W rounded to 16 bits once (two MMAs per K step)
+    ablation_products, extra_out = None, {}
+    if main != "fp32":
+        cm = ctxs[main]
+        cm.set_split_products(2)
+        try:
+            ms_p, out_p, prof_p, _ = timed(cm, k2, 3, main, profile=True)
+        finally:
+            cm.set_split_products(3)
+        ablation_products = {"products": 2, "ms_step": round(ms_p, 5), "ms_absorb_and_order": round(prof_p[0], 5),
+                             "three_products_ms_step": round(ms_main, 5),
+                             "three_products_ms_absorb_and_order": round(res[main]["prof"][0], 5),
+                             "note": "dust_ctx_set_split_products(ctx, 2): J_hi W_hi + J_lo W_hi, the J_hi W_lo "
+                                     "product left out; not held to the mixed tolerances"}
+        extra_out["two_products"] = out_p
+
     line = {
         "metric": METRIC, "value": aggregate_rate(C * G, world, ms_main * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_main, 5),
@@ -438,7 +454,12 @@ def run_ours(args):
         line["fluctuating_grains"] = fluctuating(ctxs[main], wl, J, n, stream, args, world, ex2_rate,
                                                  oracle_sample=rank == 0 and world == 1 and not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"], line["err_vs_oracle"] = cpu_baseline(args, wl, res)
+        line["cpu_baseline"], line["err_vs_oracle"], extra_err = cpu_baseline(args, wl, res, extra_out)
+        if ablation_products is not None:
+            ablation_products["err_vs_oracle"] = extra_err.get("two_products")
+    if ablation_products is not None:
+        line["ablation_split_products"] = ablation_products
+    extra_out.clear()
     del out_main, res, Jbuf, J, n
     torch.cuda.empty_cache()
     if not args.no_large:
@@ -689,7 +710,7 @@ def tiny_errors(local, dev):
     return errs
 
 
-def cpu_baseline(args, wl_full, res):
+def cpu_baseline(args, wl_full, res, extra=None):
     import numpy as np
 
     sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -701,19 +722,21 @@ def cpu_baseline(args, wl_full, res):
             "sample": f"first {nc} of {wl_full.n_cells_total} cells, full path (A, Brent T, L, resid), "
                       f"FP64 C + OpenMP, {dt:.1f} s"}
     errs = {}
-    for p, r in res.items():
-        out = r["out"]
+    items = [(p, r["out"], errs) for p, r in res.items()]
+    extra_errs = {}
+    items += [(p, o, extra_errs) for p, o in (extra or {}).items()]
+    for p, out, dst in items:
         T = out["T"][:nc].cpu().numpy()
         L = out["L"][:nc].cpu().numpy()
         fl = out["flags"][:nc].cpu().numpy()
         rs = out["resid"][:nc].cpu().numpy()
         eT = t_err(T, ref["T"], ref["flags"])
         eL = l_err(L, ref["L"])
-        errs[p] = {"T_max": float(eT.max()), "T_p99": float(np.percentile(eT, 99)),
-                   "L_max": float(eL.max()), "L_p99": float(np.percentile(eL, 99)),
-                   "resid_max": float(np.abs(rs).max()), "flags_equal": bool((fl == ref["flags"]).all()),
-                   "cells": nc}
-    return base, errs
+        dst[p] = {"T_max": float(eT.max()), "T_p99": float(np.percentile(eT, 99)),
+                  "L_max": float(eL.max()), "L_p99": float(np.percentile(eL, 99)),
+                  "resid_max": float(np.abs(rs).max()), "flags_equal": bool((fl == ref["flags"]).all()),
+                  "cells": nc}
+    return base, errs, extra_errs
 
 
 # ------------------------------------------------------------------ large solve
@@ -772,6 +795,24 @@ def run_large(args, dev, local, ex2_rate):
                 idx = torch.from_numpy(sample).to(dev)
                 kept[prec] = {k: o[k][idx].cpu().numpy() for k in ("T", "L", "flags", "resid")}
             del o
+        if prec != "fp32":
+            # the split's third product left out (an ablation): the GEMM is near its tensor bound here
+            ctx.set_split_products(2)
+            o = ctx.alloc_outputs(C, ld, False, False, True)
+            for _ in range(2):
+                ctx.solve(J, n, out=o, stream=stream)
+            torch.cuda.synchronize()
+            _lib.dust_ctx_profile_read(ctx.handle)
+            _lib.dust_ctx_profile(ctx.handle, True)
+            for _ in range(steps):
+                ctx.solve(J, n, out=o, stream=stream)
+            torch.cuda.synchronize()
+            a, b, c, cnt = _lib.dust_ctx_profile_read(ctx.handle)
+            _lib.dust_ctx_profile(ctx.handle, False)
+            ctx.set_split_products(3)
+            del o
+            r["T_only_two_products"] = {"ms_absorb": round(a / cnt, 4), "ms_solve": round(b / cnt, 4),
+                                        "note": "dust_ctx_set_split_products(ctx, 2), temperatures only"}
         assert ctx.check() == 0
         ctx.close()
         ms_a, ms_b = r["full"]["ms_absorb"], r["full"]["ms_emit"]

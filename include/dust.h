@@ -131,6 +131,15 @@ int dust_ctx_set_fused(dust_ctx *ctx, int fused);
  * DUST_EINVAL for a NULL context. */
 int dust_ctx_set_fused_emit(dust_ctx *ctx, int fused);
 
+/* Ablation of the split precisions' third product: later tensor-core solves
+ * of this context take `products` split products per K step, 3 (the default:
+ * J_hi W_hi + J_lo W_hi + J_hi W_lo, FP32 accumulation, Eq. 6) or 2 (the
+ * last left out: J is split, W rounded to 16 bits once, a relative error of
+ * up to 2^-9 in W).  With 2 the results are not held to the mixed
+ * tolerances; the FP32 path ignores the setting.  Takes the context's lock;
+ * DUST_EINVAL for a NULL context or another count. */
+int dust_ctx_set_split_products(dust_ctx *ctx, int products);
+
 /* Number of kernels that this context's solves (dust_solve and the entry
  * points built on it) have launched since it was created; the server's own
  * launches are counted by dust_server_stats.  Takes the context's lock;

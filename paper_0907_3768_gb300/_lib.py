@@ -34,6 +34,7 @@ _SIGS = {
     "dust_ctx_set_precision": (_i, [_p, _i]),
     "dust_ctx_set_fused": (_i, [_p, _i]),
     "dust_ctx_set_fused_emit": (_i, [_p, _i]),
+    "dust_ctx_set_split_products": (_i, [_p, _i]),
     "dust_ctx_launch_count": (_i, [_p, ctypes.POINTER(ctypes.c_uint64)]),
     "dust_ctx_info": (_i, [_p, _p, _p, _p, _p, _p, _p]),
     "dust_solve": (_i, [_p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]),
@@ -123,6 +124,10 @@ def dust_ctx_set_fused(ctx, fused):
 
 def dust_ctx_set_fused_emit(ctx, fused):
     return check(lib().dust_ctx_set_fused_emit(ctx, 1 if fused else 0))
+
+
+def dust_ctx_set_split_products(ctx, products):
+    return check(lib().dust_ctx_set_split_products(ctx, int(products)))
 
 
 def dust_ctx_launch_count(ctx):

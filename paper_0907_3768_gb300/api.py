@@ -87,6 +87,11 @@ class Context:
         """Temperature solve and emission as one warp-specialized kernel, where it applies."""
         _lib.dust_ctx_set_fused_emit(self.handle, fused)
 
+    def set_split_products(self, products=3):
+        """Split products per K step of the tensor-core precisions: 3 (default) or 2
+        (the J_hi W_lo product left out; an ablation, not held to the mixed tolerances)."""
+        _lib.dust_ctx_set_split_products(self.handle, products)
+
     def check(self):
         """Device status word since the last check (0 = DUST_OK)."""
         return _lib.dust_ctx_check(self.handle)

@@ -548,6 +548,14 @@ int dust_ctx_set_fused_emit(dust_ctx *ctx, int fused) {
     return DUST_OK;
 }
 
+int dust_ctx_set_split_products(dust_ctx *ctx, int products) {
+    if (!ctx) return set_error(DUST_EINVAL, "ctx is NULL");
+    if (products != 2 && products != 3) return set_error(DUST_EINVAL, "products must be 2 or 3, not %d", products);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->split_products = products;
+    return DUST_OK;
+}
+
 int dust_ctx_launch_count(dust_ctx *ctx, uint64_t *count) {
     if (!ctx || !count) return set_error(DUST_EINVAL, "ctx and count must be non-NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);

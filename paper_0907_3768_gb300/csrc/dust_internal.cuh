@@ -166,6 +166,7 @@ struct EmitPlan {
 struct TcReq {
     int64_t C, tile_begin;
     int Gs, nkc;
+    int nparts;  // split products per K step: 3 (hi.hi + lo.hi + hi.lo), or 2 without hi.lo (an ablation)
     const uint16_t *Wimg;
     float *S;
 };
@@ -206,6 +207,8 @@ struct dust_ctx {
     // solve and emission as one warp-specialized kernel where it applies
     // (dust_ctx_set_fused_emit)
     bool fused_emit = true;
+    // split products of the tensor-core precisions (dust_ctx_set_split_products)
+    int split_products = 3;
     // kernels launched by this context's solves (dust_ctx_launch_count)
     uint64_t launches = 0;
     int K = 0, G = 0, NT = 0, NI = 0;

@@ -398,7 +398,7 @@ __device__ __forceinline__ void gemm_body(const TcBatch &p, const SolveList *sl)
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
                 ri = tc_req_of(p, tile, ri);
-                const int Gs = p.req[ri].Gs, nkc = p.req[ri].nkc;
+                const int Gs = p.req[ri].Gs, nkc = p.req[ri].nkc, np = p.req[ri].nparts;
                 const int b = (int)(it % nacc);
                 const uint32_t ub = (uint32_t)((it / nacc) & 1);
                 const uint32_t d_tmem = tmem + (uint32_t)(b * p.tmem_cols);
@@ -416,7 +416,8 @@ __device__ __forceinline__ void gemm_body(const TcBatch &p, const SolveList *sl)
                     for (int ks = 0; ks < KC / 16; ++ks) {
 #pragma unroll
                         for (int part = 0; part < 3; ++part) {
-                            // hi.hi, lo.hi, hi.lo
+                            // hi.hi, lo.hi, hi.lo (np = 2: the last left out)
+                            if (part >= np) break;
                             const uint32_t aoff = (part == 1 ? A_BYTES : 0) + ks * 256;
                             const uint32_t boff = (part == 2 ? Gs * KC * 2 : 0) + ks * 256;
                             const uint32_t acc = (kc | ks | part) ? 1u : 0u;
@@ -709,7 +710,7 @@ __global__ void __launch_bounds__(NTHREADS_T, 1) k_gemm_tc_t(const __grid_consta
             const uint32_t idesc = instr_desc(BF16, MW, BN_T);
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
                 ri = tc_req_of(p, tile, ri);
-                const int nkc = p.req[ri].nkc;
+                const int nkc = p.req[ri].nkc, np = p.req[ri].nparts;
                 const int b = (int)(it & 1);
                 const uint32_t ub = (uint32_t)((it >> 1) & 1);
                 const uint32_t d_tmem = tmem + (uint32_t)(b * BN_T);
@@ -725,7 +726,8 @@ __global__ void __launch_bounds__(NTHREADS_T, 1) k_gemm_tc_t(const __grid_consta
                     for (int ks = 0; ks < KC / 16; ++ks) {
 #pragma unroll
                         for (int part = 0; part < 3; ++part) {
-                            // W hi . J hi, W hi . J lo, W lo . J hi
+                            // W hi . J hi, W hi . J lo, W lo . J hi (np = 2: the last left out)
+                            if (part >= np) break;
                             const uint32_t woff = (part == 2 ? WA_PART : 0) + ks * 256;
                             const uint32_t joff = (part == 1 ? JB_PART : 0) + ks * 256;
                             const uint32_t acc = (kc | ks | part) ? 1u : 0u;
@@ -933,6 +935,7 @@ int make_tc_req(const dust_ctx *ctx, int precision, int64_t C, const float *J, i
     r.nkc = (K + KC - 1) / KC;
     r.Wimg = ctx->Wimg[bf16 ? 0 : 1];
     r.S = S;
+    r.nparts = ctx->split_products;
     return DUST_OK;
 }
 

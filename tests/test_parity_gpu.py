@@ -140,6 +140,34 @@ def test_coarse_tables(n_table, tol_L):
     assert l_err(out["L"], ref["L"]).max() <= tol_L
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+def test_two_split_products(prec):
+    """The ablation of the split's third product (J_hi W_lo): with it left out,
+    W is rounded to 16 bits once (relative error up to 2^-9 in BF16), so the
+    absorbed power moves by up to ~2e-3 and T by that over d ln P / d ln T
+    (>= 1, about 5 on these grains): T is held to 1e-3 and L, whose Wien
+    terms scale T's error further, to 2e-2.  Switching back gives the
+    three-product bits again."""
+    from paper_0907_3768_gb300 import _lib
+
+    wl = synth.make_workload(0)
+    ref = oracle.run_workload(wl)
+    with _ctx(wl, prec) as ctx:
+        a = _run(ctx, wl.J, wl.n, precision=prec)
+        ctx.set_split_products(2)
+        b = _run(ctx, wl.J, wl.n, precision=prec)
+        ctx.set_split_products(3)
+        c = _run(ctx, wl.J, wl.n, precision=prec)
+        with pytest.raises(_lib.DustError) as e:
+            ctx.set_split_products(4)
+        assert e.value.code == _lib.DUST_EINVAL
+    for k in ("T", "L", "flags", "resid"):
+        np.testing.assert_array_equal(a[k], c[k])
+    assert not np.array_equal(a["T"], b["T"])
+    assert t_err(b["T"], ref["T"], ref["flags"]).max(initial=0.0) <= 1e-3
+    assert l_err(b["L"], ref["L"]).max() <= 2e-2
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_odd_shapes(prec):
     """G not a multiple of 16, K not a multiple of 8 or of the 32-wavelength chunk."""
