@@ -41,10 +41,10 @@ KERNEL_SOURCES = {
 }
 RECORDED_TRAFFIC = {
     # kernel: (bytes per launch on the bench's workload, profile summary, sources sha256[:16])
-    "k_solve_emit": (234.767616e6 + 357.851392e6, "profiles/k_solve_emit_2e18cells_K200_G96.md", "29eb5abaef0b1e6f"),
-    "k_emit": (220.908544e6 + 218.850816e6, "profiles/k_emit_2e18cells_K200_G96.md", "29eb5abaef0b1e6f"),
+    "k_solve_emit": (234.642176e6 + 358.232064e6, "profiles/k_solve_emit_2e18cells_K200_G96.md", "1b2b671c702a6864"),
+    "k_emit": (220.631808e6 + 218.775808e6, "profiles/k_emit_2e18cells_K200_G96.md", "1b2b671c702a6864"),
     # the full-size launch, DRAM counters only (one ncu pass; the 2^14-cell --set full capture is in the same file)
-    "k_fluct": (256.075776e6 + 175.334912e6, "profiles/k_fluct_2e14cells_K200_G36_M128.md", "7beca1b27628556b"),
+    "k_fluct": (256.181760e6 + 175.721216e6, "profiles/k_fluct_2e14cells_K200_G36_M128.md", "658010ad4220ac93"),
 }
 
 
