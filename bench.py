@@ -104,6 +104,7 @@ def parse():
     ap.add_argument("--precision", default="bf16x3")
     ap.add_argument("--paths", default="fp32,bf16x3,fp16x3", help="precisions to measure")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-interp-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream measurement")
@@ -454,7 +455,9 @@ def run_ours(args):
         line["fluctuating_grains"] = fluctuating(ctxs[main], wl, J, n, stream, args, world, ex2_rate,
                                                  oracle_sample=rank == 0 and world == 1 and not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"], line["err_vs_oracle"], extra_err = cpu_baseline(args, wl, res, extra_out)
+        line["cpu_baseline"], line["err_vs_oracle"], extra_err, line["cpu_interp_baseline"] = cpu_baseline(
+            args, wl, res, extra_out)
+        line["cpu_interp_baseline"]["gpu_speedup"] = line["value"] / line["cpu_interp_baseline"]["value"]
         if ablation_products is not None:
             ablation_products["err_vs_oracle"] = extra_err.get("two_products")
     if ablation_products is not None:
@@ -736,7 +739,47 @@ def cpu_baseline(args, wl_full, res, extra=None):
                   "L_max": float(eL.max()), "L_p99": float(np.percentile(eL, 99)),
                   "resid_max": float(np.abs(rs).max()), "flags_equal": bool((fl == ref["flags"]).all()),
                   "cells": nc}
-    return base, errs, extra_errs
+    return base, errs, extra_errs, cpu_interp_baseline(args, wl_full, wl, ref)
+
+
+def cpu_interp_baseline(args, wl_full, wl_o, ref):
+    """The paper's CPU production scheme (Section 6, Table 1's "CPU
+    (interpolation)" column): A in full, T from a 2000-point table over
+    3-1500 K, L in full, FP64 on every host core.  Timed on the first cells of
+    the workload (about --cpu-interp-seconds of work; the table build is not
+    timed); its error against the oracle on the oracle's sample cells."""
+    import numpy as np
+
+    import synth
+    from metrics import l_err, t_err
+    from oracle import cpu_interp
+
+    t = time.perf_counter()
+    tab = cpu_interp.for_workload(wl_o)
+    t_tab = time.perf_counter() - t
+    r = tab.run(wl_o.J, wl_o.n)
+    eT = t_err(r["T"], ref["T"], ref["flags"])
+    eL = l_err(r["L"], ref["L"])
+    errs = {"T_max": float(eT.max()), "T_p99": float(np.percentile(eT, 99)), "L_max": float(eL.max()),
+            "L_p99": float(np.percentile(eL, 99)), "flags_equal": bool((r["flags"] == ref["flags"]).all()),
+            "cells": len(wl_o.cells)}
+    probe = synth.make_workload(CONFIG_ID, cells=np.arange(512), seed=wl_full.seed)
+    t = time.perf_counter()
+    tab.run(probe.J, probe.n)
+    per_cell = (time.perf_counter() - t) / 512
+    nc = int(max(512, min(wl_full.n_cells_total, args.cpu_interp_seconds / max(per_cell, 1e-9))))
+    wl = synth.make_workload(CONFIG_ID, cells=np.arange(nc), seed=wl_full.seed)
+    t = time.perf_counter()
+    tab.run(wl.J, wl.n)
+    dt = time.perf_counter() - t
+    from oracle import max_threads
+
+    return {"value": nc * wl.G / dt, "unit": UNIT, "cells_per_s": nc / dt, "cores": max_threads(),
+            "kind": "paper's CPU interpolation scheme",
+            "sample": f"first {nc} of {wl_full.n_cells_total} cells: A (Eq. 6), T from a 2000-point table "
+                      f"over 3-1500 K (uniform in ln T, linear in P), L (Eq. 10); FP64 C + OpenMP, {dt:.1f} s "
+                      f"(table build {t_tab:.2f} s, not timed)",
+            "err_vs_oracle": errs}
 
 
 # ------------------------------------------------------------------ large solve

@@ -1,22 +1,23 @@
-"""Compile the FP64 CPU oracle (test infrastructure) into oracle/_build/."""
+"""Compile the FP64 CPU oracle and the CPU interpolation scheme (test
+infrastructure) into oracle/_build/libdust_oracle.so."""
 import os
 import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "dust_oracle.c")
+SRCS = [os.path.join(HERE, "dust_oracle.c"), os.path.join(HERE, "cpu_interp.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdust_oracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Build libdust_oracle.so if it is missing or older than its source."""
+    """Build libdust_oracle.so if it is missing or older than a source."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in SRCS):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-shared", "-fPIC", SRC, "-o", tmp, "-lm"]
+           "-shared", "-fPIC", *SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
