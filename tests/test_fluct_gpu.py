@@ -96,20 +96,40 @@ def test_fluct_many_levels_and_ragged_grain_count():
     _compare(g, ref, wl.K)
 
 
-@pytest.mark.parametrize("C", [1, 7, 333])
-def test_fluct_cell_results_independent_of_batch(C):
+@pytest.mark.parametrize("C,M,off,species,n_sizes", [
+    (1, 64, 50, ("silicate", "graphite"), 6), (7, 64, 50, ("silicate", "graphite"), 6),
+    (333, 64, 50, ("silicate", "graphite"), 6), (333, 64, 51, ("silicate", "graphite"), 6),
+    (1, 128, 51, ("silicate", "graphite"), 6), (6, 128, 51, ("silicate", "graphite"), 6),
+    (5, 128, 51, ("silicate", "graphite", "pah"), 12), (8, 128, 50, ("silicate", "graphite", "pah"), 12)])
+def test_fluct_cell_results_independent_of_batch(C, M, off, species, n_sizes):
+    """A cell's results do not depend on the batch around it: cells at odd
+    and even offsets, at 64 and 128 levels, with 12 and 36 grains, equal the
+    same cells inside a larger batch, bit for bit."""
     from paper_0907_3768_gb300 import Context, padded_rows
 
-    wl, N, th = _workload(400)
+    wl, N, th = _workload(400, species=species, n_sizes=n_sizes)
     grains = np.arange(wl.G)
     with Context.from_workload(wl) as ctx:
-        ctx.set_fluctuating(grains, N, th, 64)
+        ctx.set_fluctuating(grains, N, th, M)
         J = padded_rows(torch.from_numpy(wl.J).cuda())
         n_f = torch.from_numpy(np.ascontiguousarray(wl.n)).cuda()
         a = {k: v.cpu().numpy() for k, v in ctx.solve_fluct(J, n_f, want_P=True).items()}
-        b = {k: v.cpu().numpy() for k, v in ctx.solve_fluct(J[50:50 + C], n_f[50:50 + C], want_P=True).items()}
+        b = {k: v.cpu().numpy() for k, v in ctx.solve_fluct(J[off:off + C], n_f[off:off + C], want_P=True).items()}
     for k in ("L", "P", "dE"):
-        np.testing.assert_array_equal(a[k][50:50 + C], b[k])
+        np.testing.assert_array_equal(a[k][off:off + C], b[k])
+
+
+def test_fluct_benchmark_grain_count_against_oracle():
+    """36 grains at 128 levels (the benchmark's shape: 8 problem slots, so
+    the fifth pass over the grains is half full) on an odd cell count,
+    element by element against the oracle."""
+    wl, N, th = _workload(9, species=("silicate", "graphite", "pah"), n_sizes=12)
+    grains = np.arange(wl.G)
+    assert len(grains) == 36
+    g = _gpu(wl, grains, N, th, 128)
+    ref = ofl.run(wl.lam, wl.w, wl.C_abs, wl.J, wl.n[:, grains], grains, N[grains], th[grains], 128,
+                  wl.T_min, wl.T_max)
+    _compare(g, ref, wl.K)
 
 
 def test_fluct_energy_balance():
