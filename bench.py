@@ -114,6 +114,7 @@ def parse():
     ap.add_argument("--no-mass", action="store_true", help="skip the dust-mass form n[c,g] = n_g m_c")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused absorption + solve kernel")
     ap.add_argument("--no-fluct", action="store_true", help="skip the thermally fluctuating grains")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the time-per-call sweep over cell counts")
     ap.add_argument("--fluct-levels", type=int, default=128)
     ap.add_argument("--profile-case", choices=["main", "main-two-kernel", "large", "fluct"], default=None,
                     help="no measurement: run --steps solves of one case for a profiler to capture "
@@ -340,6 +341,9 @@ def run_ours(args):
         d2h = C * G * 4 + C * ld * 4 + C * 8 + C * G
         e2e = {"value": aggregate_rate(C * G, world, te), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": round(te * 1e3, 4), "api": "dust_solve_host (pinned host buffers)"}
+    sweep = None
+    if not args.no_sweep and world == 1:
+        sweep = size_sweep(ctxs[main], J, n, stream, None if args.no_e2e else args_h)
 
     # roofline of the dominant kernel: the warp-specialized solve + emission where
     # it applies (its solve is timed with the emission), else the emission kernel;
@@ -415,6 +419,8 @@ def run_ours(args):
         "clocks": clk,
         "e2e": e2e,
     }
+    if sweep is not None:
+        line["size_sweep"] = sweep
     paths = {}
     for p in ctxs:
         r = res[p]
@@ -780,6 +786,61 @@ def cpu_interp_baseline(args, wl_full, wl_o, ref):
                       f"over 3-1500 K (uniform in ln T, linear in P), L (Eq. 10); FP64 C + OpenMP, {dt:.1f} s "
                       f"(table build {t_tab:.2f} s, not timed)",
             "err_vs_oracle": errs}
+
+
+def size_sweep(ctx, J, n, stream, args_h):
+    """Time per call against the number of cells, from 32 to 2^19 (the cell
+    counts of the paper's Table 1): dust_solve on device buffers (CUDA events,
+    the full path with L, resid and flags) and, up to the resident workload's
+    size, dust_solve_host from pinned host buffers (wall clock, copies
+    included).  Below ~2^16 cells the inputs stay in L2: a latency sweep, not
+    a bandwidth one.  2^19 cells repeat the 2^18-cell workload twice."""
+    import torch
+
+    from paper_0907_3768_gb300 import _lib
+
+    C = J.shape[0]
+    J2, n2 = torch.cat([J, J]), torch.cat([n, n])
+    rows = []
+    for Cs in (32, 256, 2048, 16384, 131072, 262144, 524288):
+        if Cs > 2 * C:
+            break
+        Js, ns = (J2, n2) if Cs > C else (J, n)
+        Js, ns = Js[:Cs], ns[:Cs]
+        out = ctx.solve(Js, ns, stream=stream)
+        for _ in range(2):
+            ctx.solve(Js, ns, out=out, stream=stream)
+        reps = max(5, min(200, int(2e6 // Cs)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ctx.solve(Js, ns, out=out, stream=stream)
+        t_issue = (time.perf_counter() - t0) / reps
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_dev = e0.elapsed_time(e1) / reps
+        # host time to issue one call (Python binding, argument checks, five
+        # launches): where it matches ms_device the device waited on the host
+        row = {"cells": Cs, "ms_device": round(ms_dev, 4), "cells_per_s_device": round(Cs / (ms_dev * 1e-3)),
+               "ms_host_issue": round(t_issue * 1e3, 4)}
+        if args_h is not None and Cs <= C:
+            a = list(args_h)
+            a[1] = Cs
+            for _ in range(2):
+                _lib.dust_solve_host(*a)
+            rh = max(3, min(100, int(5e5 // Cs)))
+            t0 = time.perf_counter()
+            for _ in range(rh):
+                _lib.dust_solve_host(*a)
+            ms_h = (time.perf_counter() - t0) / rh * 1e3
+            row.update({"ms_host": round(ms_h, 4), "cells_per_s_host": round(Cs / (ms_h * 1e-3))})
+        rows.append(row)
+    assert ctx.check() == 0
+    del J2, n2
+    return {"api": "dust_solve (device buffers, CUDA events) and dust_solve_host (pinned host buffers, wall clock)",
+            "precision": "bf16x3", "rows": rows}
 
 
 # ------------------------------------------------------------------ large solve

@@ -127,9 +127,13 @@ class Context:
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
         sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-        prec = _prec(precision) if precision is not None else self.info()["precision"]
-        _lib.dust_solve_prec(self.handle, prec, C, J.data_ptr(), ld, n.data_ptr(), out["T"].data_ptr(),
-                             _ptr(out["L_buf"]), _ptr(out["resid"]), _ptr(out["flags"]), sptr)
+        if precision is None:  # the context's own precision
+            _lib.dust_solve(self.handle, C, J.data_ptr(), ld, n.data_ptr(), out["T"].data_ptr(),
+                            _ptr(out["L_buf"]), _ptr(out["resid"]), _ptr(out["flags"]), sptr)
+        else:
+            _lib.dust_solve_prec(self.handle, _prec(precision), C, J.data_ptr(), ld, n.data_ptr(),
+                                 out["T"].data_ptr(), _ptr(out["L_buf"]), _ptr(out["resid"]), _ptr(out["flags"]),
+                                 sptr)
         return out
 
     def submit(self, server, J, n, out=None, want_L=True, want_resid=True, want_flags=True, stream=None):
