@@ -114,7 +114,8 @@ def parse():
     ap.add_argument("--no-mass", action="store_true", help="skip the dust-mass form n[c,g] = n_g m_c")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused absorption + solve kernel")
     ap.add_argument("--no-fluct", action="store_true", help="skip the thermally fluctuating grains")
-    ap.add_argument("--no-sweep", action="store_true", help="skip the time-per-call sweep over cell counts")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the time-per-call sweep over cell counts (also skipped by --no-e2e)")
     ap.add_argument("--fluct-levels", type=int, default=128)
     ap.add_argument("--profile-case", choices=["main", "main-two-kernel", "large", "fluct"], default=None,
                     help="no measurement: run --steps solves of one case for a profiler to capture "
@@ -341,9 +342,11 @@ def run_ours(args):
         d2h = C * G * 4 + C * ld * 4 + C * 8 + C * G
         e2e = {"value": aggregate_rate(C * G, world, te), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": round(te * 1e3, 4), "api": "dust_solve_host (pinned host buffers)"}
+    # time per call against the cell count (with the host entry point, so it
+    # goes with the e2e leg)
     sweep = None
-    if not args.no_sweep and world == 1:
-        sweep = size_sweep(ctxs[main], J, n, stream, None if args.no_e2e else args_h)
+    if not args.no_sweep and not args.no_e2e and world == 1:
+        sweep = size_sweep(ctxs[main], J, n, stream, args_h)
 
     # roofline of the dominant kernel: the warp-specialized solve + emission where
     # it applies (its solve is timed with the emission), else the emission kernel;
