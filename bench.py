@@ -796,8 +796,10 @@ def size_sweep(ctx, J, n, stream, args_h):
     counts of the paper's Table 1): dust_solve on device buffers (CUDA events,
     the full path with L, resid and flags) and, up to the resident workload's
     size, dust_solve_host from pinned host buffers (wall clock, copies
-    included).  Below ~2^16 cells the inputs stay in L2: a latency sweep, not
-    a bandwidth one.  2^19 cells repeat the 2^18-cell workload twice."""
+    included, the median of single calls).  Below ~2^16 cells the inputs stay
+    in L2: a latency sweep, not a bandwidth one.  2^19 cells repeat the
+    2^18-cell workload twice."""
+    import numpy as np
     import torch
 
     from paper_0907_3768_gb300 import _lib
@@ -833,11 +835,15 @@ def size_sweep(ctx, J, n, stream, args_h):
             a[1] = Cs
             for _ in range(2):
                 _lib.dust_solve_host(*a)
-            rh = max(3, min(100, int(5e5 // Cs)))
-            t0 = time.perf_counter()
-            for _ in range(rh):
+            # the median of single calls: a call is host-driven (six copies and
+            # five launches per chunk), so one descheduled host thread would
+            # otherwise move a mean over a few calls
+            tt = []
+            for _ in range(max(7, min(100, int(5e5 // Cs)))):
+                t0 = time.perf_counter()
                 _lib.dust_solve_host(*a)
-            ms_h = (time.perf_counter() - t0) / rh * 1e3
+                tt.append(time.perf_counter() - t0)
+            ms_h = float(np.median(tt)) * 1e3
             row.update({"ms_host": round(ms_h, 4), "cells_per_s_host": round(Cs / (ms_h * 1e-3))})
         rows.append(row)
     assert ctx.check() == 0
