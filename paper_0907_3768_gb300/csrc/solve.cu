@@ -121,7 +121,12 @@ int solve_view(dust_ctx *ctx, int precision, int64_t C, const float *J, int64_t 
     int ftc = 0, fgc = 0;
     const size_t fsmem = !fused && ctx->fused_emit ? plan_solve_emit(ctx, L || resid, mass, &ftc, &fgc) : 0;
     if (fsmem && fgc != p.gcp) return set_error(DUST_EINVAL, "internal: grain passes of the two emission forms differ");
-    if (rc == DUST_OK && (L || resid) && sv.order && sv.bkt && sv.hist) {
+    // The emission order groups cells of like temperatures into the emission's
+    // 32-cell tiles; it never changes a result.  A call of at most one tile per
+    // SM skips it: there the ordering's three launches cost more than the
+    // warp-uniform regimes save.
+    const bool ordered = C > (int64_t)32 * ctx->num_sms;
+    if (rc == DUST_OK && (L || resid) && ordered && sv.order && sv.bkt && sv.hist) {
         // emission order: cells classed by the absorbed power of the reference
         // grain (S), or by its inverse temperature where S stayed in tensor memory
         const int gref = order_ref_grain(ctx->G);
