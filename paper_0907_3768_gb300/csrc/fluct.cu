@@ -360,20 +360,23 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
             }                                                                                 \
         }                                                                                     \
     }
-        // Fast form of a step: no test, only a flag (a branch per step
-        // measured 12 % of the kernel); a block of LW steps whose flag fails
-        // (a value past 2^100, or a level whose factor is not a normal float)
-        // is taken again from its saved state with the tested step.  Every P
-        // of a block that passes is below 2^100, so no register can pass
-        // 2^109 (at most M <= 512 terms P phi with phi <= 1), and after each
-        // block the frame is moved to the newest level when that is above
-        // 2^32.
+        // Fast form of a step: no test (a branch per step measured 12 % of
+        // the kernel, a flag per step 3 %).  A block of LW steps is checked
+        // once, at its end: a block with a value past 2^100, or a level whose
+        // factor is not a normal float, is taken again from its saved state
+        // with the tested step.  The check reads the block's new levels back
+        // off the registers that hold them: once its level is read, a
+        // register only takes zero terms (the pad below phi[1]), so it still
+        // gives the value that was broadcast, or NaN where a later value
+        // overflowed.  Every P of a block that passes is below 2^100, so no
+        // register can pass 2^109 (at most M <= 512 terms P phi with
+        // phi <= 1), and after each block the frame is moved to the newest
+        // level when that is above 2^32.
 #define FL_FAST(J, RS, R0, OWN)                                                               \
     {                                                                                         \
         const int j_ = (J);                                                                   \
         _Pragma("unroll") for (int r = (R0); r < MR; ++r) acc[r] = fmaf(ph[LW * r - j_], pj, acc[r]); \
         pj = __shfl_sync(hmask, acc[RS] * mulx[RS], (OWN), LW);                                \
-        ok &= pj < 0x1p100f;                                                                  \
     }
 #pragma unroll
         for (int r0 = 0; r0 < MR; ++r0) {
@@ -384,11 +387,18 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
 #pragma unroll
             for (int r = 0; r < MR; ++r) LT[hl + LW * r].y = acc[r];
             const float pj0 = pj;
-            bool ok = true;
 #pragma unroll 2
             for (int jj = 0; jj < LW - 1; ++jj) FL_FAST(LW * r0 + jj, r0, r0, jj + 1)
             if (r0 + 1 < MR) FL_FAST(LW * r0 + LW - 1, r0 + 1 < MR ? r0 + 1 : r0, r0 + 1, 0)
-            if (!ok) {  // the same on every lane of the problem (pj is broadcast)
+            // the block's levels: register r0 of lanes 1..LW-1, and register
+            // r0 + 1 of lane 0 (read at the block's last step; none in the
+            // last block)
+            const int rb = hl > 0 ? r0 : r0 + 1;
+            float vb = 0.f;
+#pragma unroll
+            for (int r = 0; r < MR; ++r) vb = r == rb ? acc[r] * mulx[r] : vb;
+            const bool ok = __all_sync(hmask, vb < 0x1p100f);
+            if (!ok) {  // the same on every lane of the problem (a vote)
 #pragma unroll
                 for (int r = 0; r < MR; ++r) acc[r] = LT[hl + LW * r].y;
                 pj = pj0;
