@@ -44,7 +44,7 @@ RECORDED_TRAFFIC = {
     "k_solve_emit": (234.642176e6 + 358.232064e6, "profiles/k_solve_emit_2e18cells_K200_G96.md", "1b2b671c702a6864"),
     "k_emit": (220.631808e6 + 218.775808e6, "profiles/k_emit_2e18cells_K200_G96.md", "1b2b671c702a6864"),
     # the full-size launch, DRAM counters only (one ncu pass; the 2^14-cell --set full capture is in the same file)
-    "k_fluct": (255.956992e6 + 175.320064e6, "profiles/k_fluct_2e14cells_K200_G36_M128.md", "997af84c89fb71e9"),
+    "k_fluct": (255.956992e6 + 175.320064e6, "profiles/k_fluct_2e14cells_K200_G36_M128.md", "2eac562135043b6a"),
 }
 
 

@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(fl_threads(M), fl_min_ctas(M)) k_fluct(const D
         }                                                                                     \
     }
         // Fast form of a step: no test (a branch per step measured 12 % of
-        // the kernel, a flag per step 3 %).  A block of LW steps is checked
+        // the kernel, a flag per step 1.4 %).  A block of LW steps is checked
         // once, at its end: a block with a value past 2^100, or a level whose
         // factor is not a normal float, is taken again from its saved state
         // with the tested step.  The check reads the block's new levels back
